@@ -1,0 +1,197 @@
+"""Python loader for the FP64 CPU oracle (``oracle/oracle.c``).
+
+Test infrastructure only: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it.  The product library never imports
+it, and it imports nothing from the product.
+
+Every function follows the paper section named in ``oracle.c``:
+the dispersion and form factors (Sec. 2), the Matsubara-summed bubble kernels
+of Eq. chi_ph / chi_pp in temperature form, the nested Clenshaw-Curtis pair
+(Sec. 3) and the greedy adaptive loop of Algorithm 1 with the 4-way split of
+Algorithm 2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PH, PP, MONOMIAL, OVERLAP = 0, 1, 2, 3
+CONVERGED, BUDGET, NONFINITE = 0, 1, 2
+MAX_LEVEL = 29
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_p = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, OpenMP, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            lib.oracle_cc_rule.argtypes = [_i, _p, _p]
+            lib.oracle_dispersion.argtypes = [_d] * 5
+            lib.oracle_dispersion.restype = _d
+            lib.oracle_form_factor.argtypes = [_i, _d, _d]
+            lib.oracle_form_factor.restype = _d
+            lib.oracle_kernel_ph.argtypes = [_d, _d, _d]
+            lib.oracle_kernel_ph.restype = _d
+            lib.oracle_kernel_pp.argtypes = [_d, _d, _d]
+            lib.oracle_kernel_pp.restype = _d
+            lib.oracle_integrand_point.argtypes = [_i, _d, _d, _i, _i, _d, _d, _d, _d, _d, _d]
+            lib.oracle_integrand_point.restype = _d
+            lib.oracle_region_eval.argtypes = [_i, _d, _d, _i, _i, _d, _d, _d, _d, _i,
+                                               _i, _i64, _i64, _p, _p]
+            lib.oracle_integrate_batch.argtypes = [_i, _i, _p, _i, _p, _d, _d, _d, _d,
+                                                   _d, _d, _i64, _i, _i, _i, _p, _p, _p, _p]
+            lib.oracle_integrate_list.argtypes = [_i64, _p, _p, _p, _p, _d, _d, _d,
+                                                  _d, _d, _i64, _i, _i, _i, _p, _p, _p, _p]
+            lib.oracle_integrate_trace.argtypes = [_i, _d, _d, _i, _i, _d, _d, _d, _d,
+                                                   _d, _d, _i64, _i, _i, _p, _p, _p,
+                                                   _i64, _p, _p, _p, _p, _p, _p]
+            lib.oracle_max_threads.restype = _i
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def cc_rule(N: int):
+    """Nodes and weights of the N-interval Clenshaw-Curtis rule on [-1, 1]."""
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    if _load().oracle_cc_rule(N, _ptr(x), _ptr(w)) != 0:
+        raise ValueError("invalid rule size %d" % N)
+    return x, w
+
+
+def dispersion(kx, ky, t, tp, mu):
+    return _load().oracle_dispersion(kx, ky, t, tp, mu)
+
+
+def form_factor(n, kx, ky):
+    return _load().oracle_form_factor(n, kx, ky)
+
+
+def kernel_ph(e1, e2, T):
+    return _load().oracle_kernel_ph(e1, e2, T)
+
+
+def kernel_pp(e1, e2, T):
+    return _load().oracle_kernel_pp(e1, e2, T)
+
+
+def integrand_point(kind, q, l, m, T, lat, kx, ky):
+    t, tp, mu = lat
+    return _load().oracle_integrand_point(kind, q[0], q[1], l, m, T, t, tp, mu, kx, ky)
+
+
+def region_eval(kind, q, l, m, T, lat, L, ix, iy, rule_n=4):
+    """(Q_N, Q_2N) of the level-L region with corner index (ix, iy)."""
+    t, tp, mu = lat
+    qN = np.zeros(1)
+    q2N = np.zeros(1)
+    rc = _load().oracle_region_eval(kind, q[0], q[1], l, m, T, t, tp, mu, rule_n,
+                                    L, ix, iy, _ptr(qN), _ptr(q2N))
+    if rc != 0:
+        raise ValueError("invalid rule size")
+    return float(qN[0]), float(q2N[0])
+
+
+def integrate_batch(kind, q, lm, T, lat, rel_tol, abs_tol, max_regions,
+                    rule_n=4, init_level=2, nthreads=0):
+    """Adaptive integrals for every (q, pair); output index iq * npairs + ip.
+
+    Returns (values, errors, regions, status) as numpy arrays."""
+    t, tp, mu = lat
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 2)
+    lm = np.ascontiguousarray(lm, dtype=np.int32).reshape(-1, 2)
+    n = q.shape[0] * lm.shape[0]
+    v = np.zeros(n)
+    e = np.zeros(n)
+    r = np.zeros(n, dtype=np.int64)
+    s = np.zeros(n, dtype=np.int32)
+    rc = _load().oracle_integrate_batch(kind, q.shape[0], _ptr(q), lm.shape[0], _ptr(lm),
+                                        T, t, tp, mu, rel_tol, abs_tol, int(max_regions),
+                                        rule_n, init_level, nthreads,
+                                        _ptr(v), _ptr(e), _ptr(r), _ptr(s))
+    if rc != 0:
+        raise ValueError("oracle_integrate_batch: invalid argument")
+    return v, e, r, s
+
+
+def integrate_list(kind, q, lm, T, lat, rel_tol, abs_tol, max_regions,
+                   rule_n=4, init_level=2, nthreads=0):
+    """Adaptive integrals over a flat list: kind[i], q[i], lm[i], T[i]."""
+    t, tp, mu = lat
+    kind = np.ascontiguousarray(kind, dtype=np.int32).reshape(-1)
+    n = kind.shape[0]
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(n, 2)
+    lm = np.ascontiguousarray(lm, dtype=np.int32).reshape(n, 2)
+    T = np.ascontiguousarray(np.broadcast_to(np.asarray(T, dtype=np.float64), (n,)))
+    v = np.zeros(n)
+    e = np.zeros(n)
+    r = np.zeros(n, dtype=np.int64)
+    s = np.zeros(n, dtype=np.int32)
+    rc = _load().oracle_integrate_list(n, _ptr(kind), _ptr(q), _ptr(lm), _ptr(T), t, tp, mu,
+                                       rel_tol, abs_tol, int(max_regions), rule_n,
+                                       init_level, nthreads, _ptr(v), _ptr(e), _ptr(r), _ptr(s))
+    if rc != 0:
+        raise ValueError("oracle_integrate_list: invalid argument")
+    return v, e, r, s
+
+
+def integrate_trace(kind, q, l, m, T, lat, rel_tol, abs_tol, max_regions,
+                    rule_n=4, init_level=2, trace_cap=1 << 16):
+    """One integral plus its final leaves.
+
+    Returns dict(value, error, regions, status, level, ix, iy, valN, val2N, err)."""
+    t, tp, mu = lat
+    v = np.zeros(1)
+    e = np.zeros(1)
+    nl = np.zeros(1, dtype=np.int64)
+    lev = np.zeros(trace_cap, dtype=np.int32)
+    ix = np.zeros(trace_cap, dtype=np.int64)
+    iy = np.zeros(trace_cap, dtype=np.int64)
+    vN = np.zeros(trace_cap)
+    v2N = np.zeros(trace_cap)
+    er = np.zeros(trace_cap)
+    st = _load().oracle_integrate_trace(kind, q[0], q[1], l, m, T, t, tp, mu, rel_tol, abs_tol,
+                                        int(max_regions), rule_n, init_level, _ptr(v), _ptr(e),
+                                        _ptr(nl), trace_cap, _ptr(lev), _ptr(ix), _ptr(iy),
+                                        _ptr(vN), _ptr(v2N), _ptr(er))
+    if st < 0:
+        raise ValueError("oracle_integrate_trace: invalid argument")
+    k = min(int(nl[0]), trace_cap)
+    return dict(value=float(v[0]), error=float(e[0]), regions=int(nl[0]), status=int(st),
+                level=lev[:k].copy(), ix=ix[:k].copy(), iy=iy[:k].copy(),
+                valN=vN[:k].copy(), val2N=v2N[:k].copy(), err=er[:k].copy())
