@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: converged Brillouin-zone loop integrals per second.
+
+A step is one pass of the whole hot path over one batch: the 93,312-integral
+flow-step batch (ph + pp bubbles at T = 0.05, q on a 24 x 24 zone grid, all
+81 pairs of the 9 two-shell form factors, rel tol 1e-6, abs tol 1e-10,
+<= 1e5 regions per integral), integrated to convergence on the GPU through the
+C ABI (setup, every refinement round, outputs).  Inputs are resident in HBM
+when the timed region starts; `e2e` repeats the measurement through the
+host-buffer entry point with the host<->device copies inside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paid|reference]
+
+`--impl reference` times the FP64 CPU oracle (the reference arm of this
+project) on a bounded seeded sample of the same workload.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged BZ loop integrals/s at rel tol 1e-6, learned+batched vs plain FP64"
+UNIT = "integrals/s"
+# FP64 flops per integrand node of the FP64 region-evaluation kernel
+# (k_eval_fp64, N = 4, 81 nodes per region): per region 4117 DFMA (2 flops),
+# 736 DADD and 1242 DMUL, from the ncu instruction counters of three launches
+# divided by their node evaluations (profiles/k_eval_fp64_first_shell.md).
+FP64_FLOPS_PER_NODE = (2 * 4117 + 736 + 1242) / 81.0
+# DRAM bytes per evaluated region of the same kernel (same capture): eval-list
+# entry and key read, Q_2N and err written.
+EVAL_DRAM_BYTES_PER_REGION = 18.3
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
+    ap.add_argument("--workload", choices=["flow_step", "first_shell"], default="flow_step")
+    ap.add_argument("--eval", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=4096,
+                    help="integrals in the oracle's timed sample")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1610_09991_gb300 import workloads as W
+    if name == "first_shell":
+        return W.config_first_shell(), 5
+    return W.config_flow_step(), 9
+
+
+def workload_config(w, ff, eval_mode):
+    b0 = w.batches[0]
+    return {
+        "workload": w.name,
+        "integrals": w.n,
+        "kinds": sorted({"ph" if b.kind == 0 else "pp" for b in w.batches}),
+        "T": b0.T,
+        "q_points": int(b0.q.shape[0]),
+        "form_factors": ff,
+        "pairs": int(b0.lm.shape[0]),
+        "rel_tol": b0.rel_tol,
+        "abs_tol": b0.abs_tol,
+        "max_regions": b0.max_regions,
+        "rule": "nested Clenshaw-Curtis 5x5 in 9x9",
+        "init_level": 2,
+        "eval": eval_mode,
+        "lattice": {"t": w.lattice[0], "tp": w.lattice[1], "mu": w.lattice[2]},
+        "l2": "256 MiB buffer written before every timed step; the region pool (tens of GB) exceeds L2",
+    }
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- peaks
+def fp64_peak(device):
+    import ctypes
+    from paper_1610_09991_gb300 import build as B
+    lib = ctypes.CDLL(B.PEAKS_LIB)
+    lib.pipe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    out, sec = ctypes.c_double(), ctypes.c_double()
+    peaks = {}
+    for which, name in ((0, "fp64_fma_tflops"), (1, "fp32_fma_tflops"), (2, "mufu_ex2_tops")):
+        if lib.pipe_peak(which, device, 5, ctypes.byref(out), ctypes.byref(sec)) == 0:
+            peaks[name] = out.value / 1e12
+    return peaks
+
+
+# --------------------------------------------------------------------------- oracle
+def cpu_baseline(w, sample, seed=1234):
+    import numpy as np
+    import oracle
+    from paper_1610_09991_gb300 import workloads as W
+    flat = W.flatten(w)
+    idx = W.sample_indices(w.n, sample, seed)
+    b0 = w.batches[0]
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    v, e, r, s = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
+                                       flat["T"][idx], w.lattice, b0.rel_tol, b0.abs_tol,
+                                       b0.max_regions)
+    dt = time.perf_counter() - t0
+    conv = int((s == 0).sum())
+    return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d seeded integrals (seed %d) of the %d-integral batch, all %d host "
+                      "threads, %.1f s" % (len(idx), seed, w.n, cores, dt),
+            "seconds": dt, "converged": conv, "regions_mean": float(r.mean())}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_1610_09991_gb300 import workloads as W
+    oracle.build()
+    w, ff = workload(args.workload)
+    flat = W.flatten(w)
+    b0 = w.batches[0]
+    per_step = 512
+    times, conv = [], 0
+    for k in range(args.warmup + args.steps):
+        idx = W.sample_indices(w.n, per_step, 5000 + k)
+        t0 = time.perf_counter()
+        v, e, r, s = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
+                                           flat["T"][idx], w.lattice, b0.rel_tol, b0.abs_tol,
+                                           b0.max_regions)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            conv += int((s == 0).sum())
+    total = sum(times)
+    value = conv / total
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, ff, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d seeded integrals per step (seeds 5000+k) of the "
+                                       "%d-integral batch, %d host threads" % (per_step, w.n, cores)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_paid(args):
+    import numpy as np
+    import torch
+    from paper_1610_09991_gb300 import build as B
+    B.build()
+    from paper_1610_09991_gb300 import paid as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w, ff = workload(args.workload)
+    ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1,
+                    eval_fp32=1 if args.eval == "fp32" else 0)
+    dev = torch.device("cuda", local)
+    dbs = [dict(kind=b.kind, T=b.T, q=torch.as_tensor(b.q, device=dev),
+                lm=torch.as_tensor(b.lm, dtype=torch.int32, device=dev), rel_tol=b.rel_tol,
+                abs_tol=b.abs_tol, max_regions=b.max_regions) for b in w.batches]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks = fp64_peak(local)
+
+    def step():
+        flush.fill_(1)
+        return ctx.integrate_multi(dbs, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    agg = dict(conv=0, budget=0, region_evals=0, node_evals=0, launches=0, eval_launches=0,
+               eval_ms=0.0, reduce_ms=0.0, scan_ms=0.0, split_ms=0.0, rounds=0, peak_pool=0)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        outs = step()
+        st = ctx.last_stats()
+        s = torch.cat([o.status for o in outs])
+        agg["conv"] += int((s == 0).sum())
+        agg["budget"] += int((s == 1).sum())
+        for k in ("region_evals", "node_evals", "launches", "eval_launches", "eval_ms",
+                  "reduce_ms", "scan_ms", "split_ms", "rounds"):
+            agg[k] += st[k]
+        agg["peak_pool"] = max(agg["peak_pool"], st["peak_pool"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        c = torch.tensor([agg["conv"]], device=dev, dtype=torch.float64)
+        dist.all_reduce(c)
+        conv_all = float(c.item())
+    else:
+        conv_all = agg["conv"]
+    value = conv_all / elapsed
+
+    # e2e: host numpy inputs -> pinned H2D -> integrate -> D2H, wall clock
+    e2e = None
+    if not args.no_e2e:
+        hb = [dict(kind=b.kind, T=b.T, q=b.q, lm=b.lm, rel_tol=b.rel_tol, abs_tol=b.abs_tol,
+                   max_regions=b.max_regions) for b in w.batches]
+        torch.cuda.synchronize()
+        n_e2e = 1
+        t0 = time.perf_counter()
+        conv_e2e, h2d, d2h = 0, 0, 0
+        for _ in range(n_e2e):
+            flush.fill_(1)
+            res, h2d, d2h = ctx.integrate_host(hb)
+            conv_e2e += sum(int((r.status == 0).sum()) for r in res)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": conv_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": n_e2e}
+
+    eval_s = agg["eval_ms"] / 1e3
+    roof = None
+    if FP64_FLOPS_PER_NODE and eval_s > 0 and args.eval == "fp64":
+        achieved = agg["node_evals"] * FP64_FLOPS_PER_NODE / eval_s / 1e12
+        pk = peaks.get("fp64_fma_tflops")
+        per_launch = agg["region_evals"] / max(1, agg["eval_launches"])
+        roof = {"bound": "alu", "kernel": "k_eval_fp64", "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": achieved / pk if pk else None,
+                "traffic": EVAL_DRAM_BYTES_PER_REGION * per_launch,
+                "traffic_note": "bytes per average launch, scaled by regions from the ncu "
+                                "capture of the 400-integral case (18.3 B/region)",
+                "peak_source": "measured FP64 FMA micro-benchmark in this run (pipe_peaks.cu)",
+                "flops_per_node": FP64_FLOPS_PER_NODE}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.eval == "fp64" else "f32+f64", "data": "synthetic",
+        "config": workload_config(w, ff, args.eval),
+        "clocks": clk, "roofline": roof, "gpu_launches": agg["launches"],
+        "e2e": e2e,
+        "path": "plain batched FP64 GPU cubature (learned proposal not used)",
+        "budget_integrals_per_step": agg["budget"] / args.steps,
+        "region_evals_per_s": agg["region_evals"] * world / elapsed,
+        "node_evals_per_s": agg["node_evals"] * world / elapsed,
+        "rounds_per_step": agg["rounds"] / args.steps,
+        "peak_pool_regions": agg["peak_pool"],
+        "kernel_ms_per_step": {k: agg[k] / args.steps for k in
+                               ("eval_ms", "reduce_ms", "scan_ms", "split_ms")},
+        "eval_launches": agg["eval_launches"],
+        "pipe_peaks": peaks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_paid(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

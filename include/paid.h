@@ -1,0 +1,183 @@
+/*
+ * paid.h -- C ABI of the GB300 (sm_103a) batched adaptive cubature of
+ * Brillouin-zone bubble integrals (PAID hot path).
+ *
+ * What is computed.  For each integral (kind, q, l, m, T) the library returns
+ *
+ *   ph: I = (1/(2pi)^2) Int_D f_l(k) f_m(k+q) [nF(e(k+q)) - nF(e(k))] / (e(k) - e(k+q)) d^2k
+ *   pp: I = (1/(2pi)^2) Int_D f_l(k) f_m(q-k) [1 - nF(e(k)) - nF(e(q-k))] / (e(k) + e(q-k)) d^2k
+ *
+ * over D = [-pi, pi]^2, with the analytic limit -nF'(e) at a vanishing
+ * denominator -- the momentum integrals of the paper's Eq. chi_ph / chi_pp
+ * (Sec. 2) after the Matsubara sum at temperature T.  The dispersion is the
+ * t-t' square-lattice one of Sec. 2,
+ *   e(k) = -2t (cos kx + cos ky) - 4t' cos kx cos ky - mu,
+ * and f_n are the orthonormal lattice form factors of Sec. 2:
+ *   f0 = 1, f1 = cx + cy, f2 = cx - cy, f3 = sqrt2 sx, f4 = sqrt2 sy,
+ *   f5 = 2 cx cy, f6 = 2 sx sy, f7 = 2 sx cy, f8 = 2 cx sy
+ * (cx = cos kx, sx = sin kx, ...).  Two test kinds share the same path:
+ * PAID_OVERLAP (kernel = 1, integrand f_l(k) f_m(k+q)/(2pi)^2) and
+ * PAID_MONOMIAL (integrand (kx/pi)^l (ky/pi)^m/(2pi)^2, 0 <= l, m <= 30).
+ *
+ * How.  Adaptive cubature (Algorithm 1, with the 4-way split of
+ * Algorithm 2): every region carries the nested Clenshaw-Curtis pair
+ * Q_N, Q_2N and err = |Q_N - Q_2N| (Sec. 3); the returned value is the sum of
+ * Q_2N over the final regions (Listing 5) and the returned error the sum of
+ * err.  Unlike the paper's one serial heap per group, each integral keeps its
+ * own convergence test E <= max(abs_tol, rel_tol |V|), and each round splits,
+ * per unconverged integral, the largest-error set of regions whose error
+ * covers the excess over the tolerance (a batched extract-max, Listing 2).
+ *
+ * Conventions (all entry points):
+ *   - Device pointers are CUDA device memory on the context's device; host
+ *     pointers are ordinary host memory.  The caller owns every buffer and
+ *     must keep it alive until the work on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
+ *   - Return value: PAID_OK or a negative paid_rc.  Argument errors are
+ *     detected on the host before any work is queued.  Per-integral outcomes
+ *     are in `status` (paid_status).  paid_last_error() gives a message.
+ *   - A context is used by one host thread at a time.
+ *   - Output order of a batch: idx = iq * npairs + ip.
+ *   - The integrate calls run their round loop from the host and return when
+ *     the outputs are complete (they synchronise `stream`).
+ */
+#ifndef PAID_H
+#define PAID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct paid_ctx paid_ctx;
+
+/* Form-factor sets (Sec. 2): one bond shell (5 functions) or two (9). */
+typedef enum { PAID_FF_SHELL1 = 5, PAID_FF_SHELL12 = 9 } paid_ffset;
+
+/* Integrand kinds. */
+typedef enum { PAID_PH = 0, PAID_PP = 1, PAID_MONOMIAL = 2, PAID_OVERLAP = 3 } paid_kind;
+
+/* Call status. */
+typedef enum {
+    PAID_OK = 0,
+    PAID_ERR_ARG = -1,      /* invalid argument; nothing was queued */
+    PAID_ERR_OOM = -2,      /* workspace too small for the integral count */
+    PAID_ERR_CUDA = -3,     /* a CUDA call failed; see paid_last_error */
+    PAID_ERR_POOL = -4,     /* region pool full; unfinished integrals have status PAID_POOL */
+    PAID_ERR_TIMEOUT = -5   /* round cap reached; unfinished integrals have status PAID_ROUNDCAP */
+} paid_rc;
+
+/* Per-integral status. */
+typedef enum {
+    PAID_CONVERGED = 0,     /* E <= max(abs_tol, rel_tol |V|) */
+    PAID_BUDGET = 1,        /* region budget (or the deepest level) reached first */
+    PAID_NONFINITE = 2,     /* V or E not finite (NaN/Inf input, invalid l or m) */
+    PAID_ROUNDCAP = 3,      /* options.max_rounds reached */
+    PAID_POOL = 4           /* region pool capacity reached */
+} paid_status;
+
+/* Options; paid_options_default() fills the defaults named here. */
+typedef struct {
+    int rule_n;             /* N of the nested CC pair (coarse N, fine 2N intervals): 4 or 6. Default 4 */
+    int init_level;         /* L0: initial uniform partition of D into 4^L0 regions, 0..8. Default 2 */
+    int eval_fp32;          /* 1: integrand in FP32, sums in FP64. Default 0 (all FP64) */
+    int max_rounds;         /* cap on refinement rounds. Default 4096 */
+    double cover;           /* the regions split in a round cover (E - cover * tol) of the error. Default 0.5 */
+    int64_t pool_capacity;  /* regions in the pool; 0 = the most the workspace holds. Default 0 */
+    int timing;             /* 1: time every kernel class with CUDA events on the call's stream
+                               (totals in paid_stats). Default 0 */
+} paid_options;
+
+/* Statistics of the last integrate call on a context. */
+typedef struct {
+    int rounds;                 /* refinement rounds run */
+    int64_t region_evals;       /* regions evaluated (each 81 nodes at N = 4) */
+    int64_t node_evals;         /* integrand evaluations */
+    int64_t peak_pool;          /* largest pool occupancy (regions) */
+    int64_t pool_capacity;      /* capacity used */
+    int64_t n_integrals;
+    int64_t launches;           /* kernels launched by the call */
+    int64_t eval_launches;      /* region-evaluation launches */
+    double eval_ms;             /* with options.timing: summed device time of ... */
+    double reduce_ms;           /* ... region evaluation, reduce + test, */
+    double scan_ms;             /* ... slot scan, */
+    double split_ms;            /* ... split + compaction (0 without timing) */
+} paid_stats;
+
+/* Fill *opt with the defaults.  Returns PAID_OK or PAID_ERR_ARG (opt NULL). */
+int paid_options_default(paid_options* opt);
+
+/* Create a context on CUDA device `device` for lattice (t, t', mu) and the
+ * form-factor set `ffset` (PAID_FF_SHELL1 or PAID_FF_SHELL12).  `opt` may be
+ * NULL for the defaults.  The context owns a small pinned host block and
+ * nothing else; all work memory comes from the caller's workspace.
+ * Returns PAID_OK and *out, or PAID_ERR_ARG / PAID_ERR_CUDA. */
+int paid_create(paid_ctx** out, double t, double tp, double mu, int ffset,
+                const paid_options* opt, int device);
+
+/* Release a context (NULL is allowed). */
+void paid_destroy(paid_ctx* ctx);
+
+/* Bytes of device workspace needed for `n_integrals` integrals and a pool of
+ * `pool_capacity` regions (pool_capacity >= n_integrals * 4^init_level).
+ * Returns PAID_OK and *bytes, or PAID_ERR_ARG. */
+int paid_workspace_size(paid_ctx* ctx, int64_t n_integrals, int64_t pool_capacity,
+                        size_t* bytes);
+
+/* Largest pool capacity (regions) that `ws_bytes` of workspace holds for
+ * `n_integrals` integrals.  Returns PAID_OK and *capacity (0 if none fits). */
+int paid_pool_capacity(paid_ctx* ctx, int64_t n_integrals, size_t ws_bytes,
+                       int64_t* capacity);
+
+/* One batch of integrals of one kind at one temperature.
+ *   q       device, double [nq][2]        transfer momenta (qx, qy)
+ *   lm      device, int32  [npairs][2]    form-factor pairs (l, m)
+ *   values  device, double [nq*npairs]    sum of Q_2N over the final regions
+ *   errors  device, double [nq*npairs]    sum of |Q_N - Q_2N| over them
+ *   regions device, int64  [nq*npairs]    final region count
+ *   status  device, int32  [nq*npairs]    paid_status
+ * rel_tol, abs_tol >= 0; max_regions >= 4^init_level (at most 2^23).
+ * workspace: device memory of ws_bytes (>= paid_workspace_size). */
+int paid_integrate_batch(paid_ctx* ctx, int kind,
+                         int nq, const double* q, int npairs, const int32_t* lm,
+                         double T, double rel_tol, double abs_tol, int64_t max_regions,
+                         double* values, double* errors, int64_t* regions, int32_t* status,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/* Several batches (kinds and temperatures) drained together in one pool:
+ * the argument meanings are those of paid_integrate_batch, per batch. */
+typedef struct {
+    int kind;
+    double T;
+    int nq;
+    const double* q;
+    int npairs;
+    const int32_t* lm;
+    double rel_tol;
+    double abs_tol;
+    int64_t max_regions;
+    double* values;
+    double* errors;
+    int64_t* regions;
+    int32_t* status;
+} paid_batch;
+
+int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/* Statistics of the last integrate call.  Returns PAID_OK or PAID_ERR_ARG. */
+int paid_last_stats(paid_ctx* ctx, paid_stats* out);
+
+/* Static message for a paid_rc. */
+const char* paid_error_string(int rc);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
+const char* paid_last_error(paid_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAID_H */

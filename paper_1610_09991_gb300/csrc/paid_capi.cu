@@ -1,0 +1,413 @@
+// C ABI of libpaid (declared in include/paid.h) and the host-side round
+// scheduler.  The scheduler drives the device loop of the paper's Listing 5:
+//
+//   setup:  uniform level-L0 partition of every integral (Listing 1)
+//   round:  evaluate the regions on the eval list (Listing 3)
+//           -> per-integral reduce + convergence test + selection (Listings 2, 4)
+//           -> prefix scan of the next pool / eval list / active list
+//           -> split the selected regions and compact the pool
+//   until no integral is refining (the master's `done`, Listing 5).
+//
+// The host reads one 32-byte totals block per round (the loop's only
+// device-to-host traffic) to size the next launches and to detect a full pool.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/paid.h"
+#include "paid_internal.cuh"
+
+using namespace paid;
+
+struct paid_ctx {
+    int device = 0;
+    Lattice lat{};
+    int nff = 9;
+    paid_options opt{};
+    RoundTotals* h_totals = nullptr;   // pinned
+    cudaEvent_t ev[6] = {};            // kernel-class timing (options.timing)
+    std::string last_error;
+    paid_stats stats{};
+};
+
+namespace {
+
+constexpr int kMaxBatches = 4096;
+constexpr int64_t kMaxRegionsPerIntegral = int64_t(1) << 23;
+constexpr int64_t kMaxCapacity = int64_t(0xffffffffu);
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t batches, totals, trig, meta, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
+        thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
+        err0, err1, evl, end;
+};
+
+// Byte offsets of every workspace array for n integrals and capacity cap.
+Layout layout(int64_t n, int64_t cap)
+{
+    Layout L{};
+    const int64_t nblk = (n + kScanBlock - 1) / kScanBlock + 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.batches = take(sizeof(DevBatch) * kMaxBatches);
+    L.totals = take(sizeof(RoundTotals));
+    L.trig = take(sizeof(QTrig) * n);
+    L.meta = take(4 * n);
+    L.seg_base = take(4 * n);
+    L.seg_count = take(4 * n);
+    L.active0 = take(4 * n);
+    L.active1 = take(4 * n);
+    L.cnt_new = take(4 * n);
+    L.cnt_eval = take(4 * n);
+    L.thr = take(8 * n);
+    L.pre_pool = take(8 * n);
+    L.pre_eval = take(8 * n);
+    L.pre_act = take(4 * n);
+    L.blk_pool = take(8 * nblk);
+    L.blk_eval = take(8 * nblk);
+    L.blk_act = take(4 * nblk);
+    L.key0 = take(8 * cap);
+    L.key1 = take(8 * cap);
+    L.val0 = take(8 * cap);
+    L.val1 = take(8 * cap);
+    L.err0 = take(8 * cap);
+    L.err1 = take(8 * cap);
+    L.evl = take(8 * cap);
+    L.end = o;
+    return L;
+}
+
+int fail(paid_ctx* ctx, int rc, const std::string& msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return rc;
+}
+
+int cuda_fail(paid_ctx* ctx, cudaError_t e, const char* where)
+{
+    return fail(ctx, PAID_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_finite_d(double x) { return std::isfinite(x); }
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) { if (cudaGetDevice(&prev) != cudaSuccess) prev = -1; cudaSetDevice(dev); }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+int check_options(const paid_options& o, std::string& why)
+{
+    if (o.rule_n != 4 && o.rule_n != 6) { why = "rule_n must be 4 or 6"; return PAID_ERR_ARG; }
+    if (o.init_level < 0 || o.init_level > 8) { why = "init_level must be in 0..8"; return PAID_ERR_ARG; }
+    if (o.eval_fp32 != 0 && o.eval_fp32 != 1) { why = "eval_fp32 must be 0 or 1"; return PAID_ERR_ARG; }
+    if (o.max_rounds < 1) { why = "max_rounds must be >= 1"; return PAID_ERR_ARG; }
+    if (!(o.cover >= 0.0 && o.cover <= 1.0)) { why = "cover must be in [0, 1]"; return PAID_ERR_ARG; }
+    if (o.pool_capacity < 0) { why = "pool_capacity must be >= 0"; return PAID_ERR_ARG; }
+    if (o.timing != 0 && o.timing != 1) { why = "timing must be 0 or 1"; return PAID_ERR_ARG; }
+    return PAID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int paid_options_default(paid_options* opt)
+{
+    if (!opt) return PAID_ERR_ARG;
+    opt->rule_n = 4;
+    opt->init_level = 2;
+    opt->eval_fp32 = 0;
+    opt->max_rounds = 4096;
+    opt->cover = 0.5;
+    opt->pool_capacity = 0;
+    opt->timing = 0;
+    return PAID_OK;
+}
+
+const char* paid_error_string(int rc)
+{
+    switch (rc) {
+    case PAID_OK: return "ok";
+    case PAID_ERR_ARG: return "invalid argument";
+    case PAID_ERR_OOM: return "workspace too small";
+    case PAID_ERR_CUDA: return "CUDA error";
+    case PAID_ERR_POOL: return "region pool full";
+    case PAID_ERR_TIMEOUT: return "round cap reached";
+    default: return "unknown error";
+    }
+}
+
+const char* paid_last_error(paid_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int paid_create(paid_ctx** out, double t, double tp, double mu, int ffset,
+                const paid_options* opt, int device)
+{
+    if (!out) return PAID_ERR_ARG;
+    *out = nullptr;
+    if (!is_finite_d(t) || !is_finite_d(tp) || !is_finite_d(mu)) return PAID_ERR_ARG;
+    if (ffset != PAID_FF_SHELL1 && ffset != PAID_FF_SHELL12) return PAID_ERR_ARG;
+    paid_options o;
+    paid_options_default(&o);
+    if (opt) o = *opt;
+    std::string why;
+    if (check_options(o, why) != PAID_OK) return PAID_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return PAID_ERR_CUDA;
+    DeviceGuard guard(device);
+    if (init_rule_tables(device) != cudaSuccess) return PAID_ERR_CUDA;
+    paid_ctx* c = new (std::nothrow) paid_ctx();
+    if (!c) return PAID_ERR_OOM;
+    c->device = device;
+    c->lat = Lattice{t, tp, mu};
+    c->nff = ffset;
+    c->opt = o;
+    if (cudaMallocHost(&c->h_totals, sizeof(RoundTotals)) != cudaSuccess) {
+        delete c;
+        return PAID_ERR_CUDA;
+    }
+    for (auto& e : c->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            paid_destroy(c);
+            return PAID_ERR_CUDA;
+        }
+    }
+    *out = c;
+    return PAID_OK;
+}
+
+void paid_destroy(paid_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
+    for (auto e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+int paid_workspace_size(paid_ctx* ctx, int64_t n_integrals, int64_t pool_capacity, size_t* bytes)
+{
+    if (!ctx || !bytes || n_integrals < 0) return fail(ctx, PAID_ERR_ARG, "bad argument");
+    const int64_t n0 = int64_t(1) << (2 * ctx->opt.init_level);
+    if (pool_capacity < n_integrals * n0 || pool_capacity > kMaxCapacity)
+        return fail(ctx, PAID_ERR_ARG, "pool_capacity must be >= n_integrals * 4^init_level and < 2^32");
+    *bytes = layout(n_integrals, pool_capacity).end;
+    return PAID_OK;
+}
+
+int paid_pool_capacity(paid_ctx* ctx, int64_t n_integrals, size_t ws_bytes, int64_t* capacity)
+{
+    if (!ctx || !capacity || n_integrals < 0) return fail(ctx, PAID_ERR_ARG, "bad argument");
+    const size_t fixed = layout(n_integrals, 0).end;
+    // 7 arrays of 8 bytes per region plus up to 7 * 256 bytes of alignment
+    int64_t cap = ws_bytes > fixed + 7 * 256 ? int64_t((ws_bytes - fixed - 7 * 256) / 56) : 0;
+    cap = std::min(cap, kMaxCapacity);
+    while (cap > 0 && layout(n_integrals, cap).end > ws_bytes) --cap;
+    *capacity = cap;
+    return PAID_OK;
+}
+
+int paid_last_stats(paid_ctx* ctx, paid_stats* out)
+{
+    if (!ctx || !out) return PAID_ERR_ARG;
+    *out = ctx->stats;
+    return PAID_OK;
+}
+
+int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace,
+                         size_t ws_bytes, void* stream)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    ctx->last_error.clear();
+    ctx->stats = paid_stats{};
+    if (nb < 0 || nb > kMaxBatches || (nb > 0 && !batches))
+        return fail(ctx, PAID_ERR_ARG, "nb must be in 0..4096 with a batch array");
+    const paid_options& o = ctx->opt;
+    const int64_t n0 = int64_t(1) << (2 * o.init_level);
+    std::vector<DevBatch> hb;
+    hb.reserve(nb);
+    int64_t n = 0;
+    for (int i = 0; i < nb; ++i) {
+        const paid_batch& b = batches[i];
+        if (b.kind < PAID_PH || b.kind > PAID_OVERLAP) return fail(ctx, PAID_ERR_ARG, "bad kind");
+        if (b.nq < 0 || b.npairs < 0) return fail(ctx, PAID_ERR_ARG, "nq, npairs must be >= 0");
+        const int64_t nbi = int64_t(b.nq) * b.npairs;
+        if (nbi > 0 && (!b.q || !b.lm || !b.values || !b.errors || !b.regions || !b.status))
+            return fail(ctx, PAID_ERR_ARG, "null buffer");
+        if (!(b.rel_tol >= 0.0) || !(b.abs_tol >= 0.0))
+            return fail(ctx, PAID_ERR_ARG, "tolerances must be >= 0");
+        if (b.max_regions < n0 || b.max_regions > kMaxRegionsPerIntegral)
+            return fail(ctx, PAID_ERR_ARG, "max_regions must be in [4^init_level, 2^23]");
+        if (nbi == 0) continue;
+        DevBatch d{};
+        d.kind = b.kind;
+        d.nq = b.nq;
+        d.npairs = b.npairs;
+        d.T = b.T;
+        d.inv2T = 1.0 / (2.0 * b.T);
+        d.inv4T = 1.0 / (4.0 * b.T);
+        d.rel_tol = b.rel_tol;
+        d.abs_tol = b.abs_tol;
+        d.max_regions = b.max_regions;
+        d.first = n;
+        d.q = b.q;
+        d.lm = b.lm;
+        d.values = b.values;
+        d.errors = b.errors;
+        d.regions = b.regions;
+        d.status = b.status;
+        hb.push_back(d);
+        n += nbi;
+    }
+    ctx->stats.n_integrals = n;
+    if (n == 0) return PAID_OK;
+    if (n > int64_t(0x7fffffff)) return fail(ctx, PAID_ERR_ARG, "too many integrals");
+    if (!workspace) return fail(ctx, PAID_ERR_ARG, "null workspace");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+        return fail(ctx, PAID_ERR_ARG, "workspace must be 256-byte aligned");
+
+    int64_t cap = 0;
+    paid_pool_capacity(ctx, n, ws_bytes, &cap);
+    if (o.pool_capacity > 0) cap = std::min(cap, o.pool_capacity);
+    if (cap < n * n0)
+        return fail(ctx, PAID_ERR_OOM, "workspace too small for the initial partition");
+
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout L = layout(n, cap);
+    char* base = static_cast<char*>(workspace);
+    Work w{};
+    w.batches = reinterpret_cast<DevBatch*>(base + L.batches);
+    w.nb = int(hb.size());
+    w.n = n;
+    w.cap = cap;
+    w.totals = reinterpret_cast<RoundTotals*>(base + L.totals);
+    w.trig = reinterpret_cast<QTrig*>(base + L.trig);
+    w.meta = reinterpret_cast<uint32_t*>(base + L.meta);
+    w.seg_base = reinterpret_cast<uint32_t*>(base + L.seg_base);
+    w.seg_count = reinterpret_cast<uint32_t*>(base + L.seg_count);
+    w.active[0] = reinterpret_cast<uint32_t*>(base + L.active0);
+    w.active[1] = reinterpret_cast<uint32_t*>(base + L.active1);
+    w.cnt_new = reinterpret_cast<uint32_t*>(base + L.cnt_new);
+    w.cnt_eval = reinterpret_cast<uint32_t*>(base + L.cnt_eval);
+    w.thr = reinterpret_cast<uint2*>(base + L.thr);
+    w.pre_pool = reinterpret_cast<unsigned long long*>(base + L.pre_pool);
+    w.pre_eval = reinterpret_cast<unsigned long long*>(base + L.pre_eval);
+    w.pre_act = reinterpret_cast<uint32_t*>(base + L.pre_act);
+    w.blk_pool = reinterpret_cast<unsigned long long*>(base + L.blk_pool);
+    w.blk_eval = reinterpret_cast<unsigned long long*>(base + L.blk_eval);
+    w.blk_act = reinterpret_cast<uint32_t*>(base + L.blk_act);
+    w.key[0] = reinterpret_cast<uint64_t*>(base + L.key0);
+    w.key[1] = reinterpret_cast<uint64_t*>(base + L.key1);
+    w.val[0] = reinterpret_cast<double*>(base + L.val0);
+    w.val[1] = reinterpret_cast<double*>(base + L.val1);
+    w.err[0] = reinterpret_cast<double*>(base + L.err0);
+    w.err[1] = reinterpret_cast<double*>(base + L.err1);
+    w.evl = reinterpret_cast<uint2*>(base + L.evl);
+
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "batch upload");
+    if ((e = launch_setup(w, o.init_level, ctx->nff, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "setup");
+
+    const int nodes = (2 * o.rule_n + 1) * (2 * o.rule_n + 1);
+    const bool timed = o.timing != 0;
+    cudaEvent_t* ev = ctx->ev;
+    auto mark = [&](int i) { return timed ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    auto span = [&](int a, int b) {
+        float ms = 0.f;
+        return (timed && cudaEventElapsedTime(&ms, ev[a], ev[b]) == cudaSuccess) ? double(ms) : 0.0;
+    };
+    paid_stats& st = ctx->stats;
+    st.launches = 1;
+    int64_t n_active = n, n_eval = n * n0, pool = n * n0;
+    int cur = 0;
+    int rc = PAID_OK;
+    bool split_pending = false;
+    for (int round = 0;; ++round) {
+        st.region_evals += n_eval;
+        st.peak_pool = std::max(st.peak_pool, pool);
+        if ((e = mark(0)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+        if ((e = launch_eval(w, cur, n_eval, o.rule_n, o.eval_fp32, ctx->lat, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "eval");
+        if ((e = mark(1)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+        if ((e = launch_reduce_test(w, cur, n_active, round, o.max_rounds, o.cover, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "reduce_test");
+        if ((e = mark(2)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+        if ((e = launch_scan(w, n_active, s)) != cudaSuccess) return cuda_fail(ctx, e, "scan");
+        if ((e = mark(3)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+        st.eval_launches += n_eval > 0 ? 1 : 0;
+        st.launches += (n_eval > 0 ? 1 : 0) + 1 + (n_active > 0 ? 2 : 1);
+        if ((e = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
+                                 cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "totals");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "round sync");
+        if (timed) {
+            st.eval_ms += span(0, 1);
+            st.reduce_ms += span(1, 2);
+            st.scan_ms += span(2, 3);
+            if (split_pending) st.split_ms += span(4, 5);
+        }
+        split_pending = false;
+        const RoundTotals t = *ctx->h_totals;
+        st.rounds = round + 1;
+        if (t.active == 0) {
+            if (round >= o.max_rounds) rc = fail(ctx, PAID_ERR_TIMEOUT, "round cap reached");
+            break;
+        }
+        if (int64_t(t.pool) > cap) {
+            if ((e = launch_finalize(w, cur, n_active, POOL, s)) != cudaSuccess)
+                return cuda_fail(ctx, e, "finalize");
+            st.launches += 1;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "finalize sync");
+            rc = fail(ctx, PAID_ERR_POOL, "region pool full (capacity " + std::to_string(cap) + ")");
+            break;
+        }
+        if ((e = mark(4)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+        if ((e = launch_split(w, cur, n_active, s)) != cudaSuccess) return cuda_fail(ctx, e, "split");
+        if ((e = mark(5)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+        st.launches += 1;
+        split_pending = true;
+        n_active = int64_t(t.active);
+        n_eval = int64_t(t.eval);
+        pool = int64_t(t.pool);
+        cur ^= 1;
+    }
+    st.node_evals = st.region_evals * nodes;
+    st.pool_capacity = cap;
+    return rc;
+}
+
+int paid_integrate_batch(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
+                         const int32_t* lm, double T, double rel_tol, double abs_tol,
+                         int64_t max_regions, double* values, double* errors, int64_t* regions,
+                         int32_t* status, void* workspace, size_t ws_bytes, void* stream)
+{
+    paid_batch b;
+    b.kind = kind;
+    b.T = T;
+    b.nq = nq;
+    b.q = q;
+    b.npairs = npairs;
+    b.lm = lm;
+    b.rel_tol = rel_tol;
+    b.abs_tol = abs_tol;
+    b.max_regions = max_regions;
+    b.values = values;
+    b.errors = errors;
+    b.regions = regions;
+    b.status = status;
+    return paid_integrate_multi(ctx, &b, 1, workspace, ws_bytes, stream);
+}
+
+}  // extern "C"

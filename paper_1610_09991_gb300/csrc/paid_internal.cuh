@@ -1,0 +1,123 @@
+// Internal declarations shared by the CUDA translation units of libpaid.
+// Device data layout (all structure-of-arrays in the caller's workspace):
+//
+//   per integral g (global index over all batches of a call)
+//     trig[g]   QTrig (cos qx, sin qx, cos qy, sin qy)
+//     meta[g]   uint32  kind | l << 2 | m << 7 | valid << 12 | batch << 16
+//     seg_base[g], seg_count[g]   uint32: the integral's contiguous pool segment
+//   per active slot s (the active list is compacted every round)
+//     active[s] uint32 integral index; cnt_new/cnt_eval/thr written by the
+//     reduce-test kernel and scanned before the split kernel
+//   region pool (ping-pong, capacity C)
+//     key[C] uint64  level << 58 | ix << 29 | iy   (dyadic square of Sec. 3's
+//                    adaptive scheme, side 2pi / 2^level)
+//     val[C] double  Q_2N   err[C] double |Q_N - Q_2N|
+//   eval list  uint2[C] (pool position, integral) of regions awaiting evaluation
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace paid {
+
+constexpr int kMaxLevel = 29;          // deepest dyadic level (29-bit ix, iy)
+constexpr int kMaxRuleN = 6;           // largest supported N of the CC pair
+constexpr int kHistBins = 64;          // error histogram: 4 bins per octave
+constexpr int kScanBlock = 1024;       // items per block of the slot scan
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxMonomialDegree = 30;
+
+enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3 };
+enum Status : int { CONVERGED = 0, BUDGET = 1, NONFINITE = 2, ROUNDCAP = 3, POOL = 4, RUNNING = -1 };
+
+__host__ __device__ inline uint64_t make_key(uint32_t L, uint32_t ix, uint32_t iy)
+{
+    return (uint64_t(L) << 58) | (uint64_t(ix) << 29) | uint64_t(iy);
+}
+__host__ __device__ inline uint32_t key_level(uint64_t k) { return uint32_t(k >> 58); }
+__host__ __device__ inline uint32_t key_ix(uint64_t k) { return uint32_t((k >> 29) & 0x1fffffffu); }
+__host__ __device__ inline uint32_t key_iy(uint64_t k) { return uint32_t(k & 0x1fffffffu); }
+
+__host__ __device__ inline uint32_t make_meta(int kind, int l, int m, int valid, int batch)
+{
+    return uint32_t(kind & 3) | (uint32_t(l & 31) << 2) | (uint32_t(m & 31) << 7) |
+           (uint32_t(valid & 1) << 12) | (uint32_t(batch) << 16);
+}
+__host__ __device__ inline int meta_kind(uint32_t mt) { return int(mt & 3u); }
+__host__ __device__ inline int meta_l(uint32_t mt) { return int((mt >> 2) & 31u); }
+__host__ __device__ inline int meta_m(uint32_t mt) { return int((mt >> 7) & 31u); }
+__host__ __device__ inline int meta_valid(uint32_t mt) { return int((mt >> 12) & 1u); }
+__host__ __device__ inline int meta_batch(uint32_t mt) { return int(mt >> 16); }
+
+// One batch as the kernels see it.
+struct DevBatch {
+    int kind, nq, npairs, pad;
+    double T, inv2T, inv4T;
+    double rel_tol, abs_tol;
+    int64_t max_regions;
+    int64_t first;             // global index of the batch's first integral
+    const double* q;
+    const int32_t* lm;
+    double* values;
+    double* errors;
+    int64_t* regions;
+    int32_t* status;
+};
+
+// cos/sin of the transfer momentum of one integral
+struct __align__(32) QTrig {
+    double cqx, sqx, cqy, sqy;
+};
+
+struct Lattice {
+    double t, tp, mu;
+};
+
+// Totals of one round, written by the slot scan and read by the host.
+struct RoundTotals {
+    unsigned long long pool;    // regions in the next pool
+    unsigned long long eval;    // regions to evaluate next round
+    unsigned long long active;  // integrals still refining
+    unsigned long long pad;
+};
+
+// Pointers into the workspace.
+struct Work {
+    DevBatch* batches;
+    int nb;
+    int64_t n;                 // integrals
+    int64_t cap;               // pool capacity (regions)
+    QTrig* trig;
+    uint32_t* meta;
+    uint32_t* seg_base;
+    uint32_t* seg_count;
+    uint32_t* active[2];
+    uint32_t* cnt_new;         // per slot: regions in the next pool
+    uint32_t* cnt_eval;        // per slot: children to evaluate
+    uint2* thr;                // per slot: (threshold bin, rank cap in that bin)
+    unsigned long long* pre_pool;   // per slot: exclusive prefix within its scan block
+    unsigned long long* pre_eval;
+    uint32_t* pre_act;
+    unsigned long long* blk_pool;   // per scan block: totals, then exclusive offsets
+    unsigned long long* blk_eval;
+    uint32_t* blk_act;
+    RoundTotals* totals;
+    uint64_t* key[2];
+    double* val[2];
+    double* err[2];
+    uint2* evl;
+};
+
+// ---- host-side launch wrappers (defined in the .cu files) -----------------
+// paid_eval.cu
+cudaError_t init_rule_tables(int device);
+cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
+                        Lattice lat, cudaStream_t s);
+// paid_pool.cu
+cudaError_t launch_setup(const Work& w, int L0, int nff, cudaStream_t s);
+cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int round,
+                               int max_rounds, double cover, cudaStream_t s);
+cudaError_t launch_scan(const Work& w, int64_t n_active, cudaStream_t s);
+cudaError_t launch_split(const Work& w, int cur, int64_t n_active, cudaStream_t s);
+cudaError_t launch_finalize(const Work& w, int cur, int64_t n_active, int status, cudaStream_t s);
+
+}  // namespace paid

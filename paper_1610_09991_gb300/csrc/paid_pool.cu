@@ -1,0 +1,427 @@
+// Region pool management: initial partition, per-integral reduction and
+// convergence test, batched selection, 2x2 split and stable compaction.
+//
+// Paper correspondence (Sec. 4, Listings 1-5):
+//   k_setup        Listing 1: every integral starts from the uniform level-L0
+//                  grid of D; its regions go on the eval list.
+//   k_reduce_test  Listing 4 + the master's termination check: per integral,
+//                  V = sum Q_2N, E = sum err over its current regions, and
+//                  the test E <= max(abs_tol, rel_tol |V|).  Finished
+//                  integrals write value/error/regions/status (Listing 5).
+//                  For the others it picks the regions to split: a batched
+//                  extract-max (Listing 2) that takes the largest-error
+//                  regions until their error covers E - cover * tol, using a
+//                  64-bin histogram of err on a quarter-octave scale below
+//                  the segment's maximum, limited by the region budget.
+//   k_scan_*       exclusive prefix sums over the active slots (pool, eval,
+//                  active counts) that place every integral's next segment.
+//   k_split        Listing 3 (divide into 4) + Listing 4 (insert): marked
+//                  regions emit 4 children (level + 1), others are copied;
+//                  positions come from a warp ballot / shuffle prefix so the
+//                  pool stays sorted by integral and stable within it.
+// One warp owns one integral in reduce/split; sums use a fixed lane order and
+// a xor-butterfly, and the histogram sums are integers, so a run is bitwise
+// reproducible.
+#include <cmath>
+
+#include "paid_internal.cuh"
+
+namespace paid {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_max(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(kFull, x, o));
+    return x;
+}
+// exclusive warp prefix of a 32-bit count
+__device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t& total)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    total = __shfl_sync(kFull, inc, 31);
+    return inc - x;
+}
+// quarter-octave log key of a positive double (monotone in the value)
+__device__ __forceinline__ int log_key(double x)
+{
+    return int(uint64_t(__double_as_longlong(x)) >> 50);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_setup(Work w, int L0, int nff)
+{
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= w.n) return;
+    int b = 0;   // batches are sorted by `first`
+    {
+        int lo = 0, hi = w.nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (w.batches[mid].first <= g) lo = mid; else hi = mid - 1;
+        }
+        b = lo;
+    }
+    const DevBatch& B = w.batches[b];
+    const int64_t local = g - B.first;
+    const int64_t iq = local / B.npairs, ip = local % B.npairs;
+    const double qx = B.q[2 * iq], qy = B.q[2 * iq + 1];
+    const int l = B.lm[2 * ip], m = B.lm[2 * ip + 1];
+    int valid;
+    if (B.kind == MONOMIAL)
+        valid = l >= 0 && m >= 0 && l <= kMaxMonomialDegree && m <= kMaxMonomialDegree;
+    else
+        valid = l >= 0 && m >= 0 && l < nff && m < nff;
+    double sx, cx, sy, cy;
+    sincos(qx, &sx, &cx);
+    sincos(qy, &sy, &cy);
+    w.trig[g] = QTrig{cx, sx, cy, sy};
+    w.meta[g] = make_meta(B.kind, valid ? l : 0, valid ? m : 0, valid, b);
+    const uint32_t side = 1u << L0, n0 = side * side;
+    const uint32_t base = uint32_t(g) * n0;
+    w.seg_base[g] = base;
+    w.seg_count[g] = n0;
+    for (uint32_t r = 0; r < n0; ++r) {
+        w.key[0][base + r] = make_key(uint32_t(L0), r / side, r % side);
+        w.evl[base + r] = make_uint2(base + r, uint32_t(g));
+    }
+    w.active[0][g] = uint32_t(g);
+    B.status[local] = RUNNING;
+}
+
+cudaError_t launch_setup(const Work& w, int L0, int nff, cudaStream_t s)
+{
+    if (w.n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (w.n + threads - 1) / threads;
+    k_setup<<<int(blocks), threads, 0, s>>>(w, L0, nff);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-integral reduction, convergence test and split selection.
+// force_status >= 0: finalize every slot that is still refining with that status.
+constexpr int kWarpsPerBlock = 8;
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, double cover,
+              int force_status)
+{
+    __shared__ unsigned long long hsum[kWarpsPerBlock][kHistBins];
+    __shared__ uint32_t hcnt[kWarpsPerBlock][kHistBins];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t s = int64_t(blockIdx.x) * kWarpsPerBlock + wib;
+    if (s >= n_active) return;
+    if (force_status >= 0 && w.cnt_new[s] == 0) return;   // already finished
+    const uint32_t g = w.active[cur][s];
+    const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
+    const uint32_t mt = w.meta[g];
+    const DevBatch B = w.batches[meta_batch(mt)];
+    const double* val = w.val[cur];
+    const double* err = w.err[cur];
+    const uint64_t* key = w.key[cur];
+
+    double sv = 0.0, se = 0.0, mx = 0.0;
+    for (uint32_t j = lane; j < cnt; j += 32) {
+        const double v = val[base + j], e = err[base + j];
+        sv += v;
+        se += e;
+        if (key_level(key[base + j]) < uint32_t(kMaxLevel)) mx = fmax(mx, e);
+    }
+    const double V = warp_sum(sv), E = warp_sum(se), maxE = warp_max(mx);
+    const double tol = fmax(B.abs_tol, B.rel_tol * fabs(V));
+    const int64_t allowed = (B.max_regions - int64_t(cnt)) / 3;
+
+    int st = RUNNING;
+    if (force_status >= 0) st = force_status;
+    else if (!isfinite(V) || !isfinite(E)) st = NONFINITE;
+    else if (E <= tol) st = CONVERGED;
+    else if (round >= max_rounds) st = ROUNDCAP;
+    else if (allowed <= 0 || !(maxE > 0.0)) st = BUDGET;
+
+    if (st != RUNNING) {
+        if (lane == 0) {
+            const int64_t local = int64_t(g) - B.first;
+            B.values[local] = V;
+            B.errors[local] = E;
+            B.regions[local] = cnt;
+            B.status[local] = st;
+            w.cnt_new[s] = 0;
+            w.cnt_eval[s] = 0;
+        }
+        return;
+    }
+
+    // histogram of err in quarter octaves below maxE, sums in units of maxE 2^-40
+    for (int b = lane; b < kHistBins; b += 32) { hsum[wib][b] = 0ull; hcnt[wib][b] = 0u; }
+    __syncwarp();
+    const int kmax = log_key(maxE);
+    const double unit = ldexp(1.0, 40) / maxE;
+    for (uint32_t j = lane; j < cnt; j += 32) {
+        const double e = err[base + j];
+        if (e > 0.0 && key_level(key[base + j]) < uint32_t(kMaxLevel)) {
+            const int bin = min(kHistBins - 1, kmax - log_key(e));
+            atomicAdd(&hsum[wib][bin], (unsigned long long)(e * unit));
+            atomicAdd(&hcnt[wib][bin], 1u);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const double tgt_d = (E - cover * tol) * unit;
+        const unsigned long long target =
+            tgt_d >= 9.0e18 ? ~0ull : (unsigned long long)fmax(tgt_d, 0.0);
+        unsigned long long cum = 0;
+        int64_t marked = 0;
+        int tb = kHistBins - 1;
+        for (int b = 0; b < kHistBins; ++b) {
+            cum += hsum[wib][b];
+            marked += hcnt[wib][b];
+            if (cum >= target) { tb = b; break; }
+        }
+        uint32_t cap;
+        if (marked > allowed) {       // budget binds: whole bins while they fit
+            int64_t acc = 0;
+            int b = 0;
+            while (b < tb && acc + hcnt[wib][b] <= allowed) { acc += hcnt[wib][b]; ++b; }
+            tb = b;
+            cap = uint32_t(allowed - acc);
+            marked = allowed;
+        } else {
+            cap = hcnt[wib][tb];
+        }
+        w.thr[s] = make_uint2(uint32_t(tb) | (uint32_t(kmax) << 8), cap);
+        w.cnt_new[s] = cnt + 3u * uint32_t(marked);
+        w.cnt_eval[s] = 4u * uint32_t(marked);
+    }
+}
+
+cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int round,
+                               int max_rounds, double cover, cudaStream_t s)
+{
+    if (n_active <= 0) return cudaSuccess;
+    const int64_t blocks = (n_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, cur, n_active, round,
+                                                              max_rounds, cover, -1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Work& w, int cur, int64_t n_active, int status, cudaStream_t s)
+{
+    if (n_active <= 0) return cudaSuccess;
+    const int64_t blocks = (n_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, cur, n_active, 0, 0, 0.0,
+                                                              status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of (cnt_new, cnt_eval, cnt_new > 0) over the active slots.
+__global__ void __launch_bounds__(kScanBlock) k_scan_blocks(Work w, int64_t n_active)
+{
+    __shared__ unsigned long long sp[32], se[32];
+    __shared__ uint32_t sa[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t s = int64_t(blockIdx.x) * kScanBlock + threadIdx.x;
+    unsigned long long p = 0, e = 0;
+    uint32_t a = 0;
+    if (s < n_active) {
+        p = w.cnt_new[s];
+        e = w.cnt_eval[s];
+        a = p > 0 ? 1u : 0u;
+    }
+    unsigned long long ip = p, ie = e;
+    uint32_t ia = a;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long yp = __shfl_up_sync(kFull, ip, o);
+        const unsigned long long ye = __shfl_up_sync(kFull, ie, o);
+        const uint32_t ya = __shfl_up_sync(kFull, ia, o);
+        if (lane >= o) { ip += yp; ie += ye; ia += ya; }
+    }
+    if (lane == 31) { sp[wid] = ip; se[wid] = ie; sa[wid] = ia; }
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long xp = sp[lane], xe = se[lane];
+        uint32_t xa = sa[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long yp = __shfl_up_sync(kFull, xp, o);
+            const unsigned long long ye = __shfl_up_sync(kFull, xe, o);
+            const uint32_t ya = __shfl_up_sync(kFull, xa, o);
+            if (lane >= o) { xp += yp; xe += ye; xa += ya; }
+        }
+        sp[lane] = xp; se[lane] = xe; sa[lane] = xa;   // inclusive over warps
+    }
+    __syncthreads();
+    const unsigned long long wp = wid ? sp[wid - 1] : 0ull, we = wid ? se[wid - 1] : 0ull;
+    const uint32_t wa = wid ? sa[wid - 1] : 0u;
+    if (s < n_active) {
+        w.pre_pool[s] = wp + ip - p;
+        w.pre_eval[s] = we + ie - e;
+        w.pre_act[s] = wa + ia - a;
+    }
+    if (threadIdx.x == kScanBlock - 1) {
+        w.blk_pool[blockIdx.x] = sp[31];
+        w.blk_eval[blockIdx.x] = se[31];
+        w.blk_act[blockIdx.x] = sa[31];
+    }
+}
+
+// Single block: exclusive scan of the block totals in place, grand totals out.
+__global__ void __launch_bounds__(kScanBlock) k_scan_top(Work w, int nblk)
+{
+    __shared__ unsigned long long sp[32], se[32];
+    __shared__ unsigned long long sa[32];
+    __shared__ unsigned long long carry[3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) { carry[0] = carry[1] = carry[2] = 0ull; }
+    __syncthreads();
+    for (int c0 = 0; c0 < nblk; c0 += kScanBlock) {
+        const int i = c0 + threadIdx.x;
+        unsigned long long p = 0, e = 0, a = 0;
+        if (i < nblk) { p = w.blk_pool[i]; e = w.blk_eval[i]; a = w.blk_act[i]; }
+        unsigned long long ip = p, ie = e, ia = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long yp = __shfl_up_sync(kFull, ip, o);
+            const unsigned long long ye = __shfl_up_sync(kFull, ie, o);
+            const unsigned long long ya = __shfl_up_sync(kFull, ia, o);
+            if (lane >= o) { ip += yp; ie += ye; ia += ya; }
+        }
+        if (lane == 31) { sp[wid] = ip; se[wid] = ie; sa[wid] = ia; }
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long xp = sp[lane], xe = se[lane], xa = sa[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long yp = __shfl_up_sync(kFull, xp, o);
+                const unsigned long long ye = __shfl_up_sync(kFull, xe, o);
+                const unsigned long long ya = __shfl_up_sync(kFull, xa, o);
+                if (lane >= o) { xp += yp; xe += ye; xa += ya; }
+            }
+            sp[lane] = xp; se[lane] = xe; sa[lane] = xa;
+        }
+        __syncthreads();
+        const unsigned long long wp = wid ? sp[wid - 1] : 0ull, we = wid ? se[wid - 1] : 0ull;
+        const unsigned long long wa = wid ? sa[wid - 1] : 0ull;
+        if (i < nblk) {
+            w.blk_pool[i] = carry[0] + wp + ip - p;
+            w.blk_eval[i] = carry[1] + we + ie - e;
+            w.blk_act[i] = uint32_t(carry[2] + wa + ia - a);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { carry[0] += sp[31]; carry[1] += se[31]; carry[2] += sa[31]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        w.totals->pool = carry[0];
+        w.totals->eval = carry[1];
+        w.totals->active = carry[2];
+    }
+}
+
+cudaError_t launch_scan(const Work& w, int64_t n_active, cudaStream_t s)
+{
+    const int64_t nblk = n_active > 0 ? (n_active + kScanBlock - 1) / kScanBlock : 0;
+    if (nblk > 0) k_scan_blocks<<<int(nblk), kScanBlock, 0, s>>>(w, n_active);
+    k_scan_top<<<1, kScanBlock, 0, s>>>(w, int(nblk));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Split marked regions into 4 children, copy the rest; build the eval list and
+// the next active list.  Reads pool[cur], writes pool[cur ^ 1].
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w, int cur, int64_t n_active)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t s = int64_t(blockIdx.x) * kWarpsPerBlock + wib;
+    if (s >= n_active) return;
+    const uint32_t nnew = w.cnt_new[s];
+    if (nnew == 0) return;
+    const uint32_t g = w.active[cur][s];
+    const int64_t blk = s / kScanBlock;
+    const unsigned long long pbase = w.blk_pool[blk] + w.pre_pool[s];
+    const unsigned long long ebase = w.blk_eval[blk] + w.pre_eval[s];
+    const uint32_t abase = w.blk_act[blk] + w.pre_act[s];
+    const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
+    const uint2 th = w.thr[s];
+    const int tb = int(th.x & 0xffu), kmax = int(th.x >> 8);
+    const uint32_t cap = th.y;
+    const int nxt = cur ^ 1;
+    const uint64_t* key = w.key[cur];
+    const double* val = w.val[cur];
+    const double* err = w.err[cur];
+    uint64_t* key_n = w.key[nxt];
+    double* val_n = w.val[nxt];
+    double* err_n = w.err[nxt];
+    const unsigned lt = (1u << lane) - 1u;
+
+    uint32_t run = 0, erun = 0, tbrun = 0;
+    for (uint32_t c0 = 0; c0 < cnt; c0 += 32) {
+        const uint32_t j = c0 + lane;
+        const bool valid = j < cnt;
+        uint64_t k = 0;
+        double v = 0.0, e = 0.0;
+        int bin = 255;
+        if (valid) {
+            k = key[base + j];
+            v = val[base + j];
+            e = err[base + j];
+            if (e > 0.0 && key_level(k) < uint32_t(kMaxLevel))
+                bin = min(kHistBins - 1, kmax - log_key(e));
+        }
+        const bool in_tb = bin == tb;
+        const unsigned btb = __ballot_sync(kFull, in_tb);
+        const uint32_t rank = tbrun + __popc(btb & lt);
+        tbrun += __popc(btb);
+        const bool mark = valid && (bin < tb || (in_tb && rank < cap));
+        const unsigned bm = __ballot_sync(kFull, mark);
+        uint32_t tot;
+        const uint32_t off = warp_excl(valid ? (mark ? 4u : 1u) : 0u, tot);
+        const unsigned long long p = pbase + run + off;
+        if (valid && !mark) {
+            key_n[p] = k;
+            val_n[p] = v;
+            err_n[p] = e;
+        }
+        if (mark) {
+            const uint32_t L = key_level(k), ix = key_ix(k), iy = key_iy(k);
+            const unsigned long long q = ebase + erun + 4u * __popc(bm & lt);
+#pragma unroll
+            for (uint32_t c = 0; c < 4; ++c) {
+                key_n[p + c] = make_key(L + 1, 2 * ix + (c >> 1), 2 * iy + (c & 1));
+                w.evl[q + c] = make_uint2(uint32_t(p + c), g);
+            }
+        }
+        run += tot;
+        erun += 4u * __popc(bm);
+    }
+    if (lane == 0) {
+        w.seg_base[g] = uint32_t(pbase);
+        w.seg_count[g] = nnew;
+        w.active[nxt][abase] = g;
+    }
+}
+
+cudaError_t launch_split(const Work& w, int cur, int64_t n_active, cudaStream_t s)
+{
+    if (n_active <= 0) return cudaSuccess;
+    const int64_t blocks = (n_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_split<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, cur, n_active);
+    return cudaGetLastError();
+}
+
+}  // namespace paid

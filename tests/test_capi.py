@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point that include/paid.h declares; host-side argument checks
+answer without touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1610_09991_gb300 import build as B
+from paper_1610_09991_gb300 import paid
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return paid.load()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(paid_\w+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"paid_create", "paid_integrate_batch", "paid_integrate_multi"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(paid.EXPORTS) <= names
+
+
+def test_host_side_calls_without_gpu(lib):
+    assert paid.error_string(paid.ERR_POOL) == "region pool full"
+    o = paid.options_default()
+    assert (o.rule_n, o.init_level, o.eval_fp32, o.max_rounds) == (4, 2, 0, 4096)
+    assert lib.paid_options_default(None) == paid.ERR_ARG
+    assert lib.paid_workspace_size(None, 10, 1000, None) == paid.ERR_ARG
+    h = ctypes.c_void_p()
+    # invalid arguments are rejected before any device is touched
+    assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 7, None, 0) == paid.ERR_ARG
+    assert lib.paid_create(ctypes.byref(h), float("nan"), -0.25, -1.0, 9, None, 0) == paid.ERR_ARG
+    bad = paid.options_default()
+    bad.rule_n = 5
+    assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
+    assert lib.paid_integrate_multi(None, None, 0, None, 0, None) == paid.ERR_ARG
+
+
+def test_no_cpu_fallback_without_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        paid.Context()
