@@ -167,6 +167,40 @@ typedef struct {
 int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb,
                          void* workspace, size_t ws_bytes, void* stream);
 
+/* paid_integrate_batch without a workspace argument, for callers that cannot
+ * allocate device memory when they need the integrals: code that runs while
+ * a CUDA graph is being captured, runtimes that fix their device-memory budget
+ * at start-up, or latency-bound loops that must not allocate.  (The paper has
+ * no counterpart; it is a deployment convenience.)
+ *   - The region pool is a 64 MiB array built into the library
+ *     (PAID_STATIC_SCRATCH_BYTES); every GPU that loads the library keeps it
+ *     until the process exits.  The call allocates nothing: no cudaMalloc,
+ *     cudaFree, or host heap.  It does need a context, which paid_create makes
+ *     (and which allocates a small pinned block once, at creation).
+ *   - At most PAID_STATIC_MAX_INTEGRALS = 4096 integrals (nq * npairs) per
+ *     call; more returns PAID_ERR_ARG.  A batch whose refinement outgrows the
+ *     pool returns PAID_ERR_POOL, with status PAID_POOL on the unfinished
+ *     integrals, exactly as paid_integrate_batch does with a small workspace.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) for that device; make that first call before any
+ *     stream capture begins.
+ *   - All calls on a device share the one array and each call leaves its
+ *     contents behind.  Nothing in it has to start cleared (every part is
+ *     written before it is read within a call), but two calls that overlap on
+ *     the GPU -- from two host threads or on two streams -- race on it and
+ *     corrupt each other: run them one after the other.
+ *   - paid_last_error() is not updated by this call (setting the message
+ *     could allocate); the return code and paid_error_string() say what
+ *     failed.  Other arguments, outputs and statuses are as for
+ *     paid_integrate_batch, and the results are the same. */
+#define PAID_STATIC_SCRATCH_BYTES (64u << 20)
+#define PAID_STATIC_MAX_INTEGRALS 4096
+int paid_integrate_batch_static(paid_ctx* ctx, int kind,
+                                int nq, const double* q, int npairs, const int32_t* lm,
+                                double T, double rel_tol, double abs_tol, int64_t max_regions,
+                                double* values, double* errors, int64_t* regions,
+                                int32_t* status, void* stream);
+
 /* Statistics of the last integrate call.  Returns PAID_OK or PAID_ERR_ARG. */
 int paid_last_stats(paid_ctx* ctx, paid_stats* out);
 

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -411,3 +412,181 @@ int paid_integrate_batch(paid_ctx* ctx, int kind, int nq, const double* q, int n
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of paid_integrate_batch.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// integrals: code running while a CUDA graph is being captured, host runtimes
+// that hand out a fixed device-memory budget at start-up and forbid later
+// allocations, or real-time loops where an allocation (and the device-wide
+// synchronisation it can imply) is not acceptable.  Such callers cannot pass
+// a workspace either, because that workspace would itself have to be
+// allocated.  For them the region pool lives in the file-scope array below,
+// which is part of the library's device image: every GPU that loads the
+// library holds it until the process exits.
+//
+// Host code must not use the array's name as an address (on the host it is a
+// stand-in symbol, not device memory); its device address is looked up once
+// per device with cudaGetSymbolAddress and passed to the kernels as their
+// workspace.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB
+constexpr int64_t kStaticMaxIntegrals = 4096;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticScratch {
+    void* ptr[64] = {};
+    bool ready[64] = {};
+};
+StaticScratch g_static;
+std::mutex g_static_mutex;
+
+// Device address of g_static_scratch on `device` (the current device), looked
+// up on the first call for that device.
+cudaError_t static_scratch(int device, void** out)
+{
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static.ready[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static.ptr[device] = p;
+        g_static.ready[device] = true;
+    }
+    *out = g_static.ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, const double* q,
+                                           int npairs, const int32_t* lm, double T,
+                                           double rel_tol, double abs_tol, int64_t max_regions,
+                                           double* values, double* errors, int64_t* regions,
+                                           int32_t* status, void* stream)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    const paid_options& o = ctx->opt;
+    const int64_t n0 = int64_t(1) << (2 * o.init_level);
+    if (kind < PAID_PH || kind > PAID_OVERLAP || nq < 0 || npairs < 0) return PAID_ERR_ARG;
+    const int64_t n = int64_t(nq) * npairs;
+    if (n > kStaticMaxIntegrals) return PAID_ERR_ARG;
+    if (n > 0 && (!q || !lm || !values || !errors || !regions || !status)) return PAID_ERR_ARG;
+    if (!(rel_tol >= 0.0) || !(abs_tol >= 0.0)) return PAID_ERR_ARG;
+    if (max_regions < n0 || max_regions > kMaxRegionsPerIntegral) return PAID_ERR_ARG;
+    ctx->stats = paid_stats{};
+    ctx->stats.n_integrals = n;
+    if (n == 0) return PAID_OK;
+
+    DeviceGuard guard(ctx->device);
+    void* scratch = nullptr;
+    if (static_scratch(ctx->device, &scratch) != cudaSuccess) return PAID_ERR_CUDA;
+    int64_t cap = 0;
+    paid_pool_capacity(ctx, n, kStaticScratchBytes, &cap);
+    if (o.pool_capacity > 0) cap = std::min(cap, o.pool_capacity);
+    if (cap < n * n0) return PAID_ERR_OOM;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Layout L = layout(n, cap);
+    char* base = static_cast<char*>(scratch);
+    Work w{};
+    w.batches = reinterpret_cast<DevBatch*>(base + L.batches);
+    w.nb = 1;
+    w.n = n;
+    w.cap = cap;
+    w.totals = reinterpret_cast<RoundTotals*>(base + L.totals);
+    w.trig = reinterpret_cast<QTrig*>(base + L.trig);
+    w.meta = reinterpret_cast<uint32_t*>(base + L.meta);
+    w.seg_base = reinterpret_cast<uint32_t*>(base + L.seg_base);
+    w.seg_count = reinterpret_cast<uint32_t*>(base + L.seg_count);
+    w.active[0] = reinterpret_cast<uint32_t*>(base + L.active0);
+    w.active[1] = reinterpret_cast<uint32_t*>(base + L.active1);
+    w.cnt_new = reinterpret_cast<uint32_t*>(base + L.cnt_new);
+    w.cnt_eval = reinterpret_cast<uint32_t*>(base + L.cnt_eval);
+    w.thr = reinterpret_cast<uint2*>(base + L.thr);
+    w.pre_pool = reinterpret_cast<unsigned long long*>(base + L.pre_pool);
+    w.pre_eval = reinterpret_cast<unsigned long long*>(base + L.pre_eval);
+    w.pre_act = reinterpret_cast<uint32_t*>(base + L.pre_act);
+    w.blk_pool = reinterpret_cast<unsigned long long*>(base + L.blk_pool);
+    w.blk_eval = reinterpret_cast<unsigned long long*>(base + L.blk_eval);
+    w.blk_act = reinterpret_cast<uint32_t*>(base + L.blk_act);
+    w.key[0] = reinterpret_cast<uint64_t*>(base + L.key0);
+    w.key[1] = reinterpret_cast<uint64_t*>(base + L.key1);
+    w.val[0] = reinterpret_cast<double*>(base + L.val0);
+    w.val[1] = reinterpret_cast<double*>(base + L.val1);
+    w.err[0] = reinterpret_cast<double*>(base + L.err0);
+    w.err[1] = reinterpret_cast<double*>(base + L.err1);
+    w.evl = reinterpret_cast<uint2*>(base + L.evl);
+
+    // The scratch keeps whatever the previous call left in it.  Every array
+    // is written before it is read within a call; the totals block is cleared
+    // all the same so that no count from an earlier call can be seen.
+    if (cudaMemsetAsync(w.totals, 0, sizeof(RoundTotals), s) != cudaSuccess) return PAID_ERR_CUDA;
+    DevBatch d{};
+    d.kind = kind;
+    d.nq = nq;
+    d.npairs = npairs;
+    d.T = T;
+    d.inv2T = 1.0 / (2.0 * T);
+    d.inv4T = 1.0 / (4.0 * T);
+    d.rel_tol = rel_tol;
+    d.abs_tol = abs_tol;
+    d.max_regions = max_regions;
+    d.first = 0;
+    d.q = q;
+    d.lm = lm;
+    d.values = values;
+    d.errors = errors;
+    d.regions = regions;
+    d.status = status;
+    if (cudaMemcpyAsync(w.batches, &d, sizeof(DevBatch), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        launch_setup(w, o.init_level, ctx->nff, s) != cudaSuccess)
+        return PAID_ERR_CUDA;
+
+    paid_stats& st = ctx->stats;
+    st.launches = 1;
+    int64_t n_active = n, n_eval = n * n0, pool = n * n0;
+    int cur = 0;
+    int rc = PAID_OK;
+    for (int round = 0;; ++round) {
+        st.region_evals += n_eval;
+        st.peak_pool = std::max(st.peak_pool, pool);
+        if (launch_eval(w, cur, n_eval, o.rule_n, o.eval_fp32, ctx->lat, s) != cudaSuccess ||
+            launch_reduce_test(w, cur, n_active, round, o.max_rounds, o.cover, s) != cudaSuccess ||
+            launch_scan(w, n_active, s) != cudaSuccess)
+            return PAID_ERR_CUDA;
+        st.eval_launches += n_eval > 0 ? 1 : 0;
+        st.launches += (n_eval > 0 ? 1 : 0) + 3;
+        if (cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return PAID_ERR_CUDA;
+        const RoundTotals t = *ctx->h_totals;
+        st.rounds = round + 1;
+        if (t.active == 0) {
+            if (round >= o.max_rounds) rc = PAID_ERR_TIMEOUT;
+            break;
+        }
+        if (int64_t(t.pool) > cap) {
+            if (launch_finalize(w, cur, n_active, POOL, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return PAID_ERR_CUDA;
+            st.launches += 1;
+            rc = PAID_ERR_POOL;
+            break;
+        }
+        if (launch_split(w, cur, n_active, s) != cudaSuccess) return PAID_ERR_CUDA;
+        st.launches += 1;
+        n_active = int64_t(t.active);
+        n_eval = int64_t(t.eval);
+        pool = int64_t(t.pool);
+        cur ^= 1;
+    }
+    st.node_evals = st.region_evals * (2 * o.rule_n + 1) * (2 * o.rule_n + 1);
+    st.pool_capacity = cap;
+    return rc;
+}

@@ -278,3 +278,36 @@ class Context:
             d2h += sum(x.nbytes for x in hv)
             res.append(Result(*hv))
         return res, h2d, d2h
+
+    def integrate_batch_static(self, kind, q, lm, T, rel_tol=1e-6, abs_tol=1e-10,
+                               max_regions=100000, stream=None) -> Result:
+        """paid_integrate_batch_static: like integrate_batch, but the library
+        keeps the region pool in a fixed 64 MiB device array of its own, so the
+        call needs no workspace (for callers that cannot allocate device
+        memory when they integrate; at most 4096 integrals per call, and calls
+        must not overlap on the GPU because they share that array).  The output
+        tensors here are made by torch before the call; a caller that cannot
+        allocate passes buffers it already holds to the C function."""
+        torch = _torch()
+        lib = self._lib
+        P_, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        lib.paid_integrate_batch_static.argtypes = [P_, I, I, P_, I, P_, D, D, D, I64, P_, P_,
+                                                    P_, P_, P_]
+        dev = self.torch_device
+        nq, npairs = q.shape[0], lm.shape[0]
+        r = Result(torch.empty(nq * npairs, dtype=torch.float64, device=dev),
+                   torch.empty(nq * npairs, dtype=torch.float64, device=dev),
+                   torch.empty(nq * npairs, dtype=torch.int64, device=dev),
+                   torch.empty(nq * npairs, dtype=torch.int32, device=dev))
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        rc = lib.paid_integrate_batch_static(self._h, int(kind), nq, q.data_ptr(), npairs,
+                                             lm.data_ptr(), float(T), float(rel_tol),
+                                             float(abs_tol), int(max_regions),
+                                             r.values.data_ptr(), r.errors.data_ptr(),
+                                             r.regions.data_ptr(), r.status.data_ptr(),
+                                             ctypes.c_void_p(stream.cuda_stream))
+        self.last_rc = rc
+        if rc not in (OK, ERR_TIMEOUT, ERR_POOL):
+            raise PaidError(rc, error_string(rc))
+        return r
