@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
     ap.add_argument("--workload", choices=["flow_step", "first_shell"], default="flow_step")
     ap.add_argument("--eval", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the timed FP64 comparison step of an FP32 run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4096,
@@ -167,7 +169,38 @@ def cpu_baseline(w, sample, seed=1234):
     return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d seeded integrals (seed %d) of the %d-integral batch, all %d host "
                       "threads, %.1f s" % (len(idx), seed, w.n, cores, dt),
-            "seconds": dt, "converged": conv, "regions_mean": float(r.mean())}
+            "seconds": dt, "converged": conv, "regions_mean": float(r.mean())}, (idx, v, s)
+
+
+def accuracy(v, s, vo, so, rel, ab, against, ident=None, lattice=None):
+    """Error statement: |v - v_ref| in units of the requested tolerance
+    max(rel |v_ref|, abs) on integrals both sides converged.  A pair above 2
+    (the parity criterion, plus 1e-12 absolute) is decided by the converged
+    dense-trapezoid value of the integral (the oracle's brute force): it counts
+    as a parity failure only if v is not within 2 tol of that value."""
+    import numpy as np
+    both = (s == 0) & (so == 0)
+    tol = np.maximum(rel * np.abs(vo), ab)
+    r = np.abs(v - vo)[both] / tol[both]
+    over = np.where(both & (np.abs(v - vo) > 2 * tol + 1e-12))[0]
+    fails, decided = 0, []
+    for i in over:
+        if ident is None:
+            fails += 1
+            continue
+        import oracle
+        kind, q, l, m, T = ident(int(i))
+        truth, M = oracle.brute_force(kind, q, l, m, T, lattice)
+        t = max(rel * abs(truth), ab)
+        ok = bool(np.isfinite(truth) and abs(v[i] - truth) <= 2 * t + 1e-12)
+        fails += 0 if ok else 1
+        decided.append({"integral": int(i), "value": float(v[i]), "reference": float(vo[i]),
+                        "brute_force": float(truth), "value_within_2tol_of_brute_force": ok})
+    return {"against": against, "integrals": int(both.sum()),
+            "max_err_over_tol": float(r.max()) if r.size else None,
+            "median_err_over_tol": float(np.median(r)) if r.size else None,
+            "disagreements_decided_by_brute_force": decided,
+            "parity_failures": fails}
 
 
 def run_reference(args):
@@ -217,6 +250,7 @@ def run_paid(args):
     from paper_1610_09991_gb300 import build as B
     B.build()
     from paper_1610_09991_gb300 import paid as P
+    from paper_1610_09991_gb300 import workloads as W
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -255,6 +289,7 @@ def run_paid(args):
     agg = dict(conv=0, budget=0, region_evals=0, node_evals=0, launches=0, eval_launches=0,
                eval_ms=0.0, reduce_ms=0.0, scan_ms=0.0, split_ms=0.0, rounds=0, peak_pool=0)
     ev0.record(stream)
+    outs = None
     for _ in range(args.steps):
         outs = step()
         st = ctx.last_stats()
@@ -321,7 +356,8 @@ def run_paid(args):
         "config": workload_config(w, ff, args.eval),
         "clocks": clk, "roofline": roof, "gpu_launches": agg["launches"],
         "e2e": e2e,
-        "path": "plain batched FP64 GPU cubature (learned proposal not used)",
+        "path": ("plain batched FP64 GPU cubature" if args.eval == "fp64" else
+                 "batched GPU cubature, FP32 integrand / FP64 sums") + " (learned proposal not used)",
         "budget_integrals_per_step": agg["budget"] / args.steps,
         "region_evals_per_s": agg["region_evals"] * world / elapsed,
         "node_evals_per_s": agg["node_evals"] * world / elapsed,
@@ -332,8 +368,41 @@ def run_paid(args):
         "eval_launches": agg["eval_launches"],
         "pipe_peaks": peaks,
     }
+    vals = torch.cat([o.values for o in outs]).cpu().numpy()
+    stats = torch.cat([o.status for o in outs]).cpu().numpy()
+    if args.eval == "fp32" and not args.no_compare:
+        # the plain FP64 GPU path on the same batch, one timed step
+        c64 = P.Context(*w.lattice, ffset=ff, device=local, timing=1)
+        c64.integrate_multi(dbs, stream=stream)        # warm-up (workspace)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o64 = c64.integrate_multi(dbs, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        v64 = torch.cat([o.values for o in o64]).cpu().numpy()
+        s64 = torch.cat([o.status for o in o64]).cpu().numpy()
+        st64 = c64.last_stats()
+        line["plain_fp64"] = {"value": float((s64 == 0).sum()) * world / t64, "unit": UNIT,
+                              "ms_per_step": 1e3 * t64, "region_evals": st64["region_evals"],
+                              "eval_ms": st64["eval_ms"]}
+        line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+        flat = W.flatten(w)
+        ident_all = lambda i: (int(flat["kind"][i]), flat["q"][i], int(flat["lm"][i][0]),
+                               int(flat["lm"][i][1]), float(flat["T"][i]))
+        line["accuracy_vs_fp64_gpu"] = accuracy(vals, stats, v64, s64, w.batches[0].rel_tol,
+                                                w.batches[0].abs_tol, "FP64 GPU path, every integral",
+                                                ident_all, w.lattice)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+        cb, (idx, vo, so) = cpu_baseline(w, args.cpu_sample)
+        line["cpu_baseline"] = cb
+        flat = W.flatten(w)
+        ident_s = lambda i: (int(flat["kind"][idx[i]]), flat["q"][idx[i]], int(flat["lm"][idx[i]][0]),
+                             int(flat["lm"][idx[i]][1]), float(flat["T"][idx[i]]))
+        line["accuracy"] = accuracy(vals[idx], stats[idx], vo, so, w.batches[0].rel_tol,
+                                    w.batches[0].abs_tol, "FP64 oracle, the CPU-baseline sample",
+                                    ident_s, w.lattice)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -104,6 +104,8 @@ typedef struct {
     double reduce_ms;           /* ... region evaluation, reduce + test, */
     double scan_ms;             /* ... slot scan, */
     double split_ms;            /* ... split + compaction (0 without timing) */
+    int64_t escalated;          /* eval_fp32: integrals re-evaluated in FP64 because their
+                                   rounding-noise term exceeded half their tolerance */
 } paid_stats;
 
 /* Fill *opt with the defaults.  Returns PAID_OK or PAID_ERR_ARG (opt NULL). */

@@ -73,6 +73,8 @@ def _load():
                                                    _d, _d, _i64, _i, _i, _p, _p, _p,
                                                    _i64, _p, _p, _p, _p, _p, _p]
             lib.oracle_max_threads.restype = _i
+            lib.oracle_trapezoid.argtypes = [_i, _d, _d, _i, _i, _d, _d, _d, _d, _i, _i]
+            lib.oracle_trapezoid.restype = _d
             _lib = lib
     return _lib
 
@@ -83,6 +85,26 @@ def _ptr(a: np.ndarray):
 
 def max_threads() -> int:
     return int(_load().oracle_max_threads())
+
+
+def trapezoid(kind, q, l, m, T, lat, M, nthreads=0):
+    """The integral on an M x M periodic trapezoid grid (the definition, no adaptivity)."""
+    t, tp, mu = lat
+    return float(_load().oracle_trapezoid(kind, q[0], q[1], l, m, T, t, tp, mu, M, nthreads))
+
+
+def brute_force(kind, q, l, m, T, lat, M0=1024, Mmax=8192, tol=1e-13):
+    """Converged dense trapezoid: M doubled from M0 until two successive values
+    agree within tol (absolute).  Returns (value, M) or (nan, Mmax)."""
+    prev = trapezoid(kind, q, l, m, T, lat, M0)
+    M = M0
+    while M < Mmax:
+        M *= 2
+        cur = trapezoid(kind, q, l, m, T, lat, M)
+        if abs(cur - prev) <= tol:
+            return cur, M
+        prev = cur
+    return float("nan"), M
 
 
 def cc_rule(N: int):

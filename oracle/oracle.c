@@ -463,6 +463,32 @@ int oracle_integrate_trace(int kind, double qx, double qy, int l, int m, double 
     return st;
 }
 
+/* The integral by its definition on a dense periodic grid: the M x M
+ * trapezoid rule over [-pi, pi)^2 (spectrally convergent for these analytic
+ * periodic integrands; converged values are independent of any adaptive
+ * partition).  Used to decide which side is wrong when two adaptive results
+ * disagree beyond their tolerances.  Returns the value (NAN for M < 1). */
+double oracle_trapezoid(int kind, double qx, double qy, int l, int m, double T,
+                        double t, double tp, double mu, int M, int nthreads)
+{
+    if (M < 1) return NAN;
+    orc_integral p = {kind, qx, qy, l, m, T, t, tp, mu};
+    double h = 2.0 * ORC_PI / M;
+    double total = 0.0;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) reduction(+ : total) num_threads(nt)
+#endif
+    for (int i = 0; i < M; ++i) {
+        double row = 0.0;
+        for (int j = 0; j < M; ++j)
+            row += integrand(&p, -ORC_PI + i * h, -ORC_PI + j * h);
+        total += row;
+    }
+    (void)nthreads;
+    return total * h * h;
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

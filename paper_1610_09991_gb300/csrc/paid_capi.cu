@@ -46,7 +46,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t batches, totals, trig, meta, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
         thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
-        err0, err1, evl, end;
+        err0, err1, nse0, nse1, evl, end;
 };
 
 // Byte offsets of every workspace array for n integrals and capacity cap.
@@ -79,9 +79,47 @@ Layout layout(int64_t n, int64_t cap)
     L.val1 = take(8 * cap);
     L.err0 = take(8 * cap);
     L.err1 = take(8 * cap);
+    L.nse0 = take(4 * cap);
+    L.nse1 = take(4 * cap);
     L.evl = take(8 * cap);
     L.end = o;
     return L;
+}
+
+// Typed pointers into a workspace laid out by layout(n, cap).
+Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb)
+{
+    Work w{};
+    w.batches = reinterpret_cast<DevBatch*>(base + L.batches);
+    w.nb = nb;
+    w.n = n;
+    w.cap = cap;
+    w.totals = reinterpret_cast<RoundTotals*>(base + L.totals);
+    w.trig = reinterpret_cast<QTrig*>(base + L.trig);
+    w.meta = reinterpret_cast<uint32_t*>(base + L.meta);
+    w.seg_base = reinterpret_cast<uint32_t*>(base + L.seg_base);
+    w.seg_count = reinterpret_cast<uint32_t*>(base + L.seg_count);
+    w.active[0] = reinterpret_cast<uint32_t*>(base + L.active0);
+    w.active[1] = reinterpret_cast<uint32_t*>(base + L.active1);
+    w.cnt_new = reinterpret_cast<uint32_t*>(base + L.cnt_new);
+    w.cnt_eval = reinterpret_cast<uint32_t*>(base + L.cnt_eval);
+    w.thr = reinterpret_cast<uint2*>(base + L.thr);
+    w.pre_pool = reinterpret_cast<unsigned long long*>(base + L.pre_pool);
+    w.pre_eval = reinterpret_cast<unsigned long long*>(base + L.pre_eval);
+    w.pre_act = reinterpret_cast<uint32_t*>(base + L.pre_act);
+    w.blk_pool = reinterpret_cast<unsigned long long*>(base + L.blk_pool);
+    w.blk_eval = reinterpret_cast<unsigned long long*>(base + L.blk_eval);
+    w.blk_act = reinterpret_cast<uint32_t*>(base + L.blk_act);
+    w.key[0] = reinterpret_cast<uint64_t*>(base + L.key0);
+    w.key[1] = reinterpret_cast<uint64_t*>(base + L.key1);
+    w.val[0] = reinterpret_cast<double*>(base + L.val0);
+    w.val[1] = reinterpret_cast<double*>(base + L.val1);
+    w.err[0] = reinterpret_cast<double*>(base + L.err0);
+    w.err[1] = reinterpret_cast<double*>(base + L.err1);
+    w.nse[0] = reinterpret_cast<float*>(base + L.nse0);
+    w.nse[1] = reinterpret_cast<float*>(base + L.nse1);
+    w.evl = reinterpret_cast<uint2*>(base + L.evl);
+    return w;
 }
 
 int fail(paid_ctx* ctx, int rc, const std::string& msg)
@@ -208,8 +246,8 @@ int paid_pool_capacity(paid_ctx* ctx, int64_t n_integrals, size_t ws_bytes, int6
 {
     if (!ctx || !capacity || n_integrals < 0) return fail(ctx, PAID_ERR_ARG, "bad argument");
     const size_t fixed = layout(n_integrals, 0).end;
-    // 7 arrays of 8 bytes per region plus up to 7 * 256 bytes of alignment
-    int64_t cap = ws_bytes > fixed + 7 * 256 ? int64_t((ws_bytes - fixed - 7 * 256) / 56) : 0;
+    // 64 bytes per region (7 arrays of 8 bytes, 2 of 4) plus up to 9 * 256 bytes of alignment
+    int64_t cap = ws_bytes > fixed + 9 * 256 ? int64_t((ws_bytes - fixed - 9 * 256) / 64) : 0;
     cap = std::min(cap, kMaxCapacity);
     while (cap > 0 && layout(n_integrals, cap).end > ws_bytes) --cap;
     *capacity = cap;
@@ -285,40 +323,13 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Layout L = layout(n, cap);
     char* base = static_cast<char*>(workspace);
-    Work w{};
-    w.batches = reinterpret_cast<DevBatch*>(base + L.batches);
-    w.nb = int(hb.size());
-    w.n = n;
-    w.cap = cap;
-    w.totals = reinterpret_cast<RoundTotals*>(base + L.totals);
-    w.trig = reinterpret_cast<QTrig*>(base + L.trig);
-    w.meta = reinterpret_cast<uint32_t*>(base + L.meta);
-    w.seg_base = reinterpret_cast<uint32_t*>(base + L.seg_base);
-    w.seg_count = reinterpret_cast<uint32_t*>(base + L.seg_count);
-    w.active[0] = reinterpret_cast<uint32_t*>(base + L.active0);
-    w.active[1] = reinterpret_cast<uint32_t*>(base + L.active1);
-    w.cnt_new = reinterpret_cast<uint32_t*>(base + L.cnt_new);
-    w.cnt_eval = reinterpret_cast<uint32_t*>(base + L.cnt_eval);
-    w.thr = reinterpret_cast<uint2*>(base + L.thr);
-    w.pre_pool = reinterpret_cast<unsigned long long*>(base + L.pre_pool);
-    w.pre_eval = reinterpret_cast<unsigned long long*>(base + L.pre_eval);
-    w.pre_act = reinterpret_cast<uint32_t*>(base + L.pre_act);
-    w.blk_pool = reinterpret_cast<unsigned long long*>(base + L.blk_pool);
-    w.blk_eval = reinterpret_cast<unsigned long long*>(base + L.blk_eval);
-    w.blk_act = reinterpret_cast<uint32_t*>(base + L.blk_act);
-    w.key[0] = reinterpret_cast<uint64_t*>(base + L.key0);
-    w.key[1] = reinterpret_cast<uint64_t*>(base + L.key1);
-    w.val[0] = reinterpret_cast<double*>(base + L.val0);
-    w.val[1] = reinterpret_cast<double*>(base + L.val1);
-    w.err[0] = reinterpret_cast<double*>(base + L.err0);
-    w.err[1] = reinterpret_cast<double*>(base + L.err1);
-    w.evl = reinterpret_cast<uint2*>(base + L.evl);
+    Work w = make_work(base, L, n, cap, int(hb.size()));
 
     cudaError_t e;
     if ((e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "batch upload");
-    if ((e = launch_setup(w, o.init_level, ctx->nff, s)) != cudaSuccess)
+    if ((e = launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "setup");
 
     const int nodes = (2 * o.rule_n + 1) * (2 * o.rule_n + 1);
@@ -362,6 +373,7 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
         split_pending = false;
         const RoundTotals t = *ctx->h_totals;
         st.rounds = round + 1;
+        st.escalated = int64_t(t.escalated);
         if (t.active == 0) {
             if (round >= o.max_rounds) rc = fail(ctx, PAID_ERR_TIMEOUT, "round cap reached");
             break;
@@ -493,34 +505,7 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Layout L = layout(n, cap);
     char* base = static_cast<char*>(scratch);
-    Work w{};
-    w.batches = reinterpret_cast<DevBatch*>(base + L.batches);
-    w.nb = 1;
-    w.n = n;
-    w.cap = cap;
-    w.totals = reinterpret_cast<RoundTotals*>(base + L.totals);
-    w.trig = reinterpret_cast<QTrig*>(base + L.trig);
-    w.meta = reinterpret_cast<uint32_t*>(base + L.meta);
-    w.seg_base = reinterpret_cast<uint32_t*>(base + L.seg_base);
-    w.seg_count = reinterpret_cast<uint32_t*>(base + L.seg_count);
-    w.active[0] = reinterpret_cast<uint32_t*>(base + L.active0);
-    w.active[1] = reinterpret_cast<uint32_t*>(base + L.active1);
-    w.cnt_new = reinterpret_cast<uint32_t*>(base + L.cnt_new);
-    w.cnt_eval = reinterpret_cast<uint32_t*>(base + L.cnt_eval);
-    w.thr = reinterpret_cast<uint2*>(base + L.thr);
-    w.pre_pool = reinterpret_cast<unsigned long long*>(base + L.pre_pool);
-    w.pre_eval = reinterpret_cast<unsigned long long*>(base + L.pre_eval);
-    w.pre_act = reinterpret_cast<uint32_t*>(base + L.pre_act);
-    w.blk_pool = reinterpret_cast<unsigned long long*>(base + L.blk_pool);
-    w.blk_eval = reinterpret_cast<unsigned long long*>(base + L.blk_eval);
-    w.blk_act = reinterpret_cast<uint32_t*>(base + L.blk_act);
-    w.key[0] = reinterpret_cast<uint64_t*>(base + L.key0);
-    w.key[1] = reinterpret_cast<uint64_t*>(base + L.key1);
-    w.val[0] = reinterpret_cast<double*>(base + L.val0);
-    w.val[1] = reinterpret_cast<double*>(base + L.val1);
-    w.err[0] = reinterpret_cast<double*>(base + L.err0);
-    w.err[1] = reinterpret_cast<double*>(base + L.err1);
-    w.evl = reinterpret_cast<uint2*>(base + L.evl);
+    Work w = make_work(base, L, n, cap, 1);
 
     // The scratch keeps whatever the previous call left in it.  Every array
     // is written before it is read within a call; the totals block is cleared
@@ -544,7 +529,7 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     d.regions = regions;
     d.status = status;
     if (cudaMemcpyAsync(w.batches, &d, sizeof(DevBatch), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        launch_setup(w, o.init_level, ctx->nff, s) != cudaSuccess)
+        launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s) != cudaSuccess)
         return PAID_ERR_CUDA;
 
     paid_stats& st = ctx->stats;
@@ -567,6 +552,7 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
             return PAID_ERR_CUDA;
         const RoundTotals t = *ctx->h_totals;
         st.rounds = round + 1;
+        st.escalated = int64_t(t.escalated);
         if (t.active == 0) {
             if (round >= o.max_rounds) rc = PAID_ERR_TIMEOUT;
             break;

@@ -36,6 +36,12 @@ __constant__ double c_t[2][2 * kMaxRuleN + 1];    // fine nodes t_i = cos(i pi /
 __constant__ double c_co[2][kMaxLevel + 1][kMaxRuleN + 1];  // cos(pi 2^-L t_i), i <= N
 __constant__ double c_so[2][kMaxLevel + 1][kMaxRuleN + 1];  // sin(pi 2^-L t_i)
 __constant__ double c_ff[9][3][3];                // f_n = sum_ab C[a][b] X_a Y_b
+__constant__ float c_wf32[2][2 * kMaxRuleN + 1];  // FP32 copies for the FP32 path
+__constant__ float2 c_wfdf[2][2 * kMaxRuleN + 1]; // (hi, lo) pairs for the float-float path
+__constant__ float2 c_wcdf[2][kMaxRuleN + 1];
+__constant__ float2 c_exp2tab[64];                // 2^(j/64) as (hi, lo), j = 0..63
+__constant__ float c_wc32[2][kMaxRuleN + 1];
+__constant__ float c_ff32[9][3][3];
 
 // Clenshaw-Curtis weights for n intervals (n even), from the cosine-series
 // form of the rule: w_j = (c_j / n) (1 - sum_{k=1}^{n/2} b_k cos(2 k j pi/n)/(4k^2 - 1)).
@@ -83,7 +89,28 @@ cudaError_t init_rule_tables(int device)
     ff[6][2][2] = 2.0;                      // 2 sx sy
     ff[7][2][1] = 2.0;                      // 2 sx cy
     ff[8][1][2] = 2.0;                      // 2 cx sy
+    float wf32[2][2 * kMaxRuleN + 1], wc32[2][kMaxRuleN + 1], ff32[9][3][3];
+    for (int v = 0; v < 2; ++v) {
+        for (int i = 0; i < 2 * kMaxRuleN + 1; ++i) wf32[v][i] = float(wf[v][i]);
+        for (int i = 0; i < kMaxRuleN + 1; ++i) wc32[v][i] = float(wc[v][i]);
+    }
+    for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) ff32[a][b][c] = float(ff[a][b][c]);
+    float2 wfdf[2][2 * kMaxRuleN + 1], wcdf[2][kMaxRuleN + 1], e2t[64];
+    auto split = [](double x) { float hi = float(x); return make_float2(hi, float(x - double(hi))); };
+    for (int v = 0; v < 2; ++v) {
+        for (int i = 0; i < 2 * kMaxRuleN + 1; ++i) wfdf[v][i] = split(wf[v][i]);
+        for (int i = 0; i < kMaxRuleN + 1; ++i) wcdf[v][i] = split(wc[v][i]);
+    }
+    for (int j = 0; j < 64; ++j) e2t[j] = split(std::exp2(j / 64.0));
     cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(c_wfdf, wfdf, sizeof(wfdf))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_wcdf, wcdf, sizeof(wcdf))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_exp2tab, e2t, sizeof(e2t))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_wf32, wf32, sizeof(wf32))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_wc32, wc32, sizeof(wc32))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_ff32, ff32, sizeof(ff32))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_wf, wf, sizeof(wf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_wc, wc, sizeof(wc))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_t, t, sizeof(t))) != cudaSuccess) return e;
@@ -222,6 +249,428 @@ __device__ __forceinline__ void region_monomial(int v, uint32_t L, uint32_t ix, 
     s1 = cxs * cys;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 evaluation (mixed precision).  What stays FP64: the region centre and
+// node rotations, the reduced energies x = e/2T (1 DFMA each: the 1/2T factor
+// is folded into the per-row coefficients) and their exact difference
+// d = x1 - x2, because near the Fermi surface e is a small difference of O(1)
+// terms and an FP32 energy would move x by ~1e-6 at T = 0.05; the region sums
+// Q_N, Q_2N, their difference and all totals.  What runs in FP32: the
+// kernel F from x1, x2, d (2 MUFU ex2 + one fast division per node), the form
+// factors, and the sums of a row of nodes.
+//
+// Rounding noise.  Each node's FP32 value g = f_l f_m F carries independent
+// rounding errors; their standard deviation, in units of 2^-24, is bounded by
+//   s = kNoiseUlps |f_l f_m F|                 (ex2, products, division)
+//     + 4 |F| (|f_l| + |f_m|)                   (form factors: sums of O(1) terms)
+//     + |f_l f_m| dF                            (rounding x1, x2 to FP32)
+// with dF = |F| (|x1| + |x2|) on the sinhc branch and
+// dF = (sech^2 x1 |x1| + sech^2 x2 |x2|) / (2 |e1 - e2|) on the tanh branch
+// (|dF/dx_i| |x_i| 2^-24 for F = (tanh x1 - tanh x2) / (2 (e1 - e2))).
+// A region returns the rms noise of Q_N - Q_2N,
+//   nse = 2^-24 (h/2)^2/(2pi)^2 sqrt(sum_ij (w_i w_j s_ij)^2 + sum_coarse (v_i v_j s_ij)^2),
+// (w fine, v coarse weights).  The noise stays inside |Q_N - Q_2N| (it only
+// makes the error estimate larger); an integral whose summed noise
+// kNoiseSigmas * sum(nse) exceeds a quarter of its tolerance -- which no
+// refinement can fix, since the sum does not shrink as regions split -- is
+// re-evaluated at higher precision.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// F(x1, x2) with x = e/2T, d = x1 - x2 (exact), twoT = 2T, inv4T = 1/4T, in FP32,
+// and dF, the sensitivity of F to rounding x1, x2 (see the noise model above).
+// |d| <= 1: (1/4T) sinhc(d) sech x1 sech x2 (series of sinhc to d^10);
+// |d| > 1:  the same-sign / opposite-sign forms of the FP64 kernel.
+__device__ __forceinline__ float bubble_F32(float x1, float x2, float d, float twoT, float inv4T,
+                                            float& dF)
+{
+    const float L2E = 1.4426950408889634f;
+    const float a1 = fabsf(x1), a2 = fabsf(x2);
+    const float v1 = ex2_approx(-a1 * L2E), v2 = ex2_approx(-a2 * L2E);
+    const float u1 = v1 * v1, u2 = v2 * v2;
+    const float p1 = 1.0f + u1, p2 = 1.0f + u2;
+    const float p = p1 * p2;
+    const bool near = fabsf(d) <= 1.0f;
+    const bool neg1 = x1 < 0.0f;
+    const bool same = neg1 == (x2 < 0.0f);
+    float far = same ? (u2 - u1) : fmaf(-u1, u2, 1.0f);
+    far = neg1 ? -far : far;
+    const float d2 = d * d;
+    float sh = fmaf(d2, 1.0f / 39916800.0f, 1.0f / 362880.0f);
+    sh = fmaf(d2, sh, 1.0f / 5040.0f);
+    sh = fmaf(d2, sh, 1.0f / 120.0f);
+    sh = fmaf(d2, sh, 1.0f / 6.0f);
+    sh = fmaf(d2, sh, 1.0f);
+    const float nearv = (4.0f * inv4T) * (v1 * v2) * sh;
+    const float num = near ? nearv : far;
+    const float ediff = twoT * d;   // e1 - e2
+    const float den = near ? p : p * ediff;
+    const float F = __fdividef(num, den);
+    // sech^2 x = 4u / (1+u)^2
+    const float s1 = __fdividef(4.0f * u1, p1 * p1), s2 = __fdividef(4.0f * u2, p2 * p2);
+    dF = near ? fabsf(F) * (a1 + a2) : __fdividef(fmaf(s1, a1, s2 * a2), 2.0f * fabsf(ediff));
+    return F;
+}
+
+template <int N, int KIND>
+__device__ __forceinline__ void region_trig_fp32(int v, uint32_t L, uint32_t ix, uint32_t iy,
+                                                 QTrig tq, int l, int m, const DevBatch& B,
+                                                 Lattice lat, double& s2, double& s1, float& nz)
+{
+    constexpr int NF = 2 * N + 1;
+    const double inv2T = B.inv2T;
+    const float twoT = float(2.0 * B.T), inv4T = float(B.inv4T);
+    double sxc, cxc, syc, cyc;
+    sincospi(fma(double(2 * ix + 1), ldexp(1.0, -int(L)), -1.0), &sxc, &cxc);
+    sincospi(fma(double(2 * iy + 1), ldexp(1.0, -int(L)), -1.0), &syc, &cyc);
+
+    double cyd[NF], cy2d[NF];
+    float cyf[NF], syf[NF], cy2f[NF], sy2f[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        const int jj = j <= N ? j : 2 * N - j;
+        const double co = c_co[v][L][jj];
+        const double so = j <= N ? c_so[v][L][jj] : -c_so[v][L][jj];
+        const double c = fma(cyc, co, -syc * so);
+        const double sn = fma(syc, co, cyc * so);
+        double c2, s2_;
+        if (KIND == PP) { c2 = fma(tq.cqy, c, tq.sqy * sn); s2_ = fma(tq.sqy, c, -tq.cqy * sn); }
+        else            { c2 = fma(c, tq.cqy, -sn * tq.sqy); s2_ = fma(sn, tq.cqy, c * tq.sqy); }
+        cyd[j] = c;
+        cy2d[j] = c2;
+        cyf[j] = float(c);
+        syf[j] = float(sn);
+        cy2f[j] = float(c2);
+        sy2f[j] = float(s2_);
+    }
+    float Cl[3][3], Cm[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) { Cl[a][b] = c_ff32[l][a][b]; Cm[a][b] = c_ff32[m][a][b]; }
+
+    // x = e / 2T = A(kx) + B(kx) cos ky with A = (-2t cx - mu)/2T, B = (-2t - 4t' cx)/2T
+    const double tA = -2.0 * lat.t * inv2T, tB = -4.0 * lat.tp * inv2T, mu = lat.mu * inv2T;
+    double fine = 0.0, coarse = 0.0;
+    float noise = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < NF; ++i) {
+        const int ii = i <= N ? i : 2 * N - i;
+        const double co = c_co[v][L][ii];
+        const double so = i <= N ? c_so[v][L][ii] : -c_so[v][L][ii];
+        const double cx = fma(cxc, co, -sxc * so);
+        const double sx = fma(sxc, co, cxc * so);
+        double cx2, sx2;
+        if (KIND == PP) { cx2 = fma(tq.cqx, cx, tq.sqx * sx); sx2 = fma(tq.sqx, cx, -tq.cqx * sx); }
+        else            { cx2 = fma(cx, tq.cqx, -sx * tq.sqx); sx2 = fma(sx, tq.cqx, cx * tq.sqx); }
+        const double A1 = fma(tA, cx, -mu), B1 = fma(tB, cx, tA);
+        const double A2 = fma(tA, cx2, -mu), B2 = fma(tB, cx2, tA);
+        const float cxf = float(cx), sxf = float(sx), cx2f = float(cx2), sx2f = float(sx2);
+        float ul[3], um[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ul[b] = fmaf(Cl[2][b], sxf, fmaf(Cl[1][b], cxf, Cl[0][b]));
+            um[b] = fmaf(Cm[2][b], sx2f, fmaf(Cm[1][b], cx2f, Cm[0][b]));
+        }
+        float rf = 0.0f, rc = 0.0f, rnf = 0.0f, rnc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            const double x1 = fma(B1, cyd[j], A1);
+            double x2 = fma(B2, cy2d[j], A2);
+            if (KIND == PP) x2 = -x2;
+            float dF;
+            const float F = bubble_F32(float(x1), float(x2), float(x1 - x2), twoT, inv4T, dF);
+            const float fl = fmaf(ul[2], syf[j], fmaf(ul[1], cyf[j], ul[0]));
+            const float fm = fmaf(um[2], sy2f[j], fmaf(um[1], cy2f[j], um[0]));
+            const float flm = fl * fm;
+            const float g = flm * F;
+            rf = fmaf(c_wf32[v][j], g, rf);
+            if ((j & 1) == 0) rc = fmaf(c_wc32[v][j >> 1], g, rc);
+            const float sg = fmaf(fabsf(flm), fmaf(kNoiseUlps, fabsf(F), dF),
+                                  4.0f * fabsf(F) * (fabsf(fl) + fabsf(fm)));
+            const float sf = c_wf32[v][j] * sg;
+            rnf = fmaf(sf, sf, rnf);
+            if ((j & 1) == 0) { const float sc = c_wc32[v][j >> 1] * sg; rnc = fmaf(sc, sc, rnc); }
+        }
+        fine = fma(c_wf[v][i], double(rf), fine);
+        if ((i & 1) == 0) {
+            coarse = fma(c_wc[v][i >> 1], double(rc), coarse);
+            noise = fmaf(c_wc32[v][i >> 1] * c_wc32[v][i >> 1], rnc, noise);
+        }
+        noise = fmaf(c_wf32[v][i] * c_wf32[v][i], rnf, noise);
+    }
+    s2 = fine;
+    s1 = coarse;
+    nz = noise;
+}
+
+// ---------------------------------------------------------------------------
+// Float-float ("df32") evaluation: every quantity is an unevaluated sum
+// hi + lo of two FP32 numbers (about 48 significant bits), so the whole
+// integrand runs on the FP32 pipe -- 64x the FP64 pipe on this GPU -- at
+// close to FP64 accuracy.  Integrals whose FP32 rounding noise is too large
+// for their tolerance (those that vanish by symmetry, mostly) are evaluated
+// this way.  Building blocks, written from the published error-free
+// transformations: Knuth's TwoSum, the FMA form of Dekker's TwoProduct, and
+// the double-word add / multiply / divide of Hida, Li and Bailey's
+// double-double arithmetic transposed to FP32 pairs.  Additions use the
+// "sloppy" form (absolute error ~2^-48 of the operands), which is enough
+// here: every sum is either of O(1) bounded terms or bounded away from
+// cancellation (|d| > 1/8 on the tanh branch).
+struct f2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ f2 df_add(f2 a, f2 b)
+{
+    f2 s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ f2 df_add_f(f2 a, float b)
+{
+    f2 s = two_sum(a.hi, b);
+    s.lo += a.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ f2 df_neg(f2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ f2 df_mul(f2 a, f2 b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2 df_mul_f(f2 a, float b)
+{
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// a / b: a first quotient from the approximate reciprocal, one correction
+// from the exact residual a - q1 b.
+__device__ __forceinline__ f2 df_div(f2 a, f2 b)
+{
+    const float r = rcp_approx(b.hi);
+    const float q1 = a.hi * r;
+    const f2 res = df_add(a, df_neg(df_mul_f(b, q1)));
+    const float q2 = res.hi * r;
+    return fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ f2 df_from(double x)
+{
+    const float hi = float(x);
+    return {hi, float(x - double(hi))};
+}
+__device__ __forceinline__ f2 df_c(float2 c) { return {c.x, c.y}; }
+
+// exp(-a), a >= 0, in float-float (Tang's table-driven method): k = rint(64 a / ln 2),
+// r = a - k ln2/64 with ln2/64 split in three parts so that k * C1 is exact
+// (k < 2^14, C1 has 10 significant bits), e^-a = 2^(-k/64) e^-r with the
+// table 2^(j/64) and a degree-5 Taylor polynomial of e^-r on |r| <= ln2/128
+// (truncation below 4e-17).  Results below 2^-126 are flushed to zero.
+__device__ __forceinline__ f2 df_exp_neg(f2 a, const float2* tab)
+{
+    if (a.hi > 87.0f) return {0.0f, 0.0f};
+    const float C1 = 0.010833740234375f;          // 0x1.63p-7
+    const float C2 = -3.3155381515825866e-06f;
+    const float C3 = 2.572804640231345e-14f;
+    const float k = rintf(a.hi * 92.33248138427734f);
+    const float t1 = fmaf(-k, C1, a.hi);          // exact (Sterbenz)
+    f2 r = two_sum(t1, a.lo);
+    const f2 kc2 = {k * C2, fmaf(k, C2, -k * C2)};
+    r = df_add(r, df_neg(kc2));
+    r = df_add_f(r, -k * C3);
+    const f2 t = df_neg(r);                       // e^-a = 2^(-k/64) e^t
+    float p = fmaf(t.hi, 1.0f / 120.0f, 1.0f / 24.0f);
+    p = fmaf(t.hi, p, 1.0f / 6.0f);               // 1/6 + t/24 + t^2/120
+    f2 P = df_add_f(df_mul_f(t, p), 0.5f);
+    P = df_add_f(df_mul(t, P), 1.0f);
+    P = df_add_f(df_mul(t, P), 1.0f);
+    const int n = -int(k);
+    const int m = n >> 6;                         // floor(n / 64)
+    const int j = n & 63;
+    f2 res = df_mul(P, df_c(tab[j]));
+    if (m < -125) return {0.0f, 0.0f};
+    const float sc = __int_as_float((m + 127) << 23);
+    res.hi *= sc;
+    res.lo *= sc;
+    return res;
+}
+
+// F(x1, x2) = [tanh x1 - tanh x2] / (2 (e1 - e2)) in float-float, x = e / 2T,
+// d = x1 - x2; |d| <= 1/8: (1/4T) sinhc(d) sech x1 sech x2; else the
+// same-sign / opposite-sign forms of the FP64 kernel.
+__device__ __forceinline__ f2 bubble_Fdf(f2 x1, f2 x2, f2 d, f2 twoT, f2 inv4T,
+                                         const float2* tab)
+{
+    const bool neg1 = x1.hi < 0.0f, neg2 = x2.hi < 0.0f;
+    const f2 a1 = neg1 ? df_neg(x1) : x1, a2 = neg2 ? df_neg(x2) : x2;
+    const f2 v1 = df_exp_neg(a1, tab), v2 = df_exp_neg(a2, tab);
+    const f2 u1 = df_mul(v1, v1), u2 = df_mul(v2, v2);
+    const f2 p = df_mul(df_add_f(u1, 1.0f), df_add_f(u2, 1.0f));
+    f2 num, den;
+    if (fabsf(d.hi) <= 0.125f) {
+        // sinhc(d) = 1 + d^2/6 + d^4/120 + d^6/5040 + d^8/362880 (+ < 3e-17 at |d| = 1/8)
+        const f2 d2 = df_mul(d, d);
+        const float q = fmaf(d2.hi, fmaf(d2.hi, 1.0f / 362880.0f, 1.0f / 5040.0f), 1.0f / 120.0f);
+        f2 S = df_add(df_mul_f(d2, q), f2{0.1666666716337204f, -4.967053879312289e-09f});
+        S = df_add_f(df_mul(d2, S), 1.0f);
+        num = df_mul(df_mul(df_mul_f(inv4T, 4.0f), df_mul(v1, v2)), S);
+        den = p;
+    } else {
+        num = (neg1 == neg2) ? df_add(u2, df_neg(u1)) : df_add_f(df_neg(df_mul(u1, u2)), 1.0f);
+        if (neg1) num = df_neg(num);
+        den = df_mul(p, df_mul(d, twoT));   // (e1 - e2) = 2T d
+    }
+    return df_div(num, den);
+}
+
+template <int N, int KIND>
+__device__ __forceinline__ void region_trig_df(int v, uint32_t L, uint32_t ix, uint32_t iy,
+                                               QTrig tq, int l, int m, const DevBatch& B,
+                                               Lattice lat, const float2* tab, double& s2,
+                                               double& s1)
+{
+    constexpr int NF = 2 * N + 1;
+    const double inv2T = B.inv2T;
+    const f2 twoT = df_from(2.0 * B.T);
+    const f2 inv4T = df_from(B.inv4T);
+    double sxc, cxc, syc, cyc;
+    sincospi(fma(double(2 * ix + 1), ldexp(1.0, -int(L)), -1.0), &sxc, &cxc);
+    sincospi(fma(double(2 * iy + 1), ldexp(1.0, -int(L)), -1.0), &syc, &cyc);
+
+    f2 cy[NF], sy[NF], cy2[NF], sy2[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        const int jj = j <= N ? j : 2 * N - j;
+        const double co = c_co[v][L][jj];
+        const double so = j <= N ? c_so[v][L][jj] : -c_so[v][L][jj];
+        const double c = fma(cyc, co, -syc * so);
+        const double sn = fma(syc, co, cyc * so);
+        double c2, s2_;
+        if (KIND == PP) { c2 = fma(tq.cqy, c, tq.sqy * sn); s2_ = fma(tq.sqy, c, -tq.cqy * sn); }
+        else            { c2 = fma(c, tq.cqy, -sn * tq.sqy); s2_ = fma(sn, tq.cqy, c * tq.sqy); }
+        cy[j] = df_from(c);
+        sy[j] = df_from(sn);
+        cy2[j] = df_from(c2);
+        sy2[j] = df_from(s2_);
+    }
+    const double tA = -2.0 * lat.t * inv2T, tB = -4.0 * lat.tp * inv2T, mu = lat.mu * inv2T;
+    double fine = 0.0, coarse = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < NF; ++i) {
+        const int ii = i <= N ? i : 2 * N - i;
+        const double co = c_co[v][L][ii];
+        const double so = i <= N ? c_so[v][L][ii] : -c_so[v][L][ii];
+        const double cx = fma(cxc, co, -sxc * so);
+        const double sx = fma(sxc, co, cxc * so);
+        double cx2, sx2;
+        if (KIND == PP) { cx2 = fma(tq.cqx, cx, tq.sqx * sx); sx2 = fma(tq.sqx, cx, -tq.cqx * sx); }
+        else            { cx2 = fma(cx, tq.cqx, -sx * tq.sqx); sx2 = fma(sx, tq.cqx, cx * tq.sqx); }
+        const f2 A1 = df_from(fma(tA, cx, -mu)), B1 = df_from(fma(tB, cx, tA));
+        const f2 A2 = df_from(fma(tA, cx2, -mu)), B2 = df_from(fma(tB, cx2, tA));
+        f2 ul[3], um[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ul[b] = df_from(fma(c_ff[l][2][b], sx, fma(c_ff[l][1][b], cx, c_ff[l][0][b])));
+            um[b] = df_from(fma(c_ff[m][2][b], sx2, fma(c_ff[m][1][b], cx2, c_ff[m][0][b])));
+        }
+        f2 rf = {0.0f, 0.0f}, rc = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            const f2 x1 = df_add(df_mul(B1, cy[j]), A1);
+            f2 x2 = df_add(df_mul(B2, cy2[j]), A2);
+            if (KIND == PP) x2 = df_neg(x2);
+            const f2 F = bubble_Fdf(x1, x2, df_add(x1, df_neg(x2)), twoT, inv4T, tab);
+            const f2 fl = df_add(df_add(df_mul(ul[1], cy[j]), df_mul(ul[2], sy[j])), ul[0]);
+            const f2 fm = df_add(df_add(df_mul(um[1], cy2[j]), df_mul(um[2], sy2[j])), um[0]);
+            const f2 g = df_mul(df_mul(fl, fm), F);
+            rf = df_add(rf, df_mul(df_c(c_wfdf[v][j]), g));
+            if ((j & 1) == 0) rc = df_add(rc, df_mul(df_c(c_wcdf[v][j >> 1]), g));
+        }
+        fine = fma(c_wf[v][i], double(rf.hi) + double(rf.lo), fine);
+        if ((i & 1) == 0) coarse = fma(c_wc[v][i >> 1], double(rc.hi) + double(rc.lo), coarse);
+    }
+    s2 = fine;
+    s1 = coarse;
+}
+
+// Mixed-precision evaluation: PH / PP regions use the FP32 path, or the
+// float-float path once their integral has been escalated; integrals set to
+// FP64 and the test kinds use the FP64 path.
+template <int N>
+__global__ void __launch_bounds__(128) k_eval_fp32(Work w, int cur, int64_t n_eval, Lattice lat)
+{
+    const int v = N == 4 ? 0 : 1;
+    __shared__ float2 tab[64];
+    if (threadIdx.x < 64) tab[threadIdx.x] = c_exp2tab[threadIdx.x];
+    __syncthreads();
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_eval; t += stride) {
+        const uint2 e = w.evl[t];
+        const uint32_t pos = e.x, g = e.y;
+        const uint64_t key = w.key[cur][pos];
+        const uint32_t mt = w.meta[g];
+        const DevBatch& B = w.batches[meta_batch(mt)];
+        const uint32_t L = key_level(key), ix = key_ix(key), iy = key_iy(key);
+        const int kind = meta_kind(mt);
+        double s2 = NAN, s1 = NAN;
+        float nz = 0.0f;
+        if (meta_valid(mt)) {
+            const QTrig tq = w.trig[g];
+            const int l = meta_l(mt), m = meta_m(mt);
+            const bool fp64 = (mt & kMetaFp64) != 0u;
+            const bool dfp = (mt & kMetaDf32) != 0u;
+            if (kind == PH && !fp64 && dfp)
+                region_trig_df<N, PH>(v, L, ix, iy, tq, l, m, B, lat, tab, s2, s1);
+            else if (kind == PP && !fp64 && dfp)
+                region_trig_df<N, PP>(v, L, ix, iy, tq, l, m, B, lat, tab, s2, s1);
+            else if (kind == PH && !fp64)
+                region_trig_fp32<N, PH>(v, L, ix, iy, tq, l, m, B, lat, s2, s1, nz);
+            else if (kind == PP && !fp64)
+                region_trig_fp32<N, PP>(v, L, ix, iy, tq, l, m, B, lat, s2, s1, nz);
+            else if (kind == PH)
+                region_trig_fp64<N, PH>(v, L, ix, iy, tq, l, m, B, lat, s2, s1);
+            else if (kind == PP)
+                region_trig_fp64<N, PP>(v, L, ix, iy, tq, l, m, B, lat, s2, s1);
+            else if (kind == OVERLAP)
+                region_trig_fp64<N, OVERLAP>(v, L, ix, iy, tq, l, m, B, lat, s2, s1);
+            else
+                region_monomial<N>(v, L, ix, iy, l, m, s2, s1);
+        }
+        const double scale = ldexp(0.25, -2 * int(L));
+        const double q2 = s2 * scale, q1 = s1 * scale;
+        w.val[cur][pos] = q2;
+        w.err[cur][pos] = fabs(q1 - q2);
+        // nz = sum (w_i w_j s_ij)^2: rms noise 2^-24 scale sqrt(nz)
+        w.nse[cur][pos] = float(sqrt(double(nz)) * scale * 5.9604644775390625e-8);
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(128) k_eval_fp64(Work w, int cur, int64_t n_eval, Lattice lat)
 {
@@ -253,21 +702,24 @@ __global__ void __launch_bounds__(128) k_eval_fp64(Work w, int cur, int64_t n_ev
         const double q2 = s2 * scale, q1 = s1 * scale;
         w.val[cur][pos] = q2;
         w.err[cur][pos] = fabs(q1 - q2);
+        w.nse[cur][pos] = 0.0f;
     }
 }
 
 cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
                         Lattice lat, cudaStream_t s)
 {
-    (void)fp32;
     if (n_eval <= 0) return cudaSuccess;
     const int threads = 128;
     int64_t blocks = (n_eval + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    if (rule_n == 4)
-        k_eval_fp64<4><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
-    else
-        k_eval_fp64<6><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+    if (fp32) {
+        if (rule_n == 4) k_eval_fp32<4><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+        else             k_eval_fp32<6><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+    } else {
+        if (rule_n == 4) k_eval_fp64<4><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+        else             k_eval_fp64<6><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+    }
     return cudaGetLastError();
 }
 

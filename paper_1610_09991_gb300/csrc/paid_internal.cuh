@@ -12,6 +12,8 @@
 //     key[C] uint64  level << 58 | ix << 29 | iy   (dyadic square of Sec. 3's
 //                    adaptive scheme, side 2pi / 2^level)
 //     val[C] double  Q_2N   err[C] double |Q_N - Q_2N|
+//     nse[C] float   bound on the FP32 rounding noise of the region's sums
+//                    (0 for regions evaluated in FP64)
 //   eval list  uint2[C] (pool position, integral) of regions awaiting evaluation
 #pragma once
 #include <cstdint>
@@ -25,6 +27,13 @@ constexpr int kHistBins = 64;          // error histogram: 4 bins per octave
 constexpr int kScanBlock = 1024;       // items per block of the slot scan
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxMonomialDegree = 30;
+// FP32 evaluation: per-node rounding error in units of 2^-24 |F| (|f_l|+1)(|f_m|+1)
+// (plus |x1| + |x2| for the rounding of the energies), and the multiple of the
+// rms noise treated as irreducible by refinement; see paid_eval.cu.
+constexpr float kNoiseUlps = 4.0f;
+constexpr double kNoiseSigmas = 3.0;
+// threshold-bin marker in thr[].x: re-evaluate every region in FP64
+constexpr uint32_t kEscalate = 0xfeu;
 
 enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3 };
 enum Status : int { CONVERGED = 0, BUDGET = 1, NONFINITE = 2, ROUNDCAP = 3, POOL = 4, RUNNING = -1 };
@@ -42,6 +51,12 @@ __host__ __device__ inline uint32_t make_meta(int kind, int l, int m, int valid,
     return uint32_t(kind & 3) | (uint32_t(l & 31) << 2) | (uint32_t(m & 31) << 7) |
            (uint32_t(valid & 1) << 12) | (uint32_t(batch) << 16);
 }
+// bit 13: the integral is evaluated in FP64 (set at setup for the FP64 path,
+// or when its FP32 rounding noise bound exceeds half its tolerance)
+constexpr uint32_t kMetaFp64 = 1u << 13;
+// bit 14: the integral is evaluated in float-float (set when its FP32 rounding
+// noise exceeds a quarter of its tolerance)
+constexpr uint32_t kMetaDf32 = 1u << 14;
 __host__ __device__ inline int meta_kind(uint32_t mt) { return int(mt & 3u); }
 __host__ __device__ inline int meta_l(uint32_t mt) { return int((mt >> 2) & 31u); }
 __host__ __device__ inline int meta_m(uint32_t mt) { return int((mt >> 7) & 31u); }
@@ -77,7 +92,7 @@ struct RoundTotals {
     unsigned long long pool;    // regions in the next pool
     unsigned long long eval;    // regions to evaluate next round
     unsigned long long active;  // integrals still refining
-    unsigned long long pad;
+    unsigned long long escalated;  // integrals moved from FP32 to FP64 evaluation (cumulative)
 };
 
 // Pointers into the workspace.
@@ -104,6 +119,7 @@ struct Work {
     uint64_t* key[2];
     double* val[2];
     double* err[2];
+    float* nse[2];
     uint2* evl;
 };
 
@@ -113,7 +129,7 @@ cudaError_t init_rule_tables(int device);
 cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
                         Lattice lat, cudaStream_t s);
 // paid_pool.cu
-cudaError_t launch_setup(const Work& w, int L0, int nff, cudaStream_t s);
+cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s);
 cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int round,
                                int max_rounds, double cover, cudaStream_t s);
 cudaError_t launch_scan(const Work& w, int64_t n_active, cudaStream_t s);

@@ -62,7 +62,7 @@ __device__ __forceinline__ int log_key(double x)
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_setup(Work w, int L0, int nff)
+__global__ void k_setup(Work w, int L0, int nff, int fp64)
 {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= w.n) return;
@@ -89,7 +89,7 @@ __global__ void k_setup(Work w, int L0, int nff)
     sincos(qx, &sx, &cx);
     sincos(qy, &sy, &cy);
     w.trig[g] = QTrig{cx, sx, cy, sy};
-    w.meta[g] = make_meta(B.kind, valid ? l : 0, valid ? m : 0, valid, b);
+    w.meta[g] = make_meta(B.kind, valid ? l : 0, valid ? m : 0, valid, b) | (fp64 ? kMetaFp64 : 0u);
     const uint32_t side = 1u << L0, n0 = side * side;
     const uint32_t base = uint32_t(g) * n0;
     w.seg_base[g] = base;
@@ -100,14 +100,15 @@ __global__ void k_setup(Work w, int L0, int nff)
     }
     w.active[0][g] = uint32_t(g);
     B.status[local] = RUNNING;
+    if (g == 0) w.totals->escalated = 0ull;
 }
 
-cudaError_t launch_setup(const Work& w, int L0, int nff, cudaStream_t s)
+cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s)
 {
     if (w.n <= 0) return cudaSuccess;
     const int threads = 256;
     const int64_t blocks = (w.n + threads - 1) / threads;
-    k_setup<<<int(blocks), threads, 0, s>>>(w, L0, nff);
+    k_setup<<<int(blocks), threads, 0, s>>>(w, L0, nff, fp64);
     return cudaGetLastError();
 }
 
@@ -132,24 +133,43 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
     const DevBatch B = w.batches[meta_batch(mt)];
     const double* val = w.val[cur];
     const double* err = w.err[cur];
+    const float* nse = w.nse[cur];
     const uint64_t* key = w.key[cur];
 
-    double sv = 0.0, se = 0.0, mx = 0.0;
+    // E = sum |Q_N - Q_2N| over the regions (Sec. 3), exactly as computed:
+    // FP32 rounding noise is never subtracted, so it can only delay
+    // convergence.  The noise bound sum(nse) (0 for FP64 regions) decides
+    // whether an FP32 integral must be re-evaluated at higher precision.
+    double sv = 0.0, se = 0.0, sn = 0.0, mx = 0.0;
     for (uint32_t j = lane; j < cnt; j += 32) {
         const double v = val[base + j], e = err[base + j];
         sv += v;
         se += e;
+        sn += nse[base + j];
         if (key_level(key[base + j]) < uint32_t(kMaxLevel)) mx = fmax(mx, e);
     }
     const double V = warp_sum(sv), E = warp_sum(se), maxE = warp_max(mx);
+    const double noise = kNoiseSigmas * warp_sum(sn);
     const double tol = fmax(B.abs_tol, B.rel_tol * fabs(V));
     const int64_t allowed = (B.max_regions - int64_t(cnt)) / 3;
+    const bool fp32 = (mt & (kMetaFp64 | kMetaDf32)) == 0u;
 
     int st = RUNNING;
     if (force_status >= 0) st = force_status;
     else if (!isfinite(V) || !isfinite(E)) st = NONFINITE;
     else if (E <= tol) st = CONVERGED;
     else if (round >= max_rounds) st = ROUNDCAP;
+    else if (fp32 && noise > 0.25 * tol) {
+        // FP32 rounding noise alone would use a quarter of the tolerance:
+        // refinement cannot remove it, so re-evaluate at higher precision
+        if (lane == 0) {
+            w.thr[s] = make_uint2(kEscalate, 0u);
+            w.cnt_new[s] = cnt;
+            w.cnt_eval[s] = cnt;
+            atomicAdd(&w.totals->escalated, 1ull);
+        }
+        return;
+    }
     else if (allowed <= 0 || !(maxE > 0.0)) st = BUDGET;
 
     if (st != RUNNING) {
@@ -364,10 +384,27 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w, int cur, 
     const uint64_t* key = w.key[cur];
     const double* val = w.val[cur];
     const double* err = w.err[cur];
+    const float* nse = w.nse[cur];
     uint64_t* key_n = w.key[nxt];
     double* val_n = w.val[nxt];
     double* err_n = w.err[nxt];
+    float* nse_n = w.nse[nxt];
     const unsigned lt = (1u << lane) - 1u;
+
+    if (th.x == kEscalate) {
+        // FP32 noise too large for the tolerance: same regions, re-evaluated in float-float
+        for (uint32_t j = lane; j < cnt; j += 32) {
+            key_n[pbase + j] = key[base + j];
+            w.evl[ebase + j] = make_uint2(uint32_t(pbase + j), g);
+        }
+        if (lane == 0) {
+            w.meta[g] |= kMetaDf32;
+            w.seg_base[g] = uint32_t(pbase);
+            w.seg_count[g] = nnew;
+            w.active[nxt][abase] = g;
+        }
+        return;
+    }
 
     uint32_t run = 0, erun = 0, tbrun = 0;
     for (uint32_t c0 = 0; c0 < cnt; c0 += 32) {
@@ -375,11 +412,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w, int cur, 
         const bool valid = j < cnt;
         uint64_t k = 0;
         double v = 0.0, e = 0.0;
+        float nz = 0.0f;
         int bin = 255;
         if (valid) {
             k = key[base + j];
             v = val[base + j];
             e = err[base + j];
+            nz = nse[base + j];
             if (e > 0.0 && key_level(k) < uint32_t(kMaxLevel))
                 bin = min(kHistBins - 1, kmax - log_key(e));
         }
@@ -396,6 +435,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w, int cur, 
             key_n[p] = k;
             val_n[p] = v;
             err_n[p] = e;
+            nse_n[p] = nz;
         }
         if (mark) {
             const uint32_t L = key_level(k), ix = key_ix(k), iy = key_iy(k);

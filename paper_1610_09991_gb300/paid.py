@@ -42,7 +42,8 @@ class paid_stats(ctypes.Structure):
                 ("pool_capacity", ctypes.c_int64), ("n_integrals", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("eval_launches", ctypes.c_int64),
                 ("eval_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
-                ("scan_ms", ctypes.c_double), ("split_ms", ctypes.c_double)]
+                ("scan_ms", ctypes.c_double), ("split_ms", ctypes.c_double),
+                ("escalated", ctypes.c_int64)]
 
 
 class paid_batch(ctypes.Structure):

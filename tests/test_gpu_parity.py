@@ -5,6 +5,11 @@ Criterion, for integrals both sides report CONVERGED:
 (both results lie within their own error sums of the true integral, and each
 error sum is below its tolerance).  For integrals either side stops on the
 region budget, |v_gpu - v_oracle| <= E_gpu + E_oracle + 1e-12.
+The error sum |Q_N - Q_2N| of Sec. 3 is an estimate, not a bound, so either
+side can stop with an error larger than its estimate (a false convergence).
+A pair that disagrees beyond the criterion is decided by the integral's
+definition: a dense periodic trapezoid evaluation converged to 1e-13
+(oracle.brute_force); the GPU result must lie within 2 tol of it.
 The oracle uses the strict greedy order of Algorithm 1 and the GPU splits a
 batch of regions per round, so the two partitions differ and the comparison
 is at tolerance level, never bitwise.
@@ -53,20 +58,40 @@ def run_gpu(paid, torch, ctx, batches):
     return [tuple(x.cpu().numpy() for x in (r.values, r.errors, r.regions, r.status)) for r in outs]
 
 
-def assert_parity(g, o, rel, ab):
+def assert_parity(g, o, rel, ab, ident=None, max_adjudicated=0.01):
+    """ident(i) -> (kind, q, l, m, T) of integral i, for adjudication."""
     v, e, r, s = g
     vo, eo, ro, so = o
     assert np.all(np.isin(s, [0, 1, 2, 3, 4]))
     both = (s == 0) & (so == 0)
     d = np.abs(v - vo)
-    tol = 2 * np.maximum(rel * np.abs(vo), ab) + 1e-12
-    bad = both & (d > tol)
-    assert not bad.any(), (np.where(bad)[0][:10], v[bad][:5], vo[bad][:5], e[bad][:5])
+    tol1 = np.maximum(rel * np.abs(vo), ab)
+    bad = both & (d > 2 * tol1 + 1e-12)
     rest = ~both & (s != 2) & (so != 2)
-    assert np.all(d[rest] <= e[rest] + eo[rest] + 1e-12)
+    bad |= rest & (d > e + eo + 1e-12)
+    idx = np.where(bad)[0]
+    assert ident is not None or idx.size == 0, (idx[:10], v[idx][:5], vo[idx][:5])
+    assert idx.size <= max(1, max_adjudicated * len(v)), idx.size
+    for i in idx:
+        kind, q, l, m, T = ident(int(i))
+        truth, M = oracle.brute_force(kind, q, l, m, T, LAT)
+        assert np.isfinite(truth), (i, "brute force did not converge")
+        t = max(rel * abs(truth), ab)
+        assert abs(v[i] - truth) <= 2 * t + 1e-12, (i, v[i], vo[i], truth)
     # both sides agree on which integrals are non-finite
     assert np.array_equal(s == 2, so == 2)
     return both.sum()
+
+
+def batch_ident(b):
+    npairs = b.lm.shape[0]
+    return lambda i: (b.kind, b.q[i // npairs], int(b.lm[i % npairs][0]),
+                      int(b.lm[i % npairs][1]), b.T)
+
+
+def flat_ident(flat, idx):
+    return lambda i: (int(flat["kind"][idx[i]]), flat["q"][idx[i]], int(flat["lm"][idx[i]][0]),
+                      int(flat["lm"][idx[i]][1]), float(flat["T"][idx[i]]))
 
 
 def test_first_shell_batch_matches_oracle(paid, torch):
@@ -76,7 +101,7 @@ def test_first_shell_batch_matches_oracle(paid, torch):
     (g,) = run_gpu(paid, torch, ctx, [b])
     o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol, b.max_regions)
     assert np.all(g[3] == 0) and np.all(o[3] == 0)
-    assert assert_parity(g, o, b.rel_tol, b.abs_tol) == b.n
+    assert assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b)) >= b.n - 1
     # each result within its own error estimate, and the budget respected
     assert np.all(g[1] <= np.maximum(b.abs_tol, b.rel_tol * np.abs(g[0])))
     assert np.all((g[2] - 16) % 3 == 0) and np.all(g[2] <= b.max_regions)
@@ -92,7 +117,7 @@ def test_flow_step_small_grid_matches_oracle(paid, torch):
     for b, g in zip(w.batches, gs):
         o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
                                    b.max_regions)
-        n = assert_parity(g, o, b.rel_tol, b.abs_tol)
+        n = assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b))
         assert n >= 0.9 * b.n
 
 
@@ -106,7 +131,7 @@ def test_full_flow_step_sampled(paid, torch):
     idx = W.sample_indices(w.n, 240, seed=1234)
     o = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
                               flat["T"][idx], LAT, 1e-6, 1e-10, 100000)
-    assert_parity(tuple(x[idx] for x in g), o, 1e-6, 1e-10)
+    assert_parity(tuple(x[idx] for x in g), o, 1e-6, 1e-10, flat_ident(flat, idx))
     # properties at full size
     v, e, r, s = g
     assert np.all(np.isin(s, [0, 1]))
@@ -151,7 +176,7 @@ def test_rule_n6_matches_oracle(paid, torch):
     (g,) = run_gpu(paid, torch, ctx, [b])
     o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol, b.max_regions,
                                rule_n=6)
-    assert assert_parity(g, o, b.rel_tol, b.abs_tol) > 0
+    assert assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b)) > 0
 
 
 def test_edge_cases(paid, torch):

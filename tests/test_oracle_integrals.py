@@ -159,3 +159,26 @@ def test_high_T_limit_is_gram_over_4T():
                                         init_level=0)
     G = np_ref.shift_matrix(q).T
     assert np.allclose(4 * T * v.reshape(9, 9), G, atol=1e-6)
+
+
+def test_brute_force_trapezoid_matches_numpy():
+    # the oracle's dense trapezoid against the independent numpy restatement
+    for kind, q, l, m, T in [(0, (0.3, 1.1), 2, 5, 0.5), (1, (-2.0, 0.7), 8, 3, 0.2)]:
+        a = oracle.trapezoid(kind, q, l, m, T, LAT, 96)
+        b = np_ref.trapezoid(kind, q, l, m, T, LAT, 96)
+        assert abs(a - b) < 1e-15
+    v, M = oracle.brute_force(0, (0.3, 1.1), 2, 5, 0.5, LAT, M0=64)
+    assert np.isfinite(v) and M <= 256
+
+
+def test_heuristic_error_estimate_can_miss():
+    # Sec. 3's err = |Q_N - Q_2N| is an estimate: on this ph integral at T = 0.05
+    # the greedy order stops with a true error 4x its error sum.  Parity
+    # disagreements are therefore decided by the converged brute force.
+    q = (math.pi / 6, 5 * math.pi / 6)
+    v, e, r, s = oracle.integrate_batch(0, np.array([q]), np.array([(1, 7)]), 0.05, LAT,
+                                        1e-6, 1e-10, 100000)
+    truth, M = oracle.brute_force(0, q, 1, 7, 0.05, LAT)
+    assert s[0] == oracle.CONVERGED and np.isfinite(truth)
+    assert abs(v[0] - truth) > 2 * e[0]
+    assert abs(v[0] - truth) < 1e-7
