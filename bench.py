@@ -47,8 +47,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
-    ap.add_argument("--workload", choices=["flow_step", "first_shell"], default="flow_step")
-    ap.add_argument("--eval", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell"],
+                    default="flow_step")
+    ap.add_argument("--path", choices=["plain", "fp32", "learned"], default="learned",
+                    help="plain: FP64 evaluation from the uniform start; fp32: FP32 / float-float "
+                         "evaluation; learned: fp32 plus the learned proposal's seeded start")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timed FP64 comparison step of an FP32 run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,6 +65,8 @@ def workload(name):
     from paper_1610_09991_gb300 import workloads as W
     if name == "first_shell":
         return W.config_first_shell(), 5
+    if name == "flow_step_q4":
+        return W.config_flow_step(nq=4), 9
     return W.config_flow_step(), 9
 
 
@@ -262,6 +267,7 @@ def run_paid(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w, ff = workload(args.workload)
+    args.eval = "fp64" if args.path == "plain" else "fp32"
     ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1,
                     eval_fp32=1 if args.eval == "fp32" else 0)
     dev = torch.device("cuda", local)
@@ -271,10 +277,25 @@ def run_paid(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peaks = fp64_peak(local)
+    prop_info, prop, rate = None, None, None
+    if args.path == "learned":
+        from paper_1610_09991_gb300 import proposal as PR
+        prop, hist, t_train = PR.train_default(device=local, n_draws=24, nq=8, epochs=20)
+        t0 = time.perf_counter()
+        rate, calib = PR.calibrate_default(prop, device=local)
+        t_cal = time.perf_counter() - t0
+        prop_info = {"train_seconds": t_train, "calibrate_seconds": t_cal,
+                     "training_rows": 24 * 2 * 64 * 81, "draws": "seeds 0..23 of "
+                     "t' ~ U[-0.35,0], mu ~ U[-1.4,0], T log-U[0.005,1], 8x8 q grid, ph+pp",
+                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "rate": rate,
+                     "calibration_region_evals": {str(k): v for k, v in calib.items()}}
 
     def step():
         flush.fill_(1)
-        return ctx.integrate_multi(dbs, stream=stream)
+        if prop is None:
+            return ctx.integrate_multi(dbs, stream=stream)
+        maps = PR.predict(prop, ctx, dbs)
+        return ctx.integrate_multi_seeded(dbs, maps, rate, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -328,7 +349,7 @@ def run_paid(args):
         conv_e2e, h2d, d2h = 0, 0, 0
         for _ in range(n_e2e):
             flush.fill_(1)
-            res, h2d, d2h = ctx.integrate_host(hb)
+            res, h2d, d2h = ctx.integrate_host(hb, proposal=prop, rate=rate or 2.0)
             conv_e2e += sum(int((r.status == 0).sum()) for r in res)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
@@ -356,8 +377,11 @@ def run_paid(args):
         "config": workload_config(w, ff, args.eval),
         "clocks": clk, "roofline": roof, "gpu_launches": agg["launches"],
         "e2e": e2e,
-        "path": ("plain batched FP64 GPU cubature" if args.eval == "fp64" else
-                 "batched GPU cubature, FP32 integrand / FP64 sums") + " (learned proposal not used)",
+        "path": {"plain": "plain FP64 GPU cubature from the uniform level-2 start",
+                 "fp32": "batched GPU cubature, FP32 / float-float integrand, FP64 sums",
+                 "learned": "learned proposal seeding + batched GPU cubature, FP32 / "
+                            "float-float integrand, FP64 sums"}[args.path],
+        "proposal": prop_info,
         "budget_integrals_per_step": agg["budget"] / args.steps,
         "region_evals_per_s": agg["region_evals"] * world / elapsed,
         "node_evals_per_s": agg["node_evals"] * world / elapsed,
@@ -370,7 +394,7 @@ def run_paid(args):
     }
     vals = torch.cat([o.values for o in outs]).cpu().numpy()
     stats = torch.cat([o.status for o in outs]).cpu().numpy()
-    if args.eval == "fp32" and not args.no_compare:
+    if args.path != "plain" and not args.no_compare:
         # the plain FP64 GPU path on the same batch, one timed step
         c64 = P.Context(*w.lattice, ffset=ff, device=local, timing=1)
         c64.integrate_multi(dbs, stream=stream)        # warm-up (workspace)

@@ -203,6 +203,72 @@ int paid_integrate_batch_static(paid_ctx* ctx, int kind,
                                 double* values, double* errors, int64_t* regions,
                                 int32_t* status, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned refinement proposal (not in the paper; the workload specification's
+ * learned component).  A 16 x 16 map per integral of predicted log10 cell
+ * errors, relative to the integral's scale, decides how far each level-4 cell
+ * of the domain is pre-split before refinement starts; it never decides
+ * convergence (the |Q_N - Q_2N| sums still do).
+ *
+ * Map convention: entry c = 16 ix + iy is the level-4 cell (ix, iy) of the
+ * region grid; its value is log10(err_c / S) with err_c = |Q_N - Q_2N| of the
+ * cell evaluated as one region and S = sum_c |Q_2N of cell c| (clamped to
+ * [-16, 0]).
+ * ------------------------------------------------------------------------- */
+
+/* Targets for training: evaluate each integral's uniform level-4 grid once
+ * (FP64) and write its map to out (device, float [nq*npairs][256], the batch
+ * order of paid_integrate_batch).  Workspace as for paid_integrate_batch with
+ * 4^4 initial regions per integral.  Returns PAID_OK / ERR_ARG / ERR_OOM / ERR_CUDA. */
+int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
+                     const int32_t* lm, double T, float* out, void* workspace, size_t ws_bytes,
+                     void* stream);
+
+/* paid_integrate_multi with the initial partition taken from maps:
+ *   proposal  device, float [n][256] in the global order of the batches
+ *             (batch 0's integrals first), or NULL for a uniform level-4 start;
+ *   rate      calibrated decay of a cell's error per level, as a power of 4
+ *             (a cell predicted at log10 error t is split k = floor((t - b) /
+ *             (rate log10 4)) more levels, b = log10(rel_tol / 256), k in
+ *             [-2, 3]; cells predicted below b are merged back to level 3 or 2
+ *             where all their siblings agree).
+ * Everything else as paid_integrate_multi. */
+int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb,
+                                const float* proposal, double rate, void* workspace,
+                                size_t ws_bytes, void* stream);
+
+/* The network: 32 -> 256 -> 256 -> 256 -> 256 -> 256, GELU after the four
+ * hidden layers; BF16 weights and activations, FP32 accumulation (tensor
+ * cores), FP32 master parameters in one buffer: for layer l = 0..4,
+ * W_l [K_l][256] row-major (K_0 = 32, else 256), then b_l [256]. */
+#define PAID_MLP_IN 32
+#define PAID_MLP_HIDDEN 256
+#define PAID_MLP_OUT 256
+#define PAID_MLP_LAYERS 5
+
+/* Number of FP32 parameters (270,592). */
+int paid_mlp_param_count(int64_t* n);
+/* Workspace bytes for forward / gradient passes over M rows. */
+int paid_mlp_workspace_size(int64_t M, size_t* bytes);
+/* Seeded initialisation on the device (uniform +-1/sqrt(K) weights, zero biases). */
+int paid_mlp_init(float* params, uint64_t seed, void* stream);
+/* Inputs for one batch: x (device, BF16 bits [nq*npairs][32]) =
+ * (sin qx, cos qx, sin qy, cos qy, one-hot l [9], one-hot m [9], log10 T, mu, t',
+ *  one-hot kind [ph, pp], 0 padding), mu and t' from the context. */
+int paid_mlp_features(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
+                      const int32_t* lm, double T, uint16_t* x, void* stream);
+/* Forward pass: x (BF16 [M][32]) -> out (FP32 [M][256]). */
+int paid_mlp_forward(const float* params, const uint16_t* x, int64_t M, float* out,
+                     void* workspace, size_t ws_bytes, void* stream);
+/* Mean-squared-error gradient over M rows against target (FP32 [M][256]):
+ * grad (FP32, param_count) and loss (FP32 scalar, mean over M x 256) on the device. */
+int paid_mlp_grad(const float* params, const uint16_t* x, const float* target, int64_t M,
+                  float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream);
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay on the
+ * weights only) with moments m, v (FP32, param_count); step counts from 1. */
+int paid_mlp_adamw(float* params, const float* grad, float* m, float* v, int step, float lr,
+                   float weight_decay, void* stream);
+
 /* Statistics of the last integrate call.  Returns PAID_OK or PAID_ERR_ARG. */
 int paid_last_stats(paid_ctx* ctx, paid_stats* out);
 

@@ -250,6 +250,8 @@ int paid_pool_capacity(paid_ctx* ctx, int64_t n_integrals, size_t ws_bytes, int6
     int64_t cap = ws_bytes > fixed + 9 * 256 ? int64_t((ws_bytes - fixed - 9 * 256) / 64) : 0;
     cap = std::min(cap, kMaxCapacity);
     while (cap > 0 && layout(n_integrals, cap).end > ws_bytes) --cap;
+    // the estimate above reserves worst-case alignment; take what still fits
+    while (cap < kMaxCapacity && layout(n_integrals, cap + 1).end <= ws_bytes) ++cap;
     *capacity = cap;
     return PAID_OK;
 }
@@ -261,19 +263,24 @@ int paid_last_stats(paid_ctx* ctx, paid_stats* out)
     return PAID_OK;
 }
 
-int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace,
-                         size_t ws_bytes, void* stream)
+}  // extern "C"
+
+namespace {
+
+// Validates the batches, sizes the pool, lays out the workspace and uploads
+// the batch table.  n0 = regions per integral that the start needs at least.
+int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, size_t ws_bytes,
+            int64_t n0, cudaStream_t s, Work& w, int64_t& n, int64_t& cap)
 {
-    if (!ctx) return PAID_ERR_ARG;
     ctx->last_error.clear();
     ctx->stats = paid_stats{};
     if (nb < 0 || nb > kMaxBatches || (nb > 0 && !batches))
         return fail(ctx, PAID_ERR_ARG, "nb must be in 0..4096 with a batch array");
     const paid_options& o = ctx->opt;
-    const int64_t n0 = int64_t(1) << (2 * o.init_level);
+    const int64_t nl0 = int64_t(1) << (2 * o.init_level);
     std::vector<DevBatch> hb;
     hb.reserve(nb);
-    int64_t n = 0;
+    n = 0;
     for (int i = 0; i < nb; ++i) {
         const paid_batch& b = batches[i];
         if (b.kind < PAID_PH || b.kind > PAID_OVERLAP) return fail(ctx, PAID_ERR_ARG, "bad kind");
@@ -283,7 +290,7 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
             return fail(ctx, PAID_ERR_ARG, "null buffer");
         if (!(b.rel_tol >= 0.0) || !(b.abs_tol >= 0.0))
             return fail(ctx, PAID_ERR_ARG, "tolerances must be >= 0");
-        if (b.max_regions < n0 || b.max_regions > kMaxRegionsPerIntegral)
+        if (b.max_regions < nl0 || b.max_regions > kMaxRegionsPerIntegral)
             return fail(ctx, PAID_ERR_ARG, "max_regions must be in [4^init_level, 2^23]");
         if (nbi == 0) continue;
         DevBatch d{};
@@ -312,26 +319,24 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
     if (!workspace) return fail(ctx, PAID_ERR_ARG, "null workspace");
     if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
         return fail(ctx, PAID_ERR_ARG, "workspace must be 256-byte aligned");
-
-    int64_t cap = 0;
+    cap = 0;
     paid_pool_capacity(ctx, n, ws_bytes, &cap);
     if (o.pool_capacity > 0) cap = std::min(cap, o.pool_capacity);
-    if (cap < n * n0)
-        return fail(ctx, PAID_ERR_OOM, "workspace too small for the initial partition");
-
-    DeviceGuard guard(ctx->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cap < n * n0) return fail(ctx, PAID_ERR_OOM, "workspace too small for the initial partition");
     const Layout L = layout(n, cap);
-    char* base = static_cast<char*>(workspace);
-    Work w = make_work(base, L, n, cap, int(hb.size()));
+    w = make_work(static_cast<char*>(workspace), L, n, cap, int(hb.size()));
+    cudaError_t e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+    return PAID_OK;
+}
 
+// The refinement loop of Listing 5 from a partition already on the eval list.
+int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_eval,
+               int64_t pool, cudaStream_t s)
+{
+    const paid_options& o = ctx->opt;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
-                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "batch upload");
-    if ((e = launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "setup");
-
     const int nodes = (2 * o.rule_n + 1) * (2 * o.rule_n + 1);
     const bool timed = o.timing != 0;
     cudaEvent_t* ev = ctx->ev;
@@ -341,8 +346,6 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
         return (timed && cudaEventElapsedTime(&ms, ev[a], ev[b]) == cudaSuccess) ? double(ms) : 0.0;
     };
     paid_stats& st = ctx->stats;
-    st.launches = 1;
-    int64_t n_active = n, n_eval = n * n0, pool = n * n0;
     int cur = 0;
     int rc = PAID_OK;
     bool split_pending = false;
@@ -399,6 +402,108 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
     st.node_evals = st.region_evals * nodes;
     st.pool_capacity = cap;
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace,
+                         size_t ws_bytes, void* stream)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    const paid_options& o = ctx->opt;
+    const int64_t n0 = int64_t(1) << (2 * o.init_level);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGuard guard(ctx->device);
+    Work w{};
+    int64_t n = 0, cap = 0;
+    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, n0, s, w, n, cap);
+    if (rc != PAID_OK || n == 0) return rc;
+    cudaError_t e;
+    if ((e = launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "setup");
+    ctx->stats.launches = 1;
+    return run_rounds(ctx, w, cap, n, n * n0, n * n0, s);
+}
+
+int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb,
+                                const float* proposal, double rate, void* workspace,
+                                size_t ws_bytes, void* stream)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    if (!(rate > 0.0)) return fail(ctx, PAID_ERR_ARG, "rate must be > 0");
+    const paid_options& o = ctx->opt;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGuard guard(ctx->device);
+    Work w{};
+    int64_t n = 0, cap = 0;
+    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 16, s, w, n, cap);
+    if (rc != PAID_OK || n == 0) return rc;
+    cudaError_t e;
+    if ((e = launch_setup(w, -1, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess ||
+        (e = launch_seed(w, proposal, rate, 0, s)) != cudaSuccess ||
+        (e = launch_scan(w, n, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "seed");
+    if ((e = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals), cudaMemcpyDeviceToHost,
+                             s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "seed totals");
+    const RoundTotals t = *ctx->h_totals;
+    if (int64_t(t.pool) > cap)
+        return fail(ctx, PAID_ERR_OOM, "workspace too small for the seeded partition");
+    if ((e = launch_seed(w, proposal, rate, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
+    ctx->stats.launches = 5;
+    return run_rounds(ctx, w, cap, n, int64_t(t.eval), int64_t(t.pool), s);
+}
+
+int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
+                     const int32_t* lm, double T, float* out, void* workspace, size_t ws_bytes,
+                     void* stream)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    if (int64_t(nq) * npairs > 0 && !out) return fail(ctx, PAID_ERR_ARG, "null output");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGuard guard(ctx->device);
+    // One pass over the uniform level-4 grid, no refinement round: no integral
+    // is finalised, so values / errors / regions are never written.  The setup
+    // kernel marks every integral RUNNING in `status`; that array is aimed at
+    // `out`, which k_cell_map then overwrites in full on the same stream.
+    paid_batch b{};
+    b.kind = kind;
+    b.T = T;
+    b.nq = nq;
+    b.q = q;
+    b.npairs = npairs;
+    b.lm = lm;
+    b.rel_tol = 0.0;
+    b.abs_tol = 0.0;
+    b.max_regions = 256;
+    b.values = reinterpret_cast<double*>(out);
+    b.errors = reinterpret_cast<double*>(out);
+    b.regions = reinterpret_cast<int64_t*>(out);
+    b.status = reinterpret_cast<int32_t*>(out);
+    Work w{};
+    int64_t n = 0, cap = 0;
+    int rc = prepare(ctx, &b, 1, workspace, ws_bytes, 256, s, w, n, cap);
+    if (rc != PAID_OK || n == 0) return rc;
+    cudaError_t e;
+    if ((e = launch_setup(w, 4, ctx->nff, 1, s)) != cudaSuccess ||
+        (e = launch_eval(w, 0, n * 256, ctx->opt.rule_n, 0, ctx->lat, s)) != cudaSuccess ||
+        (e = launch_cell_map(w, out, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cell errors");
+    ctx->stats.region_evals = n * 256;
+    return PAID_OK;
+}
+
+int paid_mlp_features(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
+                      const int32_t* lm, double T, uint16_t* x, void* stream)
+{
+    if (!ctx || nq < 0 || npairs < 0) return PAID_ERR_ARG;
+    if (int64_t(nq) * npairs > 0 && (!q || !lm || !x)) return PAID_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    return launch_features(kind, nq, q, npairs, lm, T, ctx->lat.mu, ctx->lat.tp, x,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
 }
 
 int paid_integrate_batch(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,

@@ -129,7 +129,14 @@ cudaError_t init_rule_tables(int device);
 cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
                         Lattice lat, cudaStream_t s);
 // paid_pool.cu
+// L0 < 0: descriptors only (the partition comes from launch_seed)
 cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s);
+// pass 0: region counts into cnt_new / cnt_eval (slot = integral); pass 1 (after
+// launch_scan): keys, eval list, segments.  proposal null = uniform level 4.
+cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s);
+cudaError_t launch_features(int kind, int nq, const double* q, int npairs, const int32_t* lm,
+                            double T, double mu, double tp, void* x, cudaStream_t s);
+cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s);
 cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int round,
                                int max_rounds, double cover, cudaStream_t s);
 cudaError_t launch_scan(const Work& w, int64_t n_active, cudaStream_t s);

@@ -1,0 +1,424 @@
+// Learned refinement proposal: a 5-layer MLP, 32 -> 256 -> 256 -> 256 -> 256 -> 256,
+// GELU after the four hidden layers, that maps an integral's parameters
+// (sin/cos of qx, qy; one-hot l and m; log10 T; mu; t'; one-hot kind) to a
+// 16 x 16 map of predicted log10 cell errors.  It only decides where the
+// initial partition is pre-split; the cubature's own error sums still decide
+// convergence.  (Not part of the paper: the proposal of the workload
+// specification.)
+//
+// Kernels: BF16 tensor-core GEMMs (mma.sync m16n8k16, FP32 accumulation)
+// with fused bias / GELU / BF16 cast epilogues, the MSE loss gradient, GELU
+// backward, bias gradients and AdamW on FP32 master weights.
+//
+// Parameter buffer (FP32 master weights), layer l = 0..4 with K_0 = 32,
+// K_l = 256 otherwise, N = 256:  W_l [K_l][N] row-major, then b_l [N].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/paid.h"
+
+namespace {
+
+constexpr int kIn = PAID_MLP_IN, kHid = PAID_MLP_HIDDEN;
+constexpr int kLayers = PAID_MLP_LAYERS;
+static_assert(PAID_MLP_OUT == PAID_MLP_HIDDEN, "the output layer has the hidden width");
+
+__host__ __device__ inline int layer_k(int l) { return l == 0 ? kIn : kHid; }
+__host__ __device__ inline int64_t layer_w_off(int l)
+{
+    int64_t o = 0;
+    for (int i = 0; i < l; ++i) o += int64_t(layer_k(i)) * kHid + kHid;
+    return o;
+}
+__host__ __device__ inline int64_t param_count()
+{
+    return layer_w_off(kLayers);
+}
+
+// ---------------------------------------------------------------------------
+// GEMM  C[M][N] = sum_k A(m, k) B(k, n), A(m, k) = A[m sam + k sak],
+// B(k, n) = B[k sbk + n sbn] (BF16), FP32 accumulation on the tensor cores.
+// Tiles 64 x 64 x 32, 4 warps of 32 x 32 (2 x 4 mma tiles of 16 x 8).
+// Epilogues:
+//   EPI_STORE : C = acc + bias (FP32)
+//   EPI_ATOMIC: C += acc (FP32 atomics; split reduction over k = blockIdx.z)
+//   EPI_GELU  : pre = acc + bias (FP32), act = gelu(pre) (BF16)
+enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_GELU = 2 };
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x)
+{
+    const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
+    return cdf + x * pdf;
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128)
+k_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64_t sam, int64_t sak,
+       const __nv_bfloat16* __restrict__ B, int64_t sbk, int64_t sbn, const float* __restrict__ bias,
+       float* __restrict__ C, int64_t ldc, __nv_bfloat16* __restrict__ act, int k_chunk)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * k_chunk;
+    const int kend = min(K, kbeg + k_chunk);
+    float acc[2][4][4] = {};
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int idx = tid; idx < BM * BK; idx += 128) {
+            const int m = idx / BK, k = idx % BK;
+            const int gm = m0 + m, gk = k0 + k;
+            As[m][k] = (gm < M && gk < kend) ? A[int64_t(gm) * sam + int64_t(gk) * sak] : zero;
+        }
+        for (int idx = tid; idx < BN * BK; idx += 128) {
+            const int n = idx / BK, k = idx % BK;
+            const int gn = n0 + n, gk = k0 + k;
+            Bs[n][k] = (gn < N && gk < kend) ? B[int64_t(gk) * sbk + int64_t(gn) * sbn] : zero;
+        }
+        __syncthreads();
+        const int r = lane >> 2, c = (lane & 3) * 2;
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int row = wm * 32 + i * 16 + r;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[row][ks + c]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[row + 8][ks + c]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[row][ks + c + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[row + 8][ks + c + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int col = wn * 32 + j * 8 + r;
+                bf[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[col][ks + c]);
+                bf[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[col][ks + c + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+    const int r = lane >> 2, c = (lane & 3) * 2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int gm = m0 + wm * 32 + i * 16 + r + (h >= 2 ? 8 : 0);
+                const int gn = n0 + wn * 32 + j * 8 + c + (h & 1);
+                if (gm >= M || gn >= N) continue;
+                const float v = acc[i][j][h];
+                if (EPI == EPI_ATOMIC) {
+                    atomicAdd(&C[int64_t(gm) * ldc + gn], v);
+                } else {
+                    const float y = v + (bias ? bias[gn] : 0.0f);
+                    C[int64_t(gm) * ldc + gn] = y;
+                    if (EPI == EPI_GELU) act[int64_t(gm) * ldc + gn] = __float2bfloat16(gelu(y));
+                }
+            }
+}
+
+template <int EPI>
+cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64_t sak,
+                 const __nv_bfloat16* B, int64_t sbk, int64_t sbn, const float* bias, float* C,
+                 int64_t ldc, __nv_bfloat16* act, int splits, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    int chunk = (K + splits - 1) / splits;
+    chunk = (chunk + BK - 1) / BK * BK;
+    const int z = (K + chunk - 1) / chunk;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, z);
+    k_gemm<EPI><<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, C, ldc, act, chunk);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 master weights -> BF16 copies W [K][N] and its transpose [N][K].
+__global__ void k_cast_weights(const float* __restrict__ p, __nv_bfloat16* __restrict__ w,
+                               __nv_bfloat16* __restrict__ wt)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t o = 0, ob = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const int64_t kn = int64_t(layer_k(l)) * kHid;
+        if (i >= ob && i < ob + kn) {
+            const int64_t e = i - ob;
+            const int k = int(e / kHid), n = int(e % kHid);
+            const __nv_bfloat16 v = __float2bfloat16(p[o + e]);
+            w[ob + e] = v;
+            wt[ob + int64_t(n) * layer_k(l) + k] = v;
+            return;
+        }
+        o += kn + kHid;
+        ob += kn;
+    }
+}
+
+// dy = 2 (y - t) / (M * N) (BF16 for the backward GEMMs); loss += sum (y - t)^2 / (M N)
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, int64_t n, float scale,
+                      __nv_bfloat16* __restrict__ dy, float* __restrict__ loss)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (i < n) {
+        const float d = y[i] - t[i];
+        dy[i] = __float2bfloat16(2.0f * d * scale);
+        l = d * d * scale;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss, l);
+}
+
+// da = dh * gelu'(pre) (BF16 out); dh given as FP32
+__global__ void k_gelu_back(const float* __restrict__ dh, const float* __restrict__ pre, int64_t n,
+                            __nv_bfloat16* __restrict__ da)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) da[i] = __float2bfloat16(dh[i] * gelu_grad(pre[i]));
+}
+
+// db[n] += sum_m d[m][n]
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ d, int M, int N, float* __restrict__ db)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int m0 = blockIdx.y * 256, m1 = min(M, m0 + 256);
+    float s = 0.0f;
+    for (int m = m0; m < m1; ++m) s += __bfloat162float(d[int64_t(m) * N + n]);
+    atomicAdd(&db[n], s);
+}
+
+// AdamW on the FP32 master weights (biases not decayed).
+__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                        float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                        float wd, float c1, float c2)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // bias entries: the last kHid of every layer block
+    bool is_bias = false;
+    int64_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const int64_t kn = int64_t(layer_k(l)) * kHid;
+        if (i >= o + kn && i < o + kn + kHid) is_bias = true;
+        o += kn + kHid;
+    }
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float upd = (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] -= lr * (upd + (is_bias ? 0.0f : wd * p[i]));
+}
+
+// Seeded uniform(-a, a) initialisation (a = 1/sqrt(K), biases 0) from a
+// counter-based hash (splitmix64) of (seed, index).
+__global__ void k_init(float* __restrict__ p, uint64_t seed)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const int64_t kn = int64_t(layer_k(l)) * kHid;
+        if (i >= o && i < o + kn + kHid) {
+            if (i >= o + kn) { p[i] = 0.0f; return; }
+            uint64_t z = seed + 0x9e3779b97f4a7c15ull * uint64_t(i + 1);
+            z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+            z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+            z ^= z >> 31;
+            const float u = float(z >> 40) * (1.0f / 16777216.0f);   // [0, 1)
+            const float a = rsqrtf(float(layer_k(l)));
+            p[i] = (2.0f * u - 1.0f) * a;
+            return;
+        }
+        o += kn + kHid;
+    }
+}
+
+struct MlpWork {
+    __nv_bfloat16 *w, *wt;                 // BF16 weights and transposes
+    float* pre[kLayers];                    // pre-activations (FP32) [M][256]
+    __nv_bfloat16* h[kLayers];              // activations (BF16) [M][256]; h[4] unused
+    __nv_bfloat16 *dy, *da;                 // BF16 gradients [M][256]
+    float* dh;                              // FP32 [M][256]
+    float* grad;                            // FP32 [param_count]
+    float* loss;                            // FP32 scalar
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t mlp_work_bytes(int64_t M, MlpWork* w, char* base)
+{
+    size_t o = 0;
+    auto take = [&](size_t b) { size_t at = o; o = align256(o + b); return base ? base + at : nullptr; };
+    const int64_t nw = param_count() - int64_t(kLayers) * kHid;   // weights only
+    char* p;
+    p = take(sizeof(__nv_bfloat16) * nw); if (w) w->w = (__nv_bfloat16*)p;
+    p = take(sizeof(__nv_bfloat16) * nw); if (w) w->wt = (__nv_bfloat16*)p;
+    for (int l = 0; l < kLayers; ++l) {
+        p = take(sizeof(float) * M * kHid); if (w) w->pre[l] = (float*)p;
+        p = take(sizeof(__nv_bfloat16) * M * kHid); if (w) w->h[l] = (__nv_bfloat16*)p;
+    }
+    p = take(sizeof(__nv_bfloat16) * M * kHid); if (w) w->dy = (__nv_bfloat16*)p;
+    p = take(sizeof(__nv_bfloat16) * M * kHid); if (w) w->da = (__nv_bfloat16*)p;
+    p = take(sizeof(float) * M * kHid); if (w) w->dh = (float*)p;
+    p = take(sizeof(float) * param_count()); if (w) w->grad = (float*)p;
+    p = take(sizeof(float)); if (w) w->loss = (float*)p;
+    return o;
+}
+
+int64_t wofs(int l)   // offset of W_l in the BF16 weight arrays
+{
+    int64_t o = 0;
+    for (int i = 0; i < l; ++i) o += int64_t(layer_k(i)) * kHid;
+    return o;
+}
+
+// forward of M rows: x [M][32] BF16 -> out [M][256] FP32 (the last layer's pre)
+cudaError_t forward(const float* params, const __nv_bfloat16* x, int64_t M, float* out,
+                    MlpWork& w, cudaStream_t s)
+{
+    cudaError_t e;
+    const int64_t nw = param_count() - int64_t(kLayers) * kHid;
+    k_cast_weights<<<int((nw + 255) / 256), 256, 0, s>>>(params, w.w, w.wt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const __nv_bfloat16* in = x;
+    for (int l = 0; l < kLayers; ++l) {
+        const int K = layer_k(l);
+        const float* b = params + layer_w_off(l) + int64_t(K) * kHid;
+        // B(k, n) = W_l[k][n] = wt[n][k]: sbk = 1, sbn = K
+        if (l < kLayers - 1)
+            e = gemm<EPI_GELU>(int(M), kHid, K, in, K, 1, w.wt + wofs(l), 1, K, b, w.pre[l], kHid,
+                               w.h[l], 1, s);
+        else
+            e = gemm<EPI_STORE>(int(M), kHid, K, in, K, 1, w.wt + wofs(l), 1, K, b,
+                                out ? out : w.pre[l], kHid, nullptr, 1, s);
+        if (e != cudaSuccess) return e;
+        in = w.h[l];
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int paid_mlp_param_count(int64_t* n)
+{
+    if (!n) return PAID_ERR_ARG;
+    *n = param_count();
+    return PAID_OK;
+}
+
+int paid_mlp_workspace_size(int64_t M, size_t* bytes)
+{
+    if (!bytes || M < 0) return PAID_ERR_ARG;
+    *bytes = mlp_work_bytes(M, nullptr, nullptr);
+    return PAID_OK;
+}
+
+int paid_mlp_init(float* params, uint64_t seed, void* stream)
+{
+    if (!params) return PAID_ERR_ARG;
+    const int64_t n = param_count();
+    k_init<<<int((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(params, seed);
+    return cudaGetLastError() == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
+}
+
+int paid_mlp_forward(const float* params, const uint16_t* x, int64_t M, float* out, void* workspace,
+                     size_t ws_bytes, void* stream)
+{
+    if (!params || (M > 0 && (!x || !out)) || M < 0) return PAID_ERR_ARG;
+    if (M == 0) return PAID_OK;
+    if (M > int64_t(0x7fffffff)) return PAID_ERR_ARG;
+    if (!workspace || ws_bytes < mlp_work_bytes(M, nullptr, nullptr)) return PAID_ERR_OOM;
+    MlpWork w;
+    mlp_work_bytes(M, &w, static_cast<char*>(workspace));
+    return forward(params, reinterpret_cast<const __nv_bfloat16*>(x), M, out, w,
+                   static_cast<cudaStream_t>(stream)) == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
+}
+
+int paid_mlp_grad(const float* params, const uint16_t* x, const float* target, int64_t M,
+                  float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!params || !x || !target || !grad || !loss || M <= 0) return PAID_ERR_ARG;
+    if (M > int64_t(0x7fffffff)) return PAID_ERR_ARG;
+    if (!workspace || ws_bytes < mlp_work_bytes(M, nullptr, nullptr)) return PAID_ERR_OOM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MlpWork w;
+    mlp_work_bytes(M, &w, static_cast<char*>(workspace));
+    const __nv_bfloat16* xb = reinterpret_cast<const __nv_bfloat16*>(x);
+    if (forward(params, xb, M, nullptr, w, s) != cudaSuccess) return PAID_ERR_CUDA;
+    const int64_t nout = M * kHid;
+    const int tb = 256;
+    if (cudaMemsetAsync(grad, 0, sizeof(float) * param_count(), s) != cudaSuccess ||
+        cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess)
+        return PAID_ERR_CUDA;
+    k_mse<<<int((nout + tb - 1) / tb), tb, 0, s>>>(w.pre[kLayers - 1], target, nout,
+                                                   1.0f / float(nout), w.dy, loss);
+    const __nv_bfloat16* d = w.dy;   // gradient w.r.t. the current layer's pre-activation
+    const int splits = int(std::min<int64_t>(64, (M + 1023) / 1024));
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int K = layer_k(l);
+        const __nv_bfloat16* in = l == 0 ? xb : w.h[l - 1];
+        float* gW = grad + layer_w_off(l);
+        float* gb = gW + int64_t(K) * kHid;
+        // dW[k][n] = sum_m in[m][k] d[m][n]:  A(k, m) = in[m K + k], B(m, n) = d[m 256 + n]
+        if (gemm<EPI_ATOMIC>(K, kHid, int(M), in, 1, K, d, kHid, 1, nullptr, gW, kHid, nullptr,
+                             splits, s) != cudaSuccess)
+            return PAID_ERR_CUDA;
+        dim3 gbg((kHid + 127) / 128, int((M + 255) / 256));
+        k_bias_grad<<<gbg, 128, 0, s>>>(d, int(M), kHid, gb);
+        if (l == 0) break;
+        // dh[m][k] = sum_n d[m][n] W_l[k][n]:  B(n, k) = W_l[k][n] = w[k 256 + n]
+        if (gemm<EPI_STORE>(int(M), K, kHid, d, kHid, 1, w.w + wofs(l), 1, kHid, nullptr,
+                            w.dh, K, nullptr, 1, s) != cudaSuccess)
+            return PAID_ERR_CUDA;
+        k_gelu_back<<<int((M * K + tb - 1) / tb), tb, 0, s>>>(w.dh, w.pre[l - 1], M * K, w.da);
+        // the next step reads da while this one's d may alias it: swap buffers
+        d = w.da;
+        if (l - 1 > 0) {
+            // keep d in da, use dy as the next gradient buffer
+            __nv_bfloat16* t = w.dy;
+            w.dy = w.da;
+            w.da = t;
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
+}
+
+int paid_mlp_adamw(float* params, const float* grad, float* m, float* v, int step, float lr,
+                   float weight_decay, void* stream)
+{
+    if (!params || !grad || !m || !v || step < 1) return PAID_ERR_ARG;
+    const int64_t n = param_count();
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, float(step)), c2 = 1.0f - powf(b2, float(step));
+    k_adamw<<<int((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        params, grad, m, v, n, lr, b1, b2, 1e-8f, weight_decay, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
+}
+
+}  // extern "C"

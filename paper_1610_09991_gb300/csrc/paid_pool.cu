@@ -24,6 +24,8 @@
 // reproducible.
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "paid_internal.cuh"
 
 namespace paid {
@@ -62,7 +64,7 @@ __device__ __forceinline__ int log_key(double x)
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_setup(Work w, int L0, int nff, int fp64)
+__global__ void k_setup(Work w, int L0, int nff, int fp64, int write_regions)
 {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= w.n) return;
@@ -90,13 +92,15 @@ __global__ void k_setup(Work w, int L0, int nff, int fp64)
     sincos(qy, &sy, &cy);
     w.trig[g] = QTrig{cx, sx, cy, sy};
     w.meta[g] = make_meta(B.kind, valid ? l : 0, valid ? m : 0, valid, b) | (fp64 ? kMetaFp64 : 0u);
-    const uint32_t side = 1u << L0, n0 = side * side;
-    const uint32_t base = uint32_t(g) * n0;
-    w.seg_base[g] = base;
-    w.seg_count[g] = n0;
-    for (uint32_t r = 0; r < n0; ++r) {
-        w.key[0][base + r] = make_key(uint32_t(L0), r / side, r % side);
-        w.evl[base + r] = make_uint2(base + r, uint32_t(g));
+    if (write_regions) {
+        const uint32_t side = 1u << L0, n0 = side * side;
+        const uint32_t base = uint32_t(g) * n0;
+        w.seg_base[g] = base;
+        w.seg_count[g] = n0;
+        for (uint32_t r = 0; r < n0; ++r) {
+            w.key[0][base + r] = make_key(uint32_t(L0), r / side, r % side);
+            w.evl[base + r] = make_uint2(base + r, uint32_t(g));
+        }
     }
     w.active[0][g] = uint32_t(g);
     B.status[local] = RUNNING;
@@ -108,7 +112,185 @@ cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t 
     if (w.n <= 0) return cudaSuccess;
     const int threads = 256;
     const int64_t blocks = (w.n + threads - 1) / threads;
-    k_setup<<<int(blocks), threads, 0, s>>>(w, L0, nff, fp64);
+    k_setup<<<int(blocks), threads, 0, s>>>(w, L0, nff, fp64, L0 >= 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Proposal-seeded initial partition.  For integral g the map gives t_c, the
+// predicted log10 error of level-4 cell c (c = 16 ix + iy) relative to the
+// integral's scale.  Cell c is split k_c = floor((t_c - b) / step) further
+// levels, b = log10(rel_tol / 256), step = rate log10 4, k_c in [-2, 3]; a
+// level-3 block whose four cells all have k <= -1 stays one region, and a
+// level-2 block whose 16 cells all have k <= -2 stays one region.  A seed of
+// more than max_regions / 2 regions falls back to the uniform level-2 grid.
+__device__ __forceinline__ int seed_k(const float* map, int c, float b, float inv_step)
+{
+    if (!map) return 0;                          // uniform level-4 start
+    const float t = map[c];
+    if (!isfinite(t)) return 0;
+    return int(fminf(fmaxf(floorf((t - b) * inv_step), -2.0f), 3.0f));
+}
+
+// regions emitted by level-2 block (bx, by) of integral g; with emit != null
+// writes them (keys and eval entries) starting at pool position p
+__device__ uint32_t seed_block(const float* map, int bx, int by, float b, float inv_step,
+                              uint64_t* key, uint2* evl, unsigned long long p,
+                              unsigned long long e, uint32_t g, bool emit)
+{
+    int kmax2 = -2;
+    for (int u = 0; u < 4; ++u)
+        for (int v = 0; v < 4; ++v) kmax2 = max(kmax2, seed_k(map, (4 * bx + u) * 16 + 4 * by + v, b, inv_step));
+    if (kmax2 <= -2) {
+        if (emit) { key[p] = make_key(2, bx, by); evl[e] = make_uint2(uint32_t(p), g); }
+        return 1;
+    }
+    uint32_t cnt = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int d = 0; d < 2; ++d) {
+            const int sx = 2 * bx + a, sy = 2 * by + d;
+            int k[4], kmax3 = -2;
+            for (int u = 0; u < 2; ++u)
+                for (int v = 0; v < 2; ++v) {
+                    k[2 * u + v] = seed_k(map, (2 * sx + u) * 16 + 2 * sy + v, b, inv_step);
+                    kmax3 = max(kmax3, k[2 * u + v]);
+                }
+            if (kmax3 <= -1) {
+                if (emit) { key[p + cnt] = make_key(3, sx, sy); evl[e + cnt] = make_uint2(uint32_t(p + cnt), g); }
+                ++cnt;
+                continue;
+            }
+            for (int u = 0; u < 2; ++u)
+                for (int v = 0; v < 2; ++v) {
+                    const int kk = max(k[2 * u + v], 0), side = 1 << kk;
+                    const uint32_t ix = uint32_t(2 * sx + u) << kk, iy = uint32_t(2 * sy + v) << kk;
+                    for (int x = 0; x < side; ++x)
+                        for (int y = 0; y < side; ++y) {
+                            if (emit) {
+                                key[p + cnt] = make_key(uint32_t(4 + kk), ix + x, iy + y);
+                                evl[e + cnt] = make_uint2(uint32_t(p + cnt), g);
+                            }
+                            ++cnt;
+                        }
+                }
+        }
+    return cnt;
+}
+
+// one warp per integral; lanes 0..15 own the 16 level-2 blocks
+__global__ void __launch_bounds__(256) k_seed(Work w, const float* proposal, float inv_step, int pass)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t g = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    if (g >= w.n) return;
+    const DevBatch& B = w.batches[meta_batch(w.meta[g])];
+    const float b = float(log10(B.rel_tol > 0.0 ? B.rel_tol / 256.0 : 1e-300));
+    const float* map = proposal ? proposal + g * 256 : nullptr;
+    uint32_t mine = 0;
+    if (lane < 16) mine = seed_block(map, lane >> 2, lane & 3, b, inv_step, nullptr, nullptr, 0, 0,
+                                     uint32_t(g), false);
+    uint32_t total = mine;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    const bool fallback = int64_t(total) > B.max_regions / 2;
+    if (pass == 0) {
+        if (lane == 0) {
+            const uint32_t c = fallback ? 16u : total;
+            w.cnt_new[g] = c;
+            w.cnt_eval[g] = c;
+        }
+        return;
+    }
+    const int64_t blk = g / kScanBlock;
+    const unsigned long long pbase = w.blk_pool[blk] + w.pre_pool[g];
+    const unsigned long long ebase = w.blk_eval[blk] + w.pre_eval[g];
+    if (fallback) {
+        if (lane < 16) {
+            w.key[0][pbase + lane] = make_key(2, lane >> 2, lane & 3);
+            w.evl[ebase + lane] = make_uint2(uint32_t(pbase + lane), uint32_t(g));
+        }
+    } else {
+        uint32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t off = incl - mine;
+        if (lane < 16)
+            seed_block(map, lane >> 2, lane & 3, b, inv_step, w.key[0], w.evl, pbase + off,
+                       ebase + off, uint32_t(g), true);
+    }
+    if (lane == 0) {
+        w.seg_base[g] = uint32_t(pbase);
+        w.seg_count[g] = fallback ? 16u : total;
+    }
+}
+
+cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s)
+{
+    if (w.n <= 0) return cudaSuccess;
+    const float inv_step = float(1.0 / (rate * log10(4.0)));
+    k_seed<<<int((w.n + 7) / 8), 256, 0, s>>>(w, proposal, inv_step, pass);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Proposal inputs (BF16) for one batch, see paid_mlp_features.
+__global__ void k_features(int kind, int nq, const double* q, int npairs, const int32_t* lm,
+                           double T, double mu, double tp, __nv_bfloat16* x)
+{
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= int64_t(nq) * npairs) return;
+    const int64_t iq = g / npairs, ip = g % npairs;
+    double sx, cx, sy, cy;
+    sincos(q[2 * iq], &sx, &cx);
+    sincos(q[2 * iq + 1], &sy, &cy);
+    const int l = lm[2 * ip], m = lm[2 * ip + 1];
+    float f[32];
+    for (int i = 0; i < 32; ++i) f[i] = 0.0f;
+    f[0] = float(sx); f[1] = float(cx); f[2] = float(sy); f[3] = float(cy);
+    if (l >= 0 && l < 9) f[4 + l] = 1.0f;
+    if (m >= 0 && m < 9) f[13 + m] = 1.0f;
+    f[22] = float(log10(T));
+    f[23] = float(mu);
+    f[24] = float(tp);
+    f[25] = kind == PH ? 1.0f : 0.0f;
+    f[26] = kind == PP ? 1.0f : 0.0f;
+    for (int i = 0; i < 32; ++i) x[g * 32 + i] = __float2bfloat16(f[i]);
+}
+
+cudaError_t launch_features(int kind, int nq, const double* q, int npairs, const int32_t* lm,
+                            double T, double mu, double tp, void* x, cudaStream_t s)
+{
+    const int64_t n = int64_t(nq) * npairs;
+    if (n <= 0) return cudaSuccess;
+    k_features<<<int((n + 255) / 256), 256, 0, s>>>(kind, nq, q, npairs, lm, T, mu, tp,
+                                                   static_cast<__nv_bfloat16*>(x));
+    return cudaGetLastError();
+}
+
+// Relative log10 error map of the uniform level-4 grid (one warp per integral).
+__global__ void k_cell_map(Work w, float* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t g = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    if (g >= w.n) return;
+    const uint32_t base = w.seg_base[g];
+    double sa = 0.0;
+    for (int c = lane; c < 256; c += 32) sa += fabs(w.val[0][base + c]);
+    sa = warp_sum(sa);
+    for (int c = lane; c < 256; c += 32) {
+        const double r = sa > 0.0 ? w.err[0][base + c] / sa : 0.0;
+        const double t = r > 1e-16 ? log10(r) : -16.0;
+        out[g * 256 + c] = float(t > 0.0 ? 0.0 : t);
+    }
+}
+
+cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s)
+{
+    if (w.n <= 0) return cudaSuccess;
+    k_cell_map<<<int((w.n + 7) / 8), 256, 0, s>>>(w, out);
     return cudaGetLastError();
 }
 

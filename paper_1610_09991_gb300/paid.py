@@ -9,6 +9,7 @@ device every call raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 from dataclasses import dataclass
@@ -26,7 +27,10 @@ CONVERGED, BUDGET, NONFINITE, ROUNDCAP, POOL = 0, 1, 2, 3, 4
 #: every entry point declared in include/paid.h
 EXPORTS = ("paid_options_default", "paid_create", "paid_destroy", "paid_workspace_size",
            "paid_pool_capacity", "paid_integrate_batch", "paid_integrate_multi",
-           "paid_last_stats", "paid_error_string", "paid_last_error")
+           "paid_integrate_multi_seeded", "paid_cell_errors", "paid_last_stats",
+           "paid_error_string", "paid_last_error", "paid_mlp_param_count",
+           "paid_mlp_workspace_size", "paid_mlp_init", "paid_mlp_features", "paid_mlp_forward",
+           "paid_mlp_grad", "paid_mlp_adamw")
 
 
 class paid_options(ctypes.Structure):
@@ -91,6 +95,16 @@ def load(path: str = LIB_PATH):
         lib.paid_error_string.restype = ctypes.c_char_p
         lib.paid_last_error.argtypes = [P]
         lib.paid_last_error.restype = ctypes.c_char_p
+        lib.paid_integrate_multi_seeded.argtypes = [P, ctypes.POINTER(paid_batch), I, P, D, P,
+                                                    ctypes.c_size_t, P]
+        lib.paid_cell_errors.argtypes = [P, I, I, P, I, P, D, P, P, ctypes.c_size_t, P]
+        lib.paid_mlp_param_count.argtypes = [ctypes.POINTER(I64)]
+        lib.paid_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(ctypes.c_size_t)]
+        lib.paid_mlp_init.argtypes = [P, ctypes.c_uint64, P]
+        lib.paid_mlp_features.argtypes = [P, I, I, P, I, P, D, P, P]
+        lib.paid_mlp_forward.argtypes = [P, P, I64, P, P, ctypes.c_size_t, P]
+        lib.paid_mlp_grad.argtypes = [P, P, P, I64, P, P, P, ctypes.c_size_t, P]
+        lib.paid_mlp_adamw.argtypes = [P, P, P, P, I, ctypes.c_float, ctypes.c_float, P]
         _lib = lib
         return lib
 
@@ -201,6 +215,45 @@ class Context:
         """Device-resident batches: a list of dicts with keys kind, T, q (cuda
         float64 [nq, 2]), lm (cuda int32 [npairs, 2]), rel_tol, abs_tol,
         max_regions.  Returns one Result of cuda tensors per batch."""
+        return self._integrate(batches, pool_capacity, stream, None)
+
+    def integrate_multi_seeded(self, batches, proposal=None, rate=2.0, pool_capacity=None,
+                               stream=None):
+        """As integrate_multi, with the initial partition from proposal maps
+        (cuda float32 [n, 256], global batch order; None = uniform level 4)."""
+        return self._integrate(batches, pool_capacity, stream, (proposal, float(rate)))
+
+    def cell_errors(self, kind, q, lm, T, stream=None):
+        """Relative log10 error maps of the uniform level-4 grid: cuda float32 [n, 256]."""
+        torch = _torch()
+        n = q.shape[0] * lm.shape[0]
+        out = torch.empty((n, 256), dtype=torch.float32, device=self.torch_device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.torch_device)
+        ws = self.workspace(n, n * 256)
+        rc = self._lib.paid_cell_errors(self._h, int(kind), q.shape[0], q.data_ptr(), lm.shape[0],
+                                        lm.data_ptr(), float(T), out.data_ptr(),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                        ctypes.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, self.last_error())
+        return out
+
+    def features(self, kind, q, lm, T, stream=None):
+        """Proposal inputs of one batch: cuda bfloat16 [n, 32]."""
+        torch = _torch()
+        n = q.shape[0] * lm.shape[0]
+        x = torch.empty((n, 32), dtype=torch.bfloat16, device=self.torch_device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.torch_device)
+        rc = self._lib.paid_mlp_features(self._h, int(kind), q.shape[0], q.data_ptr(), lm.shape[0],
+                                         lm.data_ptr(), float(T), x.data_ptr(),
+                                         ctypes.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_mlp_features")
+        return x
+
+    def _integrate(self, batches, pool_capacity, stream, seeded):
         torch = _torch()
         dev = self.torch_device
         arr = (paid_batch * max(1, len(batches)))()
@@ -233,9 +286,19 @@ class Context:
         cap = pool_capacity or self.default_capacity(n, maxr)
         while True:
             ws = self.workspace(n, cap)
-            rc = self._lib.paid_integrate_multi(self._h, arr, len(batches),
-                                                ctypes.c_void_p(ws.data_ptr()), ws.numel(),
-                                                ctypes.c_void_p(stream.cuda_stream))
+            if seeded is None:
+                rc = self._lib.paid_integrate_multi(self._h, arr, len(batches),
+                                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                    ctypes.c_void_p(stream.cuda_stream))
+            else:
+                prop, rate = seeded
+                if prop is not None and (prop.dtype != torch.float32 or prop.shape != (n, 256)
+                                         or not prop.is_contiguous()):
+                    raise ValueError("proposal must be contiguous float32 [n, 256]")
+                rc = self._lib.paid_integrate_multi_seeded(
+                    self._h, arr, len(batches), prop.data_ptr() if prop is not None else None,
+                    rate, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                    ctypes.c_void_p(stream.cuda_stream))
             if rc == ERR_POOL and pool_capacity is None and cap < 2 ** 32 - 1:
                 free, _ = torch.cuda.mem_get_info(self.device)
                 bigger = min(4 * cap, self.pool_capacity(n, int(0.9 * (free + ws.numel()))),
@@ -255,9 +318,10 @@ class Context:
                                           abs_tol=abs_tol, max_regions=max_regions)],
                                     pool_capacity=pool_capacity, stream=stream)[0]
 
-    def integrate_host(self, batches, pool_capacity=None):
+    def integrate_host(self, batches, pool_capacity=None, proposal=None, rate=2.0):
         """End-to-end call on host (numpy) inputs: copies q and lm from pinned
-        host memory to the device, integrates, and copies the results back.
+        host memory to the device, integrates (seeded from `proposal`, a
+        Proposal network, when given), and copies the results back.
         Returns (list of numpy Result, bytes host->device, bytes device->host)."""
         torch = _torch()
         dev = self.torch_device
@@ -271,7 +335,13 @@ class Context:
             d["lm"] = lh.to(dev, non_blocking=True)
             h2d += qh.numel() * 8 + lh.numel() * 4
             dbs.append(d)
-        outs = self.integrate_multi(dbs, pool_capacity=pool_capacity, stream=stream)
+        if proposal is None:
+            outs = self.integrate_multi(dbs, pool_capacity=pool_capacity, stream=stream)
+        else:
+            x = torch.cat([self.features(b["kind"], b["q"], b["lm"], b["T"], stream) for b in dbs])
+            maps = proposal.forward(x, stream)
+            outs = self.integrate_multi_seeded(dbs, maps, rate, pool_capacity=pool_capacity,
+                                               stream=stream)
         res, d2h = [], 0
         for r in outs:
             hv = [t.to("cpu", non_blocking=False).numpy() for t in
@@ -312,3 +382,106 @@ class Context:
         if rc not in (OK, ERR_TIMEOUT, ERR_POOL):
             raise PaidError(rc, error_string(rc))
         return r
+
+
+class Proposal:
+    """The refinement-proposal network on the device: FP32 master parameters,
+    AdamW moments, and the library's BF16 tensor-core kernels for the forward
+    pass, the MSE gradient and the update."""
+
+    def __init__(self, device=0, seed=0, params=None):
+        torch = _torch()
+        self._lib = load()
+        self.device = torch.device("cuda", device)
+        n = ctypes.c_int64()
+        self._lib.paid_mlp_param_count(ctypes.byref(n))
+        self.n = n.value
+        self.params = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        if params is None:
+            rc = self._lib.paid_mlp_init(self.params.data_ptr(), int(seed), None)
+            if rc != OK:
+                raise PaidError(rc, "paid_mlp_init")
+        else:
+            self.params.copy_(torch.as_tensor(params, dtype=torch.float32))
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad_buf = torch.zeros_like(self.params)
+        self.loss_buf = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.step_count = 0
+        self._ws = None
+
+    def _workspace(self, M):
+        torch = _torch()
+        b = ctypes.c_size_t()
+        self._lib.paid_mlp_workspace_size(int(M), ctypes.byref(b))
+        if self._ws is None or self._ws.numel() < b.value:
+            self._ws = None
+            self._ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def forward(self, x, stream=None):
+        torch = _torch()
+        M = x.shape[0]
+        out = torch.empty((M, 256), dtype=torch.float32, device=self.device)
+        if M == 0:
+            return out
+        ws = self._workspace(M)
+        s = stream or torch.cuda.current_stream(self.device)
+        rc = self._lib.paid_mlp_forward(self.params.data_ptr(), x.data_ptr(), M, out.data_ptr(),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                        ctypes.c_void_p(s.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_mlp_forward")
+        return out
+
+    def grad(self, x, target, stream=None):
+        """(grad FP32 [n_params], loss FP32 [1]) of the MSE over the rows of x."""
+        torch = _torch()
+        ws = self._workspace(x.shape[0])
+        s = stream or torch.cuda.current_stream(self.device)
+        rc = self._lib.paid_mlp_grad(self.params.data_ptr(), x.data_ptr(), target.data_ptr(),
+                                     x.shape[0], self.grad_buf.data_ptr(),
+                                     self.loss_buf.data_ptr(), ctypes.c_void_p(ws.data_ptr()),
+                                     ws.numel(), ctypes.c_void_p(s.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_mlp_grad")
+        return self.grad_buf, self.loss_buf
+
+    def step(self, x, target, lr=1e-3, weight_decay=1e-4, stream=None):
+        torch = _torch()
+        self.grad(x, target, stream)
+        self.step_count += 1
+        s = stream or torch.cuda.current_stream(self.device)
+        rc = self._lib.paid_mlp_adamw(self.params.data_ptr(), self.grad_buf.data_ptr(),
+                                      self.m.data_ptr(), self.v.data_ptr(), self.step_count,
+                                      float(lr), float(weight_decay), ctypes.c_void_p(s.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_mlp_adamw")
+        return self.loss_buf
+
+    def train(self, x, target, epochs=10, batch=4096, lr=2e-3, weight_decay=1e-4, seed=0):
+        """Minibatch AdamW over shuffled rows (cosine-decayed learning rate);
+        returns the mean loss per epoch."""
+        torch = _torch()
+        gen = torch.Generator(device="cpu").manual_seed(seed)
+        M = x.shape[0]
+        steps = epochs * ((M + batch - 1) // batch)
+        k = 0
+        hist = []
+        for _ in range(epochs):
+            perm = torch.randperm(M, generator=gen).to(self.device)
+            tot = torch.zeros(1, device=self.device)
+            nb = 0
+            for i in range(0, M, batch):
+                idx = perm[i:i + batch]
+                xb = x.index_select(0, idx).contiguous()
+                tb = target.index_select(0, idx).contiguous()
+                a = lr * 0.5 * (1.0 + math.cos(math.pi * k / max(1, steps)))
+                tot += self.step(xb, tb, a, weight_decay)
+                k += 1
+                nb += 1
+            hist.append(float(tot.item()) / nb)
+        return hist
+
+    def state(self):
+        return self.params.detach().cpu().numpy().copy()
