@@ -39,6 +39,11 @@ FP64_FLOPS_PER_NODE = (2 * 4117 + 736 + 1242) / 81.0
 # DRAM bytes per evaluated region of the same kernel (same capture): eval-list
 # entry and key read, Q_2N and err written.
 EVAL_DRAM_BYTES_PER_REGION = 18.3
+# FP32 flops per region of the float-float evaluation kernel (k_eval_df, N = 4):
+# FFMA counted as 2, FADD / FMUL as 1, from ncu instruction counters over all
+# launches of a run divided by the regions that kernel evaluated
+# (profiles/k_eval_df_first_shell.md).
+DF_FP32_FLOPS_PER_REGION = 2 * 7774.8 + 29243.1 + 3018.3   # 47,811
 
 
 def parse_args():
@@ -298,7 +303,9 @@ def run_paid(args):
         return ctx.integrate_multi_seeded(dbs, maps, rate, stream=stream)
 
     for _ in range(args.warmup):
-        step()
+        outs = step()
+    # the per-step bookkeeping below uses torch kernels that load on first use
+    int((torch.cat([o.status for o in outs]) == 0).sum())
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -308,23 +315,27 @@ def run_paid(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = dict(conv=0, budget=0, region_evals=0, node_evals=0, launches=0, eval_launches=0,
-               eval_ms=0.0, reduce_ms=0.0, scan_ms=0.0, split_ms=0.0, rounds=0, peak_pool=0)
+               eval_ms=0.0, reduce_ms=0.0, scan_ms=0.0, split_ms=0.0, rounds=0, peak_pool=0,
+               df_ms=0.0, df_regions=0, escalated=0)
     ev0.record(stream)
-    outs = None
+    step_outs, step_stats = [], []
     for _ in range(args.steps):
-        outs = step()
-        st = ctx.last_stats()
-        s = torch.cat([o.status for o in outs])
-        agg["conv"] += int((s == 0).sum())
-        agg["budget"] += int((s == 1).sum())
-        for k in ("region_evals", "node_evals", "launches", "eval_launches", "eval_ms",
-                  "reduce_ms", "scan_ms", "split_ms", "rounds"):
-            agg[k] += st[k]
-        agg["peak_pool"] = max(agg["peak_pool"], st["peak_pool"])
+        step_outs.append(step())
+        step_stats.append(ctx.last_stats())
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    for outs, st in zip(step_outs, step_stats):
+        s = torch.cat([o.status for o in outs])
+        agg["conv"] += int((s == 0).sum())
+        agg["budget"] += int((s == 1).sum())
+        for k in ("region_evals", "node_evals", "launches", "eval_launches", "eval_ms",
+                  "reduce_ms", "scan_ms", "split_ms", "rounds", "df_ms", "df_regions",
+                  "escalated"):
+            agg[k] += st[k]
+        agg["peak_pool"] = max(agg["peak_pool"], st["peak_pool"])
+    outs = step_outs[-1]
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     if dist:
@@ -369,6 +380,16 @@ def run_paid(args):
                                 "capture of the 400-integral case (18.3 B/region)",
                 "peak_source": "measured FP64 FMA micro-benchmark in this run (pipe_peaks.cu)",
                 "flops_per_node": FP64_FLOPS_PER_NODE}
+    df_s = agg["df_ms"] / 1e3
+    if args.eval == "fp32" and DF_FP32_FLOPS_PER_REGION and df_s > 0:
+        achieved = agg["df_regions"] * DF_FP32_FLOPS_PER_REGION / df_s / 1e12
+        pk = peaks.get("fp32_fma_tflops")
+        roof = {"bound": "alu", "kernel": "k_eval_df", "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": achieved / pk if pk else None, "traffic": None,
+                "traffic_note": "compute-bound (a region is 32 bytes of pool traffic for ~10^5 flops)",
+                "peak_source": "measured FP32 FMA micro-benchmark in this run (pipe_peaks.cu)",
+                "flops_per_region": DF_FP32_FLOPS_PER_REGION,
+                "share_of_eval": df_s / max(eval_s, 1e-12)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -388,7 +409,9 @@ def run_paid(args):
         "rounds_per_step": agg["rounds"] / args.steps,
         "peak_pool_regions": agg["peak_pool"],
         "kernel_ms_per_step": {k: agg[k] / args.steps for k in
-                               ("eval_ms", "reduce_ms", "scan_ms", "split_ms")},
+                               ("eval_ms", "df_ms", "reduce_ms", "scan_ms", "split_ms")},
+        "float_float_regions_per_step": agg["df_regions"] / args.steps,
+        "escalated_integrals_per_step": agg["escalated"] / args.steps,
         "eval_launches": agg["eval_launches"],
         "pipe_peaks": peaks,
     }

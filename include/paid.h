@@ -104,8 +104,10 @@ typedef struct {
     double reduce_ms;           /* ... region evaluation, reduce + test, */
     double scan_ms;             /* ... slot scan, */
     double split_ms;            /* ... split + compaction (0 without timing) */
-    int64_t escalated;          /* eval_fp32: integrals re-evaluated in FP64 because their
-                                   rounding-noise term exceeded half their tolerance */
+    int64_t escalated;          /* eval_fp32: integrals moved to float-float evaluation because
+                                   their FP32 rounding-noise term crowded their tolerance */
+    int64_t df_regions;         /* eval_fp32: regions evaluated in float-float */
+    double df_ms;               /* with options.timing: the float-float kernel's share of eval_ms */
 } paid_stats;
 
 /* Fill *opt with the defaults.  Returns PAID_OK or PAID_ERR_ARG (opt NULL). */

@@ -30,7 +30,7 @@ struct paid_ctx {
     int nff = 9;
     paid_options opt{};
     RoundTotals* h_totals = nullptr;   // pinned
-    cudaEvent_t ev[6] = {};            // kernel-class timing (options.timing)
+    cudaEvent_t ev[7] = {};            // kernel-class timing (options.timing)
     std::string last_error;
     paid_stats stats{};
 };
@@ -353,12 +353,14 @@ int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_
         st.region_evals += n_eval;
         st.peak_pool = std::max(st.peak_pool, pool);
         if ((e = mark(0)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-        if ((e = launch_eval(w, cur, n_eval, o.rule_n, o.eval_fp32, ctx->lat, s)) != cudaSuccess)
+        if ((e = launch_eval(w, cur, n_eval, o.rule_n, o.eval_fp32, ctx->lat, s,
+                             timed && o.eval_fp32 ? ev[6] : nullptr)) != cudaSuccess)
             return cuda_fail(ctx, e, "eval");
         if ((e = mark(1)) != cudaSuccess) return cuda_fail(ctx, e, "event");
         if ((e = launch_reduce_test(w, cur, n_active, round, o.max_rounds, o.cover, s)) != cudaSuccess)
             return cuda_fail(ctx, e, "reduce_test");
         if ((e = mark(2)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+        st.launches += (o.eval_fp32 && n_eval > 0) ? 1 : 0;
         if ((e = launch_scan(w, n_active, s)) != cudaSuccess) return cuda_fail(ctx, e, "scan");
         if ((e = mark(3)) != cudaSuccess) return cuda_fail(ctx, e, "event");
         st.eval_launches += n_eval > 0 ? 1 : 0;
@@ -369,6 +371,7 @@ int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "round sync");
         if (timed) {
             st.eval_ms += span(0, 1);
+            if (o.eval_fp32 && n_eval > 0) st.df_ms += span(6, 1);
             st.reduce_ms += span(1, 2);
             st.scan_ms += span(2, 3);
             if (split_pending) st.split_ms += span(4, 5);
@@ -377,6 +380,7 @@ int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_
         const RoundTotals t = *ctx->h_totals;
         st.rounds = round + 1;
         st.escalated = int64_t(t.escalated);
+        st.df_regions = int64_t(t.df_regions);
         if (t.active == 0) {
             if (round >= o.max_rounds) rc = fail(ctx, PAID_ERR_TIMEOUT, "round cap reached");
             break;

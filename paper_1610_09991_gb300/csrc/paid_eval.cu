@@ -22,6 +22,7 @@
 // offsets, so a region costs 2 sincospi instead of 2(2N+1)^2 cos/sin.  The
 // dispersion is affine in cos ky for fixed kx, e = A(kx) + B(kx) cos ky, and
 // each form factor is X(kx)^T C Y(ky) with X = (1, cos kx, sin kx).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -40,6 +41,9 @@ __constant__ float c_wf32[2][2 * kMaxRuleN + 1];  // FP32 copies for the FP32 pa
 __constant__ float2 c_wfdf[2][2 * kMaxRuleN + 1]; // (hi, lo) pairs for the float-float path
 __constant__ float2 c_wcdf[2][kMaxRuleN + 1];
 __constant__ float2 c_exp2tab[64];                // 2^(j/64) as (hi, lo), j = 0..63
+__constant__ float2 c_codf[2][kMaxLevel + 1][kMaxRuleN + 1];  // c_co / c_so as (hi, lo)
+__constant__ float2 c_sodf[2][kMaxLevel + 1][kMaxRuleN + 1];
+__constant__ float2 c_ffdf[9][3][3];              // c_ff as (hi, lo)
 __constant__ float c_wc32[2][kMaxRuleN + 1];
 __constant__ float c_ff32[9][3][3];
 
@@ -104,7 +108,21 @@ cudaError_t init_rule_tables(int device)
         for (int i = 0; i < kMaxRuleN + 1; ++i) wcdf[v][i] = split(wc[v][i]);
     }
     for (int j = 0; j < 64; ++j) e2t[j] = split(std::exp2(j / 64.0));
+    float2 codf[2][kMaxLevel + 1][kMaxRuleN + 1], sodf[2][kMaxLevel + 1][kMaxRuleN + 1];
+    float2 ffdf[9][3][3];
+    for (int v = 0; v < 2; ++v)
+        for (int L = 0; L <= kMaxLevel; ++L)
+            for (int i = 0; i <= kMaxRuleN; ++i) {
+                codf[v][L][i] = split(co[v][L][i]);
+                sodf[v][L][i] = split(so[v][L][i]);
+            }
+    for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) ffdf[a][b][c] = split(ff[a][b][c]);
     cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(c_codf, codf, sizeof(codf))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_sodf, sodf, sizeof(sodf))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_ffdf, ffdf, sizeof(ffdf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_wfdf, wfdf, sizeof(wfdf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_wcdf, wcdf, sizeof(wcdf))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_exp2tab, e2t, sizeof(e2t))) != cudaSuccess) return e;
@@ -549,65 +567,108 @@ __device__ __forceinline__ f2 bubble_Fdf(f2 x1, f2 x2, f2 d, f2 twoT, f2 inv4T,
     return df_div(num, den);
 }
 
-template <int N, int KIND>
+// Column values of a region: cos/sin of ky and of the shifted ky (4 x NF
+// float-float numbers).  Kept in registers, or -- when ys is a shared-memory
+// slice -- at ys[(f NF + j) kYsStride] (thread-minor, bank-conflict free),
+// which frees 72 registers and lets more warps hide the latency of the
+// float-float dependency chains.
+constexpr int kYsStride = 128;   // threads per block of the float-float kernel
+
+template <int NF>
+struct YCols {
+    float2* ys;                  // shared slice, or null for registers
+    f2 r[4][NF];
+    __device__ __forceinline__ void set(int f, int j, f2 v)
+    {
+        if (ys) ys[(f * NF + j) * kYsStride] = make_float2(v.hi, v.lo);
+        else r[f][j] = v;
+    }
+    __device__ __forceinline__ f2 get(int f, int j) const
+    {
+        if (ys) { const float2 t = ys[(f * NF + j) * kYsStride]; return {t.x, t.y}; }
+        return r[f][j];
+    }
+};
+
+template <int N, int KIND, bool SMEM>
 __device__ __forceinline__ void region_trig_df(int v, uint32_t L, uint32_t ix, uint32_t iy,
                                                QTrig tq, int l, int m, const DevBatch& B,
-                                               Lattice lat, const float2* tab, double& s2,
-                                               double& s1)
+                                               Lattice lat, const float2* tab, float2* ys,
+                                               double& s2, double& s1)
 {
     constexpr int NF = 2 * N + 1;
     const double inv2T = B.inv2T;
     const f2 twoT = df_from(2.0 * B.T);
     const f2 inv4T = df_from(B.inv4T);
-    double sxc, cxc, syc, cyc;
-    sincospi(fma(double(2 * ix + 1), ldexp(1.0, -int(L)), -1.0), &sxc, &cxc);
-    sincospi(fma(double(2 * iy + 1), ldexp(1.0, -int(L)), -1.0), &syc, &cyc);
+    // FP64 only for the exact dyadic centre; rotations, energies and form
+    // factors below are float-float
+    double sxc_, cxc_, syc_, cyc_;
+    sincospi(fma(double(2 * ix + 1), ldexp(1.0, -int(L)), -1.0), &sxc_, &cxc_);
+    sincospi(fma(double(2 * iy + 1), ldexp(1.0, -int(L)), -1.0), &syc_, &cyc_);
+    const f2 cxc = df_from(cxc_), sxc = df_from(sxc_), cyc = df_from(cyc_), syc = df_from(syc_);
+    const f2 cqx = df_from(tq.cqx), sqx = df_from(tq.sqx), cqy = df_from(tq.cqy), sqy = df_from(tq.sqy);
 
-    f2 cy[NF], sy[NF], cy2[NF], sy2[NF];
+    YCols<NF> Y;
+    Y.ys = SMEM ? ys : nullptr;
 #pragma unroll
     for (int j = 0; j < NF; ++j) {
         const int jj = j <= N ? j : 2 * N - j;
-        const double co = c_co[v][L][jj];
-        const double so = j <= N ? c_so[v][L][jj] : -c_so[v][L][jj];
-        const double c = fma(cyc, co, -syc * so);
-        const double sn = fma(syc, co, cyc * so);
-        double c2, s2_;
-        if (KIND == PP) { c2 = fma(tq.cqy, c, tq.sqy * sn); s2_ = fma(tq.sqy, c, -tq.cqy * sn); }
-        else            { c2 = fma(c, tq.cqy, -sn * tq.sqy); s2_ = fma(sn, tq.cqy, c * tq.sqy); }
-        cy[j] = df_from(c);
-        sy[j] = df_from(sn);
-        cy2[j] = df_from(c2);
-        sy2[j] = df_from(s2_);
+        const f2 co = df_c(c_codf[v][L][jj]);
+        const f2 so = j <= N ? df_c(c_sodf[v][L][jj]) : df_neg(df_c(c_sodf[v][L][jj]));
+        const f2 c = df_add(df_mul(cyc, co), df_neg(df_mul(syc, so)));
+        const f2 sn = df_add(df_mul(syc, co), df_mul(cyc, so));
+        f2 c2, s2_;
+        if (KIND == PP) {   // q - k
+            c2 = df_add(df_mul(cqy, c), df_mul(sqy, sn));
+            s2_ = df_add(df_mul(sqy, c), df_neg(df_mul(cqy, sn)));
+        } else {            // k + q
+            c2 = df_add(df_mul(c, cqy), df_neg(df_mul(sn, sqy)));
+            s2_ = df_add(df_mul(sn, cqy), df_mul(c, sqy));
+        }
+        Y.set(0, j, c);
+        Y.set(1, j, sn);
+        Y.set(2, j, c2);
+        Y.set(3, j, s2_);
     }
-    const double tA = -2.0 * lat.t * inv2T, tB = -4.0 * lat.tp * inv2T, mu = lat.mu * inv2T;
+    // x = e / 2T = A(kx) + B(kx) cos ky, A = -(2t cx + mu)/2T, B = -(2t + 4t' cx)/2T
+    const f2 tA = df_from(-2.0 * lat.t * inv2T), tB = df_from(-4.0 * lat.tp * inv2T);
+    const f2 nmu = df_from(-lat.mu * inv2T);
     double fine = 0.0, coarse = 0.0;
 #pragma unroll 1
     for (int i = 0; i < NF; ++i) {
         const int ii = i <= N ? i : 2 * N - i;
-        const double co = c_co[v][L][ii];
-        const double so = i <= N ? c_so[v][L][ii] : -c_so[v][L][ii];
-        const double cx = fma(cxc, co, -sxc * so);
-        const double sx = fma(sxc, co, cxc * so);
-        double cx2, sx2;
-        if (KIND == PP) { cx2 = fma(tq.cqx, cx, tq.sqx * sx); sx2 = fma(tq.sqx, cx, -tq.cqx * sx); }
-        else            { cx2 = fma(cx, tq.cqx, -sx * tq.sqx); sx2 = fma(sx, tq.cqx, cx * tq.sqx); }
-        const f2 A1 = df_from(fma(tA, cx, -mu)), B1 = df_from(fma(tB, cx, tA));
-        const f2 A2 = df_from(fma(tA, cx2, -mu)), B2 = df_from(fma(tB, cx2, tA));
+        const f2 co = df_c(c_codf[v][L][ii]);
+        const f2 so = i <= N ? df_c(c_sodf[v][L][ii]) : df_neg(df_c(c_sodf[v][L][ii]));
+        const f2 cx = df_add(df_mul(cxc, co), df_neg(df_mul(sxc, so)));
+        const f2 sx = df_add(df_mul(sxc, co), df_mul(cxc, so));
+        f2 cx2, sx2;
+        if (KIND == PP) {
+            cx2 = df_add(df_mul(cqx, cx), df_mul(sqx, sx));
+            sx2 = df_add(df_mul(sqx, cx), df_neg(df_mul(cqx, sx)));
+        } else {
+            cx2 = df_add(df_mul(cx, cqx), df_neg(df_mul(sx, sqx)));
+            sx2 = df_add(df_mul(sx, cqx), df_mul(cx, sqx));
+        }
+        const f2 A1 = df_add(df_mul(tA, cx), nmu), B1 = df_add(df_mul(tB, cx), tA);
+        const f2 A2 = df_add(df_mul(tA, cx2), nmu), B2 = df_add(df_mul(tB, cx2), tA);
         f2 ul[3], um[3];
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            ul[b] = df_from(fma(c_ff[l][2][b], sx, fma(c_ff[l][1][b], cx, c_ff[l][0][b])));
-            um[b] = df_from(fma(c_ff[m][2][b], sx2, fma(c_ff[m][1][b], cx2, c_ff[m][0][b])));
+            ul[b] = df_add(df_add(df_mul(df_c(c_ffdf[l][1][b]), cx), df_mul(df_c(c_ffdf[l][2][b]), sx)),
+                           df_c(c_ffdf[l][0][b]));
+            um[b] = df_add(df_add(df_mul(df_c(c_ffdf[m][1][b]), cx2), df_mul(df_c(c_ffdf[m][2][b]), sx2)),
+                           df_c(c_ffdf[m][0][b]));
         }
         f2 rf = {0.0f, 0.0f}, rc = {0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < NF; ++j) {
-            const f2 x1 = df_add(df_mul(B1, cy[j]), A1);
-            f2 x2 = df_add(df_mul(B2, cy2[j]), A2);
+            const f2 cyj = Y.get(0, j), syj = Y.get(1, j), cy2j = Y.get(2, j), sy2j = Y.get(3, j);
+            const f2 x1 = df_add(df_mul(B1, cyj), A1);
+            f2 x2 = df_add(df_mul(B2, cy2j), A2);
             if (KIND == PP) x2 = df_neg(x2);
             const f2 F = bubble_Fdf(x1, x2, df_add(x1, df_neg(x2)), twoT, inv4T, tab);
-            const f2 fl = df_add(df_add(df_mul(ul[1], cy[j]), df_mul(ul[2], sy[j])), ul[0]);
-            const f2 fm = df_add(df_add(df_mul(um[1], cy2[j]), df_mul(um[2], sy2[j])), um[0]);
+            const f2 fl = df_add(df_add(df_mul(ul[1], cyj), df_mul(ul[2], syj)), ul[0]);
+            const f2 fm = df_add(df_add(df_mul(um[1], cy2j), df_mul(um[2], sy2j)), um[0]);
             const f2 g = df_mul(df_mul(fl, fm), F);
             rf = df_add(rf, df_mul(df_c(c_wfdf[v][j]), g));
             if ((j & 1) == 0) rc = df_add(rc, df_mul(df_c(c_wcdf[v][j >> 1]), g));
@@ -619,22 +680,72 @@ __device__ __forceinline__ void region_trig_df(int v, uint32_t L, uint32_t ix, u
     s1 = coarse;
 }
 
-// Mixed-precision evaluation: PH / PP regions use the FP32 path, or the
-// float-float path once their integral has been escalated; integrals set to
+// PH / PP regions of integrals escalated to float-float (and not set to FP64).
+__device__ __forceinline__ bool is_df_region(uint32_t mt)
+{
+    const int kind = meta_kind(mt);
+    return meta_valid(mt) && (mt & kMetaDf32) != 0u && (mt & kMetaFp64) == 0u &&
+           (kind == PH || kind == PP);
+}
+
+// Float-float evaluation kernel: one region per thread, the column values in
+// a shared-memory slice per thread (N = 4) so that three 128-thread blocks fit
+// per SM without spills.
+template <int N>
+__global__ void __launch_bounds__(kYsStride, N == 4 ? 3 : 1)
+k_eval_df(Work w, int cur, int64_t n_eval, Lattice lat)
+{
+    constexpr bool SMEM = N == 4;
+    constexpr int NF = 2 * N + 1;
+    const int v = N == 4 ? 0 : 1;
+    __shared__ float2 tab[64];
+    __shared__ float2 ysm[SMEM ? 4 * NF * kYsStride : 1];
+    if (threadIdx.x < 64) tab[threadIdx.x] = c_exp2tab[threadIdx.x];
+    __syncthreads();
+    float2* ys = SMEM ? ysm + threadIdx.x : nullptr;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    unsigned count = 0;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_eval; t += stride) {
+        const uint2 e = w.evl[t];
+        const uint32_t pos = e.x, g = e.y;
+        const uint32_t mt = w.meta[g];
+        if (!is_df_region(mt)) continue;
+        ++count;
+        const uint64_t key = w.key[cur][pos];
+        const DevBatch& B = w.batches[meta_batch(mt)];
+        const uint32_t L = key_level(key), ix = key_ix(key), iy = key_iy(key);
+        const QTrig tq = w.trig[g];
+        const int l = meta_l(mt), m = meta_m(mt);
+        double s2, s1;
+        if (meta_kind(mt) == PH)
+            region_trig_df<N, PH, SMEM>(v, L, ix, iy, tq, l, m, B, lat, tab, ys, s2, s1);
+        else
+            region_trig_df<N, PP, SMEM>(v, L, ix, iy, tq, l, m, B, lat, tab, ys, s2, s1);
+        const double scale = ldexp(0.25, -2 * int(L));
+        const double q2 = s2 * scale, q1 = s1 * scale;
+        w.val[cur][pos] = q2;
+        w.err[cur][pos] = fabs(q1 - q2);
+        w.nse[cur][pos] = 0.0f;   // ~2^-44 relative: below every accepted tolerance
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
+    if ((threadIdx.x & 31) == 0 && count) atomicAdd(&w.totals->df_regions, (unsigned long long)count);
+}
+
+// Mixed-precision evaluation: PH / PP regions use the FP32 path (regions of
+// integrals escalated to float-float are left to k_eval_df); integrals set to
 // FP64 and the test kinds use the FP64 path.
 template <int N>
 __global__ void __launch_bounds__(128) k_eval_fp32(Work w, int cur, int64_t n_eval, Lattice lat)
 {
     const int v = N == 4 ? 0 : 1;
-    __shared__ float2 tab[64];
-    if (threadIdx.x < 64) tab[threadIdx.x] = c_exp2tab[threadIdx.x];
-    __syncthreads();
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_eval; t += stride) {
         const uint2 e = w.evl[t];
         const uint32_t pos = e.x, g = e.y;
-        const uint64_t key = w.key[cur][pos];
         const uint32_t mt = w.meta[g];
+        if (is_df_region(mt)) continue;   // evaluated by k_eval_df
+        const uint64_t key = w.key[cur][pos];
         const DevBatch& B = w.batches[meta_batch(mt)];
         const uint32_t L = key_level(key), ix = key_ix(key), iy = key_iy(key);
         const int kind = meta_kind(mt);
@@ -644,12 +755,7 @@ __global__ void __launch_bounds__(128) k_eval_fp32(Work w, int cur, int64_t n_ev
             const QTrig tq = w.trig[g];
             const int l = meta_l(mt), m = meta_m(mt);
             const bool fp64 = (mt & kMetaFp64) != 0u;
-            const bool dfp = (mt & kMetaDf32) != 0u;
-            if (kind == PH && !fp64 && dfp)
-                region_trig_df<N, PH>(v, L, ix, iy, tq, l, m, B, lat, tab, s2, s1);
-            else if (kind == PP && !fp64 && dfp)
-                region_trig_df<N, PP>(v, L, ix, iy, tq, l, m, B, lat, tab, s2, s1);
-            else if (kind == PH && !fp64)
+            if (kind == PH && !fp64)
                 region_trig_fp32<N, PH>(v, L, ix, iy, tq, l, m, B, lat, s2, s1, nz);
             else if (kind == PP && !fp64)
                 region_trig_fp32<N, PP>(v, L, ix, iy, tq, l, m, B, lat, s2, s1, nz);
@@ -707,15 +813,22 @@ __global__ void __launch_bounds__(128) k_eval_fp64(Work w, int cur, int64_t n_ev
 }
 
 cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
-                        Lattice lat, cudaStream_t s)
+                        Lattice lat, cudaStream_t s, cudaEvent_t mid)
 {
     if (n_eval <= 0) return cudaSuccess;
     const int threads = 128;
     int64_t blocks = (n_eval + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (fp32) {
+        const int dblocks = int(std::min<int64_t>((n_eval + kYsStride - 1) / kYsStride, 152 * 48));
         if (rule_n == 4) k_eval_fp32<4><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
         else             k_eval_fp32<6><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+        if (mid) {
+            const cudaError_t e = cudaEventRecord(mid, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (rule_n == 4) k_eval_df<4><<<dblocks, kYsStride, 0, s>>>(w, cur, n_eval, lat);
+        else             k_eval_df<6><<<dblocks, kYsStride, 0, s>>>(w, cur, n_eval, lat);
     } else {
         if (rule_n == 4) k_eval_fp64<4><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
         else             k_eval_fp64<6><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);

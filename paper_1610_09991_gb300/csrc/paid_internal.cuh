@@ -31,7 +31,12 @@ constexpr int kMaxMonomialDegree = 30;
 // (plus |x1| + |x2| for the rounding of the energies), and the multiple of the
 // rms noise treated as irreducible by refinement; see paid_eval.cu.
 constexpr float kNoiseUlps = 4.0f;
-constexpr double kNoiseSigmas = 3.0;
+// An FP32 integral moves to float-float evaluation when kNoiseSigmas * sum(nse)
+// exceeds kNoiseTol * tol.  Measured against float-float values the FP32 error
+// of Q_N - Q_2N is 0.11 nse at the median and 0.59 nse at the 99th percentile,
+// so at the threshold the noise left inside the error sum is ~0.2 tol.
+constexpr double kNoiseSigmas = 1.0;
+constexpr double kNoiseTol = 2.0;
 // threshold-bin marker in thr[].x: re-evaluate every region in FP64
 constexpr uint32_t kEscalate = 0xfeu;
 
@@ -92,7 +97,9 @@ struct RoundTotals {
     unsigned long long pool;    // regions in the next pool
     unsigned long long eval;    // regions to evaluate next round
     unsigned long long active;  // integrals still refining
-    unsigned long long escalated;  // integrals moved from FP32 to FP64 evaluation (cumulative)
+    unsigned long long escalated;  // integrals moved from FP32 to float-float evaluation (cumulative)
+    unsigned long long df_regions; // regions evaluated in float-float (cumulative)
+    unsigned long long pad[3];
 };
 
 // Pointers into the workspace.
@@ -126,8 +133,10 @@ struct Work {
 // ---- host-side launch wrappers (defined in the .cu files) -----------------
 // paid_eval.cu
 cudaError_t init_rule_tables(int device);
+// fp32 = 1: the FP32 / FP64 kernel, then the float-float kernel; `mid`, when
+// given, is recorded between the two
 cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
-                        Lattice lat, cudaStream_t s);
+                        Lattice lat, cudaStream_t s, cudaEvent_t mid = nullptr);
 // paid_pool.cu
 // L0 < 0: descriptors only (the partition comes from launch_seed)
 cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s);

@@ -104,7 +104,10 @@ __global__ void k_setup(Work w, int L0, int nff, int fp64, int write_regions)
     }
     w.active[0][g] = uint32_t(g);
     B.status[local] = RUNNING;
-    if (g == 0) w.totals->escalated = 0ull;
+    if (g == 0) {
+        w.totals->escalated = 0ull;
+        w.totals->df_regions = 0ull;
+    }
 }
 
 cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s)
@@ -341,9 +344,9 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
     else if (!isfinite(V) || !isfinite(E)) st = NONFINITE;
     else if (E <= tol) st = CONVERGED;
     else if (round >= max_rounds) st = ROUNDCAP;
-    else if (fp32 && noise > 0.25 * tol) {
-        // FP32 rounding noise alone would use a quarter of the tolerance:
-        // refinement cannot remove it, so re-evaluate at higher precision
+    else if (fp32 && noise > kNoiseTol * tol) {
+        // FP32 rounding noise would crowd the tolerance, and refinement does
+        // not shrink it: re-evaluate at higher precision
         if (lane == 0) {
             w.thr[s] = make_uint2(kEscalate, 0u);
             w.cnt_new[s] = cnt;

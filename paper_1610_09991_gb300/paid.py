@@ -47,7 +47,8 @@ class paid_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("eval_launches", ctypes.c_int64),
                 ("eval_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
                 ("scan_ms", ctypes.c_double), ("split_ms", ctypes.c_double),
-                ("escalated", ctypes.c_int64)]
+                ("escalated", ctypes.c_int64), ("df_regions", ctypes.c_int64),
+                ("df_ms", ctypes.c_double)]
 
 
 class paid_batch(ctypes.Structure):
