@@ -40,6 +40,12 @@
  *   - Output order of a batch: idx = iq * npairs + ip.
  *   - The integrate calls run their round loop from the host and return when
  *     the outputs are complete (they synchronise `stream`).
+ *   - The region pool need not hold every integral at once: integrals enter
+ *     it as room frees up, and when a round's splits would overflow it the
+ *     integrals split in order while the growth fits and the rest wait a
+ *     round.  Only a pool that
+ *     cannot make progress at all returns PAID_ERR_POOL (status PAID_POOL on
+ *     the integrals it could not finish, NaN values for those never started).
  */
 #ifndef PAID_H
 #define PAID_H
@@ -108,6 +114,7 @@ typedef struct {
                                    their FP32 rounding-noise term crowded their tolerance */
     int64_t df_regions;         /* eval_fp32: regions evaluated in float-float */
     double df_ms;               /* with options.timing: the float-float kernel's share of eval_ms */
+    int64_t throttled_rounds;   /* rounds in which some integrals waited (pool pressure) */
 } paid_stats;
 
 /* Fill *opt with the defaults.  Returns PAID_OK or PAID_ERR_ARG (opt NULL). */

@@ -44,7 +44,7 @@ constexpr int64_t kMaxCapacity = int64_t(0xffffffffu);
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t batches, totals, trig, meta, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
+    size_t batches, totals, trig, meta, born, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
         thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
         err0, err1, nse0, nse1, evl, end;
 };
@@ -60,6 +60,7 @@ Layout layout(int64_t n, int64_t cap)
     L.totals = take(sizeof(RoundTotals));
     L.trig = take(sizeof(QTrig) * n);
     L.meta = take(4 * n);
+    L.born = take(4 * n);
     L.seg_base = take(4 * n);
     L.seg_count = take(4 * n);
     L.active0 = take(4 * n);
@@ -97,6 +98,7 @@ Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb)
     w.totals = reinterpret_cast<RoundTotals*>(base + L.totals);
     w.trig = reinterpret_cast<QTrig*>(base + L.trig);
     w.meta = reinterpret_cast<uint32_t*>(base + L.meta);
+    w.born = reinterpret_cast<uint32_t*>(base + L.born);
     w.seg_base = reinterpret_cast<uint32_t*>(base + L.seg_base);
     w.seg_count = reinterpret_cast<uint32_t*>(base + L.seg_count);
     w.active[0] = reinterpret_cast<uint32_t*>(base + L.active0);
@@ -332,18 +334,31 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
 }
 
 // The refinement loop of Listing 5 from a partition already on the eval list.
-int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_eval,
-               int64_t pool, cudaStream_t s)
+// Integrals [0, admitted) are in the pool; with L0 >= 0 the rest are admitted
+// (uniform level-L0 start) as room frees up.  In a round whose splits would
+// overflow the pool, integrals split in slot order while the growth fits and
+// the rest wait a round unsplit; only a round that can neither grow nor
+// retire anything ends the call with PAID_ERR_POOL.
+int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_total, int64_t admitted,
+               int64_t n_active, int64_t n_eval, int64_t pool, int L0, cudaStream_t s)
 {
     const paid_options& o = ctx->opt;
     cudaError_t e;
     const int nodes = (2 * o.rule_n + 1) * (2 * o.rule_n + 1);
+    const int64_t n0 = L0 >= 0 ? (int64_t(1) << (2 * L0)) : 16;
     const bool timed = o.timing != 0;
     cudaEvent_t* ev = ctx->ev;
     auto mark = [&](int i) { return timed ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     auto span = [&](int a, int b) {
         float ms = 0.f;
         return (timed && cudaEventElapsedTime(&ms, ev[a], ev[b]) == cudaSuccess) ? double(ms) : 0.0;
+    };
+    auto read_totals = [&](RoundTotals& t) -> cudaError_t {
+        cudaError_t r = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
+                                        cudaMemcpyDeviceToHost, s);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+        t = *ctx->h_totals;
+        return r;
     };
     paid_stats& st = ctx->stats;
     int cur = 0;
@@ -365,10 +380,8 @@ int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_
         if ((e = mark(3)) != cudaSuccess) return cuda_fail(ctx, e, "event");
         st.eval_launches += n_eval > 0 ? 1 : 0;
         st.launches += (n_eval > 0 ? 1 : 0) + 1 + (n_active > 0 ? 2 : 1);
-        if ((e = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
-                                 cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-            return cuda_fail(ctx, e, "totals");
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "round sync");
+        RoundTotals t;
+        if ((e = read_totals(t)) != cudaSuccess) return cuda_fail(ctx, e, "round sync");
         if (timed) {
             st.eval_ms += span(0, 1);
             if (o.eval_fp32 && n_eval > 0) st.df_ms += span(6, 1);
@@ -377,18 +390,34 @@ int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_
             if (split_pending) st.split_ms += span(4, 5);
         }
         split_pending = false;
-        const RoundTotals t = *ctx->h_totals;
+        // pool pressure: integrals split in slot order while the growth fits;
+        // the rest keep their regions this round
+        bool throttled = false;
+        if (int64_t(t.pool) > cap) {
+            const unsigned long long room = (unsigned long long)(cap - pool);
+            if ((e = launch_throttle(w, n_active, room, s)) != cudaSuccess ||
+                (e = launch_scan(w, n_active, s)) != cudaSuccess ||
+                (e = read_totals(t)) != cudaSuccess)
+                return cuda_fail(ctx, e, "throttle");
+            st.launches += 3;
+            ++st.throttled_rounds;
+            throttled = true;
+        }
         st.rounds = round + 1;
         st.escalated = int64_t(t.escalated);
         st.df_regions = int64_t(t.df_regions);
-        if (t.active == 0) {
-            if (round >= o.max_rounds) rc = fail(ctx, PAID_ERR_TIMEOUT, "round cap reached");
+        // throttled to no growth, nothing retired, nothing to evaluate: no progress
+        const bool stuck = int64_t(t.pool) > cap ||
+                           (throttled && int64_t(t.active) == n_active && int64_t(t.eval) == 0);
+        if (t.active == 0 && admitted == n_total) {
+            if (t.roundcap > 0) rc = fail(ctx, PAID_ERR_TIMEOUT, "round cap reached");
             break;
         }
-        if (int64_t(t.pool) > cap) {
-            if ((e = launch_finalize(w, cur, n_active, POOL, s)) != cudaSuccess)
+        if (stuck) {
+            if ((e = launch_finalize(w, cur, n_active, POOL, s)) != cudaSuccess ||
+                (e = launch_mark_unadmitted(w, admitted, n_total, POOL, s)) != cudaSuccess)
                 return cuda_fail(ctx, e, "finalize");
-            st.launches += 1;
+            st.launches += 2;
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "finalize sync");
             rc = fail(ctx, PAID_ERR_POOL, "region pool full (capacity " + std::to_string(cap) + ")");
             break;
@@ -401,6 +430,30 @@ int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_active, int64_t n_
         n_active = int64_t(t.active);
         n_eval = int64_t(t.eval);
         pool = int64_t(t.pool);
+        // streaming admission: more integrals while the pool is under half full
+        if (admitted < n_total && L0 >= 0) {
+            const int64_t est = std::max<int64_t>(16 * n0, 4 * (pool / std::max<int64_t>(1, n_active)));
+            int64_t c = cap / 2 > pool ? (cap / 2 - pool) / est : 0;
+            if (n_active == 0) c = std::max<int64_t>(c, 1);
+            c = std::min(c, n_total - admitted);
+            c = std::min(c, (cap - pool) / n0);
+            if (c > 0) {
+                if ((e = launch_setup(w, L0, ctx->nff, o.eval_fp32 ? 0 : 1, s, admitted, admitted + c,
+                                      cur ^ 1, (unsigned long long)pool, (unsigned long long)n_eval,
+                                      (unsigned long long)n_active, round + 1)) != cudaSuccess)
+                    return cuda_fail(ctx, e, "admit");
+                st.launches += 1;
+                admitted += c;
+                n_active += c;
+                n_eval += c * n0;
+                pool += c * n0;
+            } else if (n_active == 0) {
+                if ((e = launch_mark_unadmitted(w, admitted, n_total, POOL, s)) != cudaSuccess)
+                    return cuda_fail(ctx, e, "finalize");
+                rc = fail(ctx, PAID_ERR_POOL, "region pool too small for one integral's start");
+                break;
+            }
+        }
         cur ^= 1;
     }
     st.node_evals = st.region_evals * nodes;
@@ -422,13 +475,18 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
     DeviceGuard guard(ctx->device);
     Work w{};
     int64_t n = 0, cap = 0;
-    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, n0, s, w, n, cap);
+    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 1, s, w, n, cap);
     if (rc != PAID_OK || n == 0) return rc;
+    if (cap < n0) return fail(ctx, PAID_ERR_OOM, "workspace too small for one integral's start");
+    // first admission: as many integrals as the pool can take at ~16k regions
+    // each (all of them when the pool is large), the rest stream in later
+    int64_t a = std::max<int64_t>(1, std::min(n, cap / (2 * std::max<int64_t>(16384, 16 * n0))));
+    a = std::min(a, cap / n0);
     cudaError_t e;
-    if ((e = launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess)
+    if ((e = launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s, 0, a)) != cudaSuccess)
         return cuda_fail(ctx, e, "setup");
     ctx->stats.launches = 1;
-    return run_rounds(ctx, w, cap, n, n * n0, n * n0, s);
+    return run_rounds(ctx, w, cap, n, a, a, a * n0, a * n0, o.init_level, s);
 }
 
 int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb,
@@ -458,7 +516,7 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
         return fail(ctx, PAID_ERR_OOM, "workspace too small for the seeded partition");
     if ((e = launch_seed(w, proposal, rate, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
     ctx->stats.launches = 5;
-    return run_rounds(ctx, w, cap, n, int64_t(t.eval), int64_t(t.pool), s);
+    return run_rounds(ctx, w, cap, n, n, n, int64_t(t.eval), int64_t(t.pool), -1, s);
 }
 
 int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
@@ -659,14 +717,28 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
                             s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return PAID_ERR_CUDA;
-        const RoundTotals t = *ctx->h_totals;
+        RoundTotals t = *ctx->h_totals;
+        bool throttled = false;
+        if (int64_t(t.pool) > cap) {   // integrals split in order while the growth fits
+            if (launch_throttle(w, n_active, (unsigned long long)(cap - pool), s) != cudaSuccess ||
+                launch_scan(w, n_active, s) != cudaSuccess ||
+                cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return PAID_ERR_CUDA;
+            t = *ctx->h_totals;
+            st.launches += 3;
+            ++st.throttled_rounds;
+            throttled = true;
+        }
         st.rounds = round + 1;
         st.escalated = int64_t(t.escalated);
         if (t.active == 0) {
-            if (round >= o.max_rounds) rc = PAID_ERR_TIMEOUT;
+            if (t.roundcap > 0) rc = PAID_ERR_TIMEOUT;
             break;
         }
-        if (int64_t(t.pool) > cap) {
+        if (int64_t(t.pool) > cap ||
+            (throttled && int64_t(t.active) == n_active && int64_t(t.eval) == 0)) {
             if (launch_finalize(w, cur, n_active, POOL, s) != cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess)
                 return PAID_ERR_CUDA;

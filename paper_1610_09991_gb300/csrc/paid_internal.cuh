@@ -99,7 +99,8 @@ struct RoundTotals {
     unsigned long long active;  // integrals still refining
     unsigned long long escalated;  // integrals moved from FP32 to float-float evaluation (cumulative)
     unsigned long long df_regions; // regions evaluated in float-float (cumulative)
-    unsigned long long pad[3];
+    unsigned long long roundcap;   // integrals ended by the round cap (cumulative)
+    unsigned long long pad[2];
 };
 
 // Pointers into the workspace.
@@ -110,6 +111,7 @@ struct Work {
     int64_t cap;               // pool capacity (regions)
     QTrig* trig;
     uint32_t* meta;
+    uint32_t* born;            // per integral: the round it entered the pool
     uint32_t* seg_base;
     uint32_t* seg_count;
     uint32_t* active[2];
@@ -138,8 +140,13 @@ cudaError_t init_rule_tables(int device);
 cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
                         Lattice lat, cudaStream_t s, cudaEvent_t mid = nullptr);
 // paid_pool.cu
-// L0 < 0: descriptors only (the partition comes from launch_seed)
-cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s);
+// Integrals [g0, g1) (g1 < 0: all): descriptors and, for L0 >= 0, their uniform
+// level-L0 regions appended at the given bases of pool[buf] / eval list /
+// active[buf].  L0 < 0: descriptors only (the partition comes from launch_seed).
+cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s, int64_t g0 = 0,
+                         int64_t g1 = -1, int buf = 0, unsigned long long pool_base = 0,
+                         unsigned long long eval_base = 0, unsigned long long act_base = 0,
+                         int round = 0);
 // pass 0: region counts into cnt_new / cnt_eval (slot = integral); pass 1 (after
 // launch_scan): keys, eval list, segments.  proposal null = uniform level 4.
 cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s);
@@ -151,5 +158,9 @@ cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int rou
 cudaError_t launch_scan(const Work& w, int64_t n_active, cudaStream_t s);
 cudaError_t launch_split(const Work& w, int cur, int64_t n_active, cudaStream_t s);
 cudaError_t launch_finalize(const Work& w, int cur, int64_t n_active, int status, cudaStream_t s);
+cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int status, cudaStream_t s);
+// after launch_scan: integrals past `room` regions of cumulative growth keep
+// their regions unsplit this round (re-scan afterwards)
+cudaError_t launch_throttle(const Work& w, int64_t n_active, unsigned long long room, cudaStream_t s);
 
 }  // namespace paid

@@ -64,10 +64,16 @@ __device__ __forceinline__ int log_key(double x)
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_setup(Work w, int L0, int nff, int fp64, int write_regions)
+// Integrals [g0, g1): descriptors, and (write_regions) their uniform level-L0
+// regions at pool[buf][pool_base + (g - g0) n0 ...], on the eval list from
+// eval_base and on the active list active[buf] from act_base.
+__global__ void k_setup(Work w, int64_t g0, int64_t g1, int L0, int nff, int fp64, int buf,
+                        unsigned long long pool_base, unsigned long long eval_base,
+                        unsigned long long act_base, int write_regions, int round)
 {
-    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= w.n) return;
+    const int64_t g = g0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= g1) return;
+    const int64_t i = g - g0;
     int b = 0;   // batches are sorted by `first`
     {
         int lo = 0, hi = w.nb - 1;
@@ -92,30 +98,37 @@ __global__ void k_setup(Work w, int L0, int nff, int fp64, int write_regions)
     sincos(qy, &sy, &cy);
     w.trig[g] = QTrig{cx, sx, cy, sy};
     w.meta[g] = make_meta(B.kind, valid ? l : 0, valid ? m : 0, valid, b) | (fp64 ? kMetaFp64 : 0u);
+    w.born[g] = uint32_t(round);
     if (write_regions) {
         const uint32_t side = 1u << L0, n0 = side * side;
-        const uint32_t base = uint32_t(g) * n0;
-        w.seg_base[g] = base;
+        const unsigned long long base = pool_base + (unsigned long long)(i) * n0;
+        const unsigned long long ebase = eval_base + (unsigned long long)(i) * n0;
+        w.seg_base[g] = uint32_t(base);
         w.seg_count[g] = n0;
         for (uint32_t r = 0; r < n0; ++r) {
-            w.key[0][base + r] = make_key(uint32_t(L0), r / side, r % side);
-            w.evl[base + r] = make_uint2(base + r, uint32_t(g));
+            w.key[buf][base + r] = make_key(uint32_t(L0), r / side, r % side);
+            w.evl[ebase + r] = make_uint2(uint32_t(base + r), uint32_t(g));
         }
     }
-    w.active[0][g] = uint32_t(g);
+    w.active[buf][act_base + i] = uint32_t(g);
     B.status[local] = RUNNING;
     if (g == 0) {
         w.totals->escalated = 0ull;
         w.totals->df_regions = 0ull;
+        w.totals->roundcap = 0ull;
     }
 }
 
-cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s)
+cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t s, int64_t g0,
+                         int64_t g1, int buf, unsigned long long pool_base,
+                         unsigned long long eval_base, unsigned long long act_base, int round)
 {
-    if (w.n <= 0) return cudaSuccess;
+    if (g1 < 0) g1 = w.n;
+    if (g1 <= g0) return cudaSuccess;
     const int threads = 256;
-    const int64_t blocks = (w.n + threads - 1) / threads;
-    k_setup<<<int(blocks), threads, 0, s>>>(w, L0, nff, fp64, L0 >= 0 ? 1 : 0);
+    const int64_t blocks = (g1 - g0 + threads - 1) / threads;
+    k_setup<<<int(blocks), threads, 0, s>>>(w, g0, g1, L0, nff, fp64, buf, pool_base, eval_base,
+                                            act_base, L0 >= 0 ? 1 : 0, round);
     return cudaGetLastError();
 }
 
@@ -343,7 +356,7 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
     if (force_status >= 0) st = force_status;
     else if (!isfinite(V) || !isfinite(E)) st = NONFINITE;
     else if (E <= tol) st = CONVERGED;
-    else if (round >= max_rounds) st = ROUNDCAP;
+    else if (round - int(w.born[g]) >= max_rounds) st = ROUNDCAP;   // rounds since admission
     else if (fp32 && noise > kNoiseTol * tol) {
         // FP32 rounding noise would crowd the tolerance, and refinement does
         // not shrink it: re-evaluate at higher precision
@@ -351,7 +364,6 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
             w.thr[s] = make_uint2(kEscalate, 0u);
             w.cnt_new[s] = cnt;
             w.cnt_eval[s] = cnt;
-            atomicAdd(&w.totals->escalated, 1ull);
         }
         return;
     }
@@ -364,6 +376,7 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
             B.errors[local] = E;
             B.regions[local] = cnt;
             B.status[local] = st;
+            if (st == ROUNDCAP && force_status < 0) atomicAdd(&w.totals->roundcap, 1ull);
             w.cnt_new[s] = 0;
             w.cnt_eval[s] = 0;
         }
@@ -397,13 +410,14 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
             if (cum >= target) { tb = b; break; }
         }
         uint32_t cap;
-        if (marked > allowed) {       // budget binds: whole bins while they fit
+        const int64_t lim = allowed;
+        if (marked > lim) {           // region budget binds: whole bins while they fit
             int64_t acc = 0;
             int b = 0;
-            while (b < tb && acc + hcnt[wib][b] <= allowed) { acc += hcnt[wib][b]; ++b; }
+            while (b < tb && acc + hcnt[wib][b] <= lim) { acc += hcnt[wib][b]; ++b; }
             tb = b;
-            cap = uint32_t(allowed - acc);
-            marked = allowed;
+            cap = uint32_t(lim - acc);
+            marked = lim;
         } else {
             cap = hcnt[wib][tb];
         }
@@ -420,6 +434,65 @@ cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int rou
     const int64_t blocks = (n_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, cur, n_active, round,
                                                               max_rounds, cover, -1);
+    return cudaGetLastError();
+}
+
+// Pool pressure: after the slot scan, an integral keeps its splits only while
+// the growth of all slots up to it fits in `room` regions, so the kept slots
+// form a prefix and the first integrals always progress; the others keep
+// their regions unsplit for this round.  The growth of a slot is 3/4 of its
+// eval count (4 children replace each marked region); escalated slots count
+// their full eval count there, which only makes the bound conservative.
+// With room = capacity - current pool the next pool stays within capacity.
+__global__ void k_throttle(Work w, int64_t n_active, unsigned long long room)
+{
+    const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= n_active) return;
+    const uint32_t nnew = w.cnt_new[s];
+    if (nnew == 0 || w.thr[s].x == kEscalate) return;
+    const unsigned long long evals =
+        w.blk_eval[s / kScanBlock] + w.pre_eval[s] + w.cnt_eval[s];
+    if (3ull * evals <= 4ull * room) return;
+    w.cnt_new[s] = nnew - w.cnt_eval[s] / 4u * 3u;   // current region count
+    w.cnt_eval[s] = 0;
+    // threshold bin 0 with rank cap 0 under the same kmax: every region's bin
+    // is >= 0 there, so none is marked
+    w.thr[s] = make_uint2(w.thr[s].x & ~0xffu, 0u);
+}
+
+cudaError_t launch_throttle(const Work& w, int64_t n_active, unsigned long long room, cudaStream_t s)
+{
+    if (n_active <= 0) return cudaSuccess;
+    k_throttle<<<int((n_active + 255) / 256), 256, 0, s>>>(w, n_active, room);
+    return cudaGetLastError();
+}
+
+// Integrals [g0, g1) that never entered the pool: status, NaN value and error.
+__global__ void k_mark_unadmitted(Work w, int64_t g0, int64_t g1, int status)
+{
+    const int64_t g = g0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= g1) return;
+    int b = 0;
+    {
+        int lo = 0, hi = w.nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (w.batches[mid].first <= g) lo = mid; else hi = mid - 1;
+        }
+        b = lo;
+    }
+    const DevBatch& B = w.batches[b];
+    const int64_t local = g - B.first;
+    B.values[local] = NAN;
+    B.errors[local] = NAN;
+    B.regions[local] = 0;
+    B.status[local] = status;
+}
+
+cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int status, cudaStream_t s)
+{
+    if (g1 <= g0) return cudaSuccess;
+    k_mark_unadmitted<<<int((g1 - g0 + 255) / 256), 256, 0, s>>>(w, g0, g1, status);
     return cudaGetLastError();
 }
 
@@ -584,6 +657,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w, int cur, 
         }
         if (lane == 0) {
             w.meta[g] |= kMetaDf32;
+            atomicAdd(&w.totals->escalated, 1ull);
             w.seg_base[g] = uint32_t(pbase);
             w.seg_count[g] = nnew;
             w.active[nxt][abase] = g;

@@ -48,7 +48,7 @@ class paid_stats(ctypes.Structure):
                 ("eval_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
                 ("scan_ms", ctypes.c_double), ("split_ms", ctypes.c_double),
                 ("escalated", ctypes.c_int64), ("df_regions", ctypes.c_int64),
-                ("df_ms", ctypes.c_double)]
+                ("df_ms", ctypes.c_double), ("throttled_rounds", ctypes.c_int64)]
 
 
 class paid_batch(ctypes.Structure):
@@ -206,10 +206,12 @@ class Context:
         bounded by 70 % of the device's free memory."""
         torch = _torch()
         free, _ = torch.cuda.mem_get_info(self.device)
+        # memory torch holds in its cache is available to this allocation too
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
         n0 = 4 ** self.options.init_level
         want = max(n_integrals * n0, n_integrals * max_regions)
         held = self._ws.numel() if self._ws is not None else 0
-        limit = self.pool_capacity(n_integrals, int(0.7 * (free + held)))
+        limit = self.pool_capacity(n_integrals, int(0.7 * (free + cached + held)))
         return int(max(n_integrals * n0, min(want, limit, 2 ** 32 - 1)))
 
     def integrate_multi(self, batches, pool_capacity=None, stream=None):
@@ -287,9 +289,12 @@ class Context:
         cap = pool_capacity or self.default_capacity(n, maxr)
         while True:
             ws = self.workspace(n, cap)
+            # the library sizes its pool from the bytes it is given: pass the
+            # size for `cap`, not the (possibly larger) cached workspace
+            nbytes = self.workspace_size(n, cap)
             if seeded is None:
                 rc = self._lib.paid_integrate_multi(self._h, arr, len(batches),
-                                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                    ctypes.c_void_p(ws.data_ptr()), nbytes,
                                                     ctypes.c_void_p(stream.cuda_stream))
             else:
                 prop, rate = seeded
@@ -298,7 +303,7 @@ class Context:
                     raise ValueError("proposal must be contiguous float32 [n, 256]")
                 rc = self._lib.paid_integrate_multi_seeded(
                     self._h, arr, len(batches), prop.data_ptr() if prop is not None else None,
-                    rate, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                    rate, ctypes.c_void_p(ws.data_ptr()), nbytes,
                     ctypes.c_void_p(stream.cuda_stream))
             if rc == ERR_POOL and pool_capacity is None and cap < 2 ** 32 - 1:
                 free, _ = torch.cuda.mem_get_info(self.device)

@@ -242,3 +242,43 @@ def test_host_entry_point(paid, torch):
     assert d2h == b.n * (8 + 8 + 8 + 4)
     (g,) = run_gpu(paid, torch, ctx, [b])
     assert np.array_equal(r.values, g[0])
+
+
+def test_streaming_pool_smaller_than_the_batch(paid, torch):
+    # a pool that holds ~1/3 of the batch's final regions: integrals enter as
+    # room frees up and splits are throttled, with the same results
+    b = W.Batch(W.PH, 0.2, W.q_grid_bz(4), W.all_pairs(9)[::5], 1e-6, 1e-10, 100000)
+    ctx = paid.Context(*LAT, ffset=9)
+    (g,) = run_gpu(paid, torch, ctx, [b])
+    full = ctx.last_stats()
+    dbs = [dict(kind=b.kind, T=b.T, q=_dev(torch, b.q, torch.float64),
+                lm=_dev(torch, b.lm, torch.int32), rel_tol=b.rel_tol, abs_tol=b.abs_tol,
+                max_regions=b.max_regions)]
+    (r,) = ctx.integrate_multi(dbs, pool_capacity=max(full["peak_pool"] // 3, 20000))
+    torch.cuda.synchronize()
+    st = ctx.last_stats()
+    assert ctx.last_rc == paid.OK
+    assert st["throttled_rounds"] > 0 or st["rounds"] > full["rounds"]
+    assert np.array_equal(r.status.cpu().numpy(), g[3])
+    v = r.values.cpu().numpy()
+    tol = np.maximum(1e-6 * np.abs(g[0]), 1e-10)
+    assert np.all(np.abs(v - g[0]) <= 2 * tol + 1e-12)
+
+
+def test_temperature_sweep_sampled(paid, torch):
+    # 12 temperatures from 1 down to 0.005 x 4x4 zone grid x 81 pairs x {ph, pp}
+    # (31,104 integrals of very uneven depth) in one FP64 call, against the
+    # oracle on a seeded sample
+    w = W.config_temperature_sweep(nq=4)
+    ctx = paid.Context(*w.lattice, ffset=9)
+    gs = run_gpu(paid, torch, ctx, w.batches)
+    g = tuple(np.concatenate([x[i] for x in gs]) for i in range(4))
+    flat = W.flatten(w)
+    idx = W.sample_indices(w.n, 48, seed=77)
+    o = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
+                              flat["T"][idx], LAT, 1e-6, 1e-10, 100000)
+    assert_parity(tuple(x[idx] for x in g), o, 1e-6, 1e-10, flat_ident(flat, idx))
+    assert np.all(np.isin(g[3], [0, 1]))
+    # deeper at low T: mean region count grows as T falls
+    r = g[2].reshape(12, -1).mean(axis=1)
+    assert r[-1] > 5 * r[0]
