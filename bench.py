@@ -61,6 +61,8 @@ def parse_args():
                     help="skip the timed FP64 comparison step of an FP32 run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-device-loop", action="store_true",
+                    help="skip the extra measurement with the refinement loop as one CUDA graph")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="integrals in the oracle's timed sample")
     return ap.parse_args()
@@ -420,6 +422,41 @@ def run_paid(args):
     }
     vals = torch.cat([o.values for o in outs]).cpu().numpy()
     stats = torch.cat([o.status for o in outs]).cpu().numpy()
+    if not args.no_device_loop:
+        # the same steps with the refinement loop on the device: one CUDA graph
+        # launch per call (conditional WHILE node), no per-round host sync and
+        # no per-kernel events
+        cg = P.Context(*w.lattice, ffset=ff, device=local, device_loop=1,
+                       eval_fp32=1 if args.eval == "fp32" else 0)
+
+        def gstep():
+            flush.fill_(1)
+            if prop is None:
+                return cg.integrate_multi(dbs, stream=stream)
+            maps = PR.predict(prop, ctx, dbs)
+            return cg.integrate_multi_seeded(dbs, maps, rate, stream=stream)
+
+        gstep()                                        # warm-up: workspace and graph
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        gouts, gst = [], []
+        for _ in range(args.steps):
+            gouts.append(gstep())
+            gst.append(cg.last_stats())
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tg = g0.elapsed_time(g1) / 1e3
+        gconv = sum(int((torch.cat([o.status for o in go]) == 0).sum()) for go in gouts)
+        same = all(torch.equal(torch.cat([a.values for a in go]), torch.cat([b.values for b in outs]))
+                   for go in gouts)
+        line["device_loop"] = {
+            "value": gconv * world / tg, "unit": UNIT, "ms_per_step": 1e3 * tg / args.steps,
+            "graph_launches_per_step": sum(x["graph_launches"] for x in gst) / args.steps,
+            "kernels_per_step": sum(x["launches"] for x in gst) / args.steps,
+            "rounds_per_step": sum(x["rounds"] for x in gst) / args.steps,
+            "values_identical_to_host_loop": bool(same)}
+        del cg
     if args.path != "plain" and not args.no_compare:
         # the plain FP64 GPU path on the same batch, one timed step
         c64 = P.Context(*w.lattice, ffset=ff, device=local, timing=1)

@@ -89,11 +89,16 @@ typedef struct {
     int rule_n;             /* N of the nested CC pair (coarse N, fine 2N intervals): 4 or 6. Default 4 */
     int init_level;         /* L0: initial uniform partition of D into 4^L0 regions, 0..8. Default 2 */
     int eval_fp32;          /* 1: integrand in FP32, sums in FP64. Default 0 (all FP64) */
-    int max_rounds;         /* cap on refinement rounds. Default 4096 */
+    int max_rounds;         /* cap on refinement rounds of an integral, counted from the round
+                               it entered the pool. Default 4096 */
     double cover;           /* the regions split in a round cover (E - cover * tol) of the error. Default 0.5 */
     int64_t pool_capacity;  /* regions in the pool; 0 = the most the workspace holds. Default 0 */
     int timing;             /* 1: time every kernel class with CUDA events on the call's stream
-                               (totals in paid_stats). Default 0 */
+                               (totals in paid_stats); implies device_loop = 0. Default 0 */
+    int device_loop;        /* 1: the refinement loop runs on the device as one CUDA graph launch
+                               (a conditional WHILE node around one round's kernels; the host
+                               waits once, at the end).  0: the host launches every round and
+                               reads its counts back.  Default 1 */
 } paid_options;
 
 /* Statistics of the last integrate call on a context. */
@@ -115,6 +120,7 @@ typedef struct {
     int64_t df_regions;         /* eval_fp32: regions evaluated in float-float */
     double df_ms;               /* with options.timing: the float-float kernel's share of eval_ms */
     int64_t throttled_rounds;   /* rounds in which some integrals waited (pool pressure) */
+    int64_t graph_launches;     /* device-loop graph launches (1 per call with device_loop) */
 } paid_stats;
 
 /* Fill *opt with the defaults.  Returns PAID_OK or PAID_ERR_ARG (opt NULL). */

@@ -1,15 +1,21 @@
-// C ABI of libpaid (declared in include/paid.h) and the host-side round
-// scheduler.  The scheduler drives the device loop of the paper's Listing 5:
+// C ABI of libpaid (declared in include/paid.h) and the refinement loop of
+// the paper's Listing 5:
 //
 //   setup:  uniform level-L0 partition of every integral (Listing 1)
 //   round:  evaluate the regions on the eval list (Listing 3)
 //           -> per-integral reduce + convergence test + selection (Listings 2, 4)
 //           -> prefix scan of the next pool / eval list / active list
+//              (+ in-order throttling when the next pool would not fit)
 //           -> split the selected regions and compact the pool
+//           -> control: next round's counts, admission of waiting
+//              integrals, stop decision
 //   until no integral is refining (the master's `done`, Listing 5).
 //
-// The host reads one 32-byte totals block per round (the loop's only
-// device-to-host traffic) to size the next launches and to detect a full pool.
+// Every round kernel reads its counts from the device-side loop state, so
+// the round needs no host arguments.  With options.device_loop the rounds run
+// inside one CUDA graph: a conditional WHILE node whose body is one round,
+// ended by the control kernel; the host waits once.  Otherwise the host
+// launches each round and reads the loop state back (per-phase timing).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -24,13 +30,28 @@
 
 using namespace paid;
 
+// The instantiated device-loop graph of the last call, reused while the
+// workspace layout and the options it was captured with are unchanged.
+struct LoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* base = nullptr;        // workspace layout it was captured for
+    int64_t n = 0, cap = 0;
+    int nb = 0;
+    int rule_n = 0, eval_fp32 = 0, max_rounds = 0;
+    double cover = 0.0;
+};
+
 struct paid_ctx {
     int device = 0;
     Lattice lat{};
     int nff = 9;
     paid_options opt{};
     RoundTotals* h_totals = nullptr;   // pinned
+    LoopState* h_state = nullptr;      // pinned
     cudaEvent_t ev[7] = {};            // kernel-class timing (options.timing)
+    cudaStream_t capture = nullptr;    // stream the device loop is captured on
+    LoopGraph loop;
     std::string last_error;
     paid_stats stats{};
 };
@@ -44,7 +65,7 @@ constexpr int64_t kMaxCapacity = int64_t(0xffffffffu);
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t batches, totals, trig, meta, born, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
+    size_t batches, totals, ls, trig, meta, born, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
         thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
         err0, err1, nse0, nse1, evl, end;
 };
@@ -58,6 +79,7 @@ Layout layout(int64_t n, int64_t cap)
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     L.batches = take(sizeof(DevBatch) * kMaxBatches);
     L.totals = take(sizeof(RoundTotals));
+    L.ls = take(sizeof(LoopState));
     L.trig = take(sizeof(QTrig) * n);
     L.meta = take(4 * n);
     L.born = take(4 * n);
@@ -96,6 +118,7 @@ Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb)
     w.n = n;
     w.cap = cap;
     w.totals = reinterpret_cast<RoundTotals*>(base + L.totals);
+    w.ls = reinterpret_cast<LoopState*>(base + L.ls);
     w.trig = reinterpret_cast<QTrig*>(base + L.trig);
     w.meta = reinterpret_cast<uint32_t*>(base + L.meta);
     w.born = reinterpret_cast<uint32_t*>(base + L.born);
@@ -153,6 +176,7 @@ int check_options(const paid_options& o, std::string& why)
     if (!(o.cover >= 0.0 && o.cover <= 1.0)) { why = "cover must be in [0, 1]"; return PAID_ERR_ARG; }
     if (o.pool_capacity < 0) { why = "pool_capacity must be >= 0"; return PAID_ERR_ARG; }
     if (o.timing != 0 && o.timing != 1) { why = "timing must be 0 or 1"; return PAID_ERR_ARG; }
+    if (o.device_loop != 0 && o.device_loop != 1) { why = "device_loop must be 0 or 1"; return PAID_ERR_ARG; }
     return PAID_OK;
 }
 
@@ -170,6 +194,7 @@ int paid_options_default(paid_options* opt)
     opt->cover = 0.5;
     opt->pool_capacity = 0;
     opt->timing = 0;
+    opt->device_loop = 1;
     return PAID_OK;
 }
 
@@ -211,8 +236,9 @@ int paid_create(paid_ctx** out, double t, double tp, double mu, int ffset,
     c->lat = Lattice{t, tp, mu};
     c->nff = ffset;
     c->opt = o;
-    if (cudaMallocHost(&c->h_totals, sizeof(RoundTotals)) != cudaSuccess) {
-        delete c;
+    if (cudaMallocHost(&c->h_totals, sizeof(RoundTotals)) != cudaSuccess ||
+        cudaMallocHost(&c->h_state, sizeof(LoopState)) != cudaSuccess) {
+        paid_destroy(c);
         return PAID_ERR_CUDA;
     }
     for (auto& e : c->ev) {
@@ -228,7 +254,11 @@ int paid_create(paid_ctx** out, double t, double tp, double mu, int ffset,
 void paid_destroy(paid_ctx* ctx)
 {
     if (!ctx) return;
+    if (ctx->loop.exec) cudaGraphExecDestroy(ctx->loop.exec);
+    if (ctx->loop.graph) cudaGraphDestroy(ctx->loop.graph);
+    if (ctx->capture) cudaStreamDestroy(ctx->capture);
     if (ctx->h_totals) cudaFreeHost(ctx->h_totals);
+    if (ctx->h_state) cudaFreeHost(ctx->h_state);
     for (auto e : ctx->ev)
         if (e) cudaEventDestroy(e);
     delete ctx;
@@ -333,131 +363,233 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
     return PAID_OK;
 }
 
+// Kernels of one round: evaluation, reduce + test + selection, scan,
+// throttle and rescan (both no-ops while the next pool fits), split, control;
+// inside the graph also the admission wave that control chose.  `hint_*`
+// size the grids (exact counts in the host loop, bounds in the graph).  `ev`
+// (host loop with timing) gets marks between the kernel classes.
+cudaError_t launch_round(paid_ctx* ctx, const Work& w, int64_t hint_eval, int64_t hint_active,
+                         cudaGraphConditionalHandle h, int in_graph, cudaStream_t s,
+                         cudaEvent_t* ev)
+{
+    const paid_options& o = ctx->opt;
+    auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    cudaError_t e;
+    if ((e = mark(0)) != cudaSuccess ||
+        (e = launch_eval(w, hint_eval, o.rule_n, o.eval_fp32, ctx->lat, s,
+                         ev && o.eval_fp32 ? ev[6] : nullptr)) != cudaSuccess ||
+        (e = mark(1)) != cudaSuccess ||
+        (e = launch_reduce_test(w, hint_active, o.max_rounds, o.cover, s)) != cudaSuccess ||
+        (e = mark(2)) != cudaSuccess ||
+        (e = launch_scan(w, hint_active, 0, s)) != cudaSuccess ||
+        (e = launch_throttle(w, hint_active, s)) != cudaSuccess ||
+        (e = launch_scan(w, hint_active, 1, s)) != cudaSuccess ||
+        (e = mark(3)) != cudaSuccess ||
+        (e = launch_split(w, hint_active, s)) != cudaSuccess ||
+        (e = mark(4)) != cudaSuccess ||
+        (e = launch_control(w, h, in_graph, s)) != cudaSuccess)
+        return e;
+    if (in_graph) e = launch_setup_wave(w, hint_active, ctx->nff, o.eval_fp32 ? 0 : 1, s);
+    return e;
+}
+
+// kernels one round launches (graph: every node; host loop: those with work)
+int64_t round_kernels(const paid_options& o, int64_t n_eval, int64_t n_active, bool in_graph)
+{
+    const int64_t ev = n_eval > 0 ? (o.eval_fp32 ? 2 : 1) : 0;
+    const int64_t slots = n_active > 0 ? 1 : 0;
+    // eval, reduce, scan (2), throttle, rescan (2), split, control, [wave]
+    return ev + slots + (slots + 1) + slots + (slots + 1) + slots + 1 + (in_graph ? 1 : 0);
+}
+
+// The device-loop graph for this workspace layout and these options:
+// WHILE (condition) { one round }, the condition cleared by k_control.
+int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
+{
+    const paid_options& o = ctx->opt;
+    LoopGraph& G = ctx->loop;
+    if (G.exec && G.base == w.batches && G.n == w.n && G.cap == w.cap && G.nb == w.nb &&
+        G.rule_n == o.rule_n && G.eval_fp32 == o.eval_fp32 && G.max_rounds == o.max_rounds &&
+        G.cover == o.cover) {
+        *out = G.exec;
+        return PAID_OK;
+    }
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = LoopGraph{};
+    cudaError_t e;
+    if (!ctx->capture &&
+        (e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(ctx, e, "capture stream");
+    cudaGraph_t g = nullptr;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return cuda_fail(ctx, e, "graph");
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "graph condition");
+    }
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "graph while node");
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(ctx->capture, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "graph capture");
+    }
+    const cudaError_t el = launch_round(ctx, w, w.cap, w.n, h, 1, ctx->capture, nullptr);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->capture, &captured);
+    if (el != cudaSuccess || ec != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, el != cudaSuccess ? el : ec, "graph capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "graph instantiate");
+    }
+    G.graph = g;
+    G.exec = exec;
+    G.base = w.batches;
+    G.n = w.n;
+    G.cap = w.cap;
+    G.nb = w.nb;
+    G.rule_n = o.rule_n;
+    G.eval_fp32 = o.eval_fp32;
+    G.max_rounds = o.max_rounds;
+    G.cover = o.cover;
+    *out = exec;
+    return PAID_OK;
+}
+
 // The refinement loop of Listing 5 from a partition already on the eval list.
 // Integrals [0, admitted) are in the pool; with L0 >= 0 the rest are admitted
 // (uniform level-L0 start) as room frees up.  In a round whose splits would
 // overflow the pool, integrals split in slot order while the growth fits and
 // the rest wait a round unsplit; only a round that can neither grow nor
-// retire anything ends the call with PAID_ERR_POOL.
-int run_rounds(paid_ctx* ctx, Work& w, int64_t cap, int64_t n_total, int64_t admitted,
-               int64_t n_active, int64_t n_eval, int64_t pool, int L0, cudaStream_t s)
+// retire anything ends the call with PAID_ERR_POOL.  no_alloc = true (the
+// allocation-free entry point) keeps the loop on the host, since building a
+// graph allocates, and leaves the error message alone.
+int run_loop(paid_ctx* ctx, const Work& w, int64_t admitted, int64_t n_eval, int64_t pool, int L0,
+             cudaStream_t s, bool no_alloc = false)
 {
     const paid_options& o = ctx->opt;
-    cudaError_t e;
-    const int nodes = (2 * o.rule_n + 1) * (2 * o.rule_n + 1);
-    const int64_t n0 = L0 >= 0 ? (int64_t(1) << (2 * L0)) : 16;
+    const int64_t n = w.n, cap = w.cap;
     const bool timed = o.timing != 0;
+    const bool graph = !no_alloc && o.device_loop != 0 && !timed;
+    auto cfail = [&](cudaError_t e, const char* where) {
+        return no_alloc ? int(PAID_ERR_CUDA) : cuda_fail(ctx, e, where);
+    };
+    auto rfail = [&](int rc, const char* msg) { return no_alloc ? rc : fail(ctx, rc, msg); };
+    // the loop's own bound: every integral has at most max_rounds rounds from
+    // its admission; streaming admission spreads them over more rounds
+    const int hard = admitted >= n ? o.max_rounds
+                                   : int(std::min<int64_t>(int64_t(o.max_rounds) * 64, 1 << 30));
+    paid_stats& st = ctx->stats;
     cudaEvent_t* ev = ctx->ev;
-    auto mark = [&](int i) { return timed ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     auto span = [&](int a, int b) {
         float ms = 0.f;
-        return (timed && cudaEventElapsedTime(&ms, ev[a], ev[b]) == cudaSuccess) ? double(ms) : 0.0;
+        return cudaEventElapsedTime(&ms, ev[a], ev[b]) == cudaSuccess ? double(ms) : 0.0;
     };
-    auto read_totals = [&](RoundTotals& t) -> cudaError_t {
-        cudaError_t r = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
+    auto read_state = [&](LoopState& L, RoundTotals& t) -> cudaError_t {
+        cudaError_t r = cudaMemcpyAsync(ctx->h_state, w.ls, sizeof(LoopState),
                                         cudaMemcpyDeviceToHost, s);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
+                                cudaMemcpyDeviceToHost, s);
         if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+        L = *ctx->h_state;
         t = *ctx->h_totals;
         return r;
     };
-    paid_stats& st = ctx->stats;
-    int cur = 0;
-    int rc = PAID_OK;
-    bool split_pending = false;
-    for (int round = 0;; ++round) {
-        st.region_evals += n_eval;
-        st.peak_pool = std::max(st.peak_pool, pool);
-        if ((e = mark(0)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-        if ((e = launch_eval(w, cur, n_eval, o.rule_n, o.eval_fp32, ctx->lat, s,
-                             timed && o.eval_fp32 ? ev[6] : nullptr)) != cudaSuccess)
-            return cuda_fail(ctx, e, "eval");
-        if ((e = mark(1)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-        if ((e = launch_reduce_test(w, cur, n_active, round, o.max_rounds, o.cover, s)) != cudaSuccess)
-            return cuda_fail(ctx, e, "reduce_test");
-        if ((e = mark(2)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-        st.launches += (o.eval_fp32 && n_eval > 0) ? 1 : 0;
-        if ((e = launch_scan(w, n_active, s)) != cudaSuccess) return cuda_fail(ctx, e, "scan");
-        if ((e = mark(3)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-        st.eval_launches += n_eval > 0 ? 1 : 0;
-        st.launches += (n_eval > 0 ? 1 : 0) + 1 + (n_active > 0 ? 2 : 1);
-        RoundTotals t;
-        if ((e = read_totals(t)) != cudaSuccess) return cuda_fail(ctx, e, "round sync");
-        if (timed) {
-            st.eval_ms += span(0, 1);
-            if (o.eval_fp32 && n_eval > 0) st.df_ms += span(6, 1);
-            st.reduce_ms += span(1, 2);
-            st.scan_ms += span(2, 3);
-            if (split_pending) st.split_ms += span(4, 5);
-        }
-        split_pending = false;
-        // pool pressure: integrals split in slot order while the growth fits;
-        // the rest keep their regions this round
-        bool throttled = false;
-        if (int64_t(t.pool) > cap) {
-            const unsigned long long room = (unsigned long long)(cap - pool);
-            if ((e = launch_throttle(w, n_active, room, s)) != cudaSuccess ||
-                (e = launch_scan(w, n_active, s)) != cudaSuccess ||
-                (e = read_totals(t)) != cudaSuccess)
-                return cuda_fail(ctx, e, "throttle");
-            st.launches += 3;
-            ++st.throttled_rounds;
-            throttled = true;
-        }
-        st.rounds = round + 1;
-        st.escalated = int64_t(t.escalated);
-        st.df_regions = int64_t(t.df_regions);
-        // throttled to no growth, nothing retired, nothing to evaluate: no progress
-        const bool stuck = int64_t(t.pool) > cap ||
-                           (throttled && int64_t(t.active) == n_active && int64_t(t.eval) == 0);
-        if (t.active == 0 && admitted == n_total) {
-            if (t.roundcap > 0) rc = fail(ctx, PAID_ERR_TIMEOUT, "round cap reached");
-            break;
-        }
-        if (stuck) {
-            if ((e = launch_finalize(w, cur, n_active, POOL, s)) != cudaSuccess ||
-                (e = launch_mark_unadmitted(w, admitted, n_total, POOL, s)) != cudaSuccess)
-                return cuda_fail(ctx, e, "finalize");
-            st.launches += 2;
-            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "finalize sync");
-            rc = fail(ctx, PAID_ERR_POOL, "region pool full (capacity " + std::to_string(cap) + ")");
-            break;
-        }
-        if ((e = mark(4)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-        if ((e = launch_split(w, cur, n_active, s)) != cudaSuccess) return cuda_fail(ctx, e, "split");
-        if ((e = mark(5)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-        st.launches += 1;
-        split_pending = true;
-        n_active = int64_t(t.active);
-        n_eval = int64_t(t.eval);
-        pool = int64_t(t.pool);
-        // streaming admission: more integrals while the pool is under half full
-        if (admitted < n_total && L0 >= 0) {
-            const int64_t est = std::max<int64_t>(16 * n0, 4 * (pool / std::max<int64_t>(1, n_active)));
-            int64_t c = cap / 2 > pool ? (cap / 2 - pool) / est : 0;
-            if (n_active == 0) c = std::max<int64_t>(c, 1);
-            c = std::min(c, n_total - admitted);
-            c = std::min(c, (cap - pool) / n0);
-            if (c > 0) {
-                if ((e = launch_setup(w, L0, ctx->nff, o.eval_fp32 ? 0 : 1, s, admitted, admitted + c,
-                                      cur ^ 1, (unsigned long long)pool, (unsigned long long)n_eval,
-                                      (unsigned long long)n_active, round + 1)) != cudaSuccess)
-                    return cuda_fail(ctx, e, "admit");
+    cudaError_t e;
+    if ((e = launch_state_init(w, admitted, n_eval, pool, admitted, L0, hard, s)) != cudaSuccess)
+        return cfail(e, "loop state");
+    st.launches += 1;
+    LoopState L{};
+    RoundTotals t{};
+    if (graph) {
+        cudaGraphExec_t exec = nullptr;
+        const int rc = loop_graph(ctx, w, &exec);
+        if (rc != PAID_OK) return rc;
+        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cfail(e, "graph launch");
+        st.graph_launches = 1;
+        if ((e = read_state(L, t)) != cudaSuccess) return cfail(e, "device loop");
+        st.launches += int64_t(L.rounds_done) * round_kernels(o, 1, 1, true);
+        st.eval_launches += L.rounds_done;
+    } else {
+        L.n_eval = n_eval;
+        L.n_active = admitted;
+        for (;;) {
+            const int64_t ne = L.n_eval, na = L.n_active;
+            if ((e = launch_round(ctx, w, ne, na, 0, 0, s, timed ? ev : nullptr)) != cudaSuccess)
+                return cfail(e, "round");
+            st.launches += round_kernels(o, ne, na, false);
+            st.eval_launches += ne > 0 ? 1 : 0;
+            if ((e = read_state(L, t)) != cudaSuccess) return cfail(e, "round sync");
+            if (timed) {
+                st.eval_ms += span(0, 1);
+                if (o.eval_fp32 && ne > 0) st.df_ms += span(6, 1);
+                st.reduce_ms += span(1, 2);
+                st.scan_ms += span(2, 3);
+                st.split_ms += span(3, 4);
+            }
+            if (L.stop != kRunning) break;
+            if (L.wave_g1 > L.wave_g0) {
+                if ((e = launch_setup_wave(w, L.wave_g1 - L.wave_g0, ctx->nff, o.eval_fp32 ? 0 : 1,
+                                           s)) != cudaSuccess)
+                    return cfail(e, "admit");
                 st.launches += 1;
-                admitted += c;
-                n_active += c;
-                n_eval += c * n0;
-                pool += c * n0;
-            } else if (n_active == 0) {
-                if ((e = launch_mark_unadmitted(w, admitted, n_total, POOL, s)) != cudaSuccess)
-                    return cuda_fail(ctx, e, "finalize");
-                rc = fail(ctx, PAID_ERR_POOL, "region pool too small for one integral's start");
-                break;
             }
         }
-        cur ^= 1;
     }
-    st.node_evals = st.region_evals * nodes;
+    st.rounds = L.rounds_done;
+    st.region_evals = L.region_evals;
+    st.peak_pool = L.peak_pool;
+    st.throttled_rounds = L.throttled_rounds;
+    st.escalated = int64_t(t.escalated);
+    st.df_regions = int64_t(t.df_regions);
+    st.node_evals = st.region_evals * int64_t(2 * o.rule_n + 1) * (2 * o.rule_n + 1);
     st.pool_capacity = cap;
+    int rc = PAID_OK;
+    switch (L.stop) {
+    case kDone:
+        if (t.roundcap > 0) rc = rfail(PAID_ERR_TIMEOUT, "round cap reached");
+        break;
+    case kStuck:
+        if ((e = launch_finalize(w, L.n_active, POOL, s)) != cudaSuccess ||
+            (e = launch_mark_unadmitted(w, L.admitted, n, POOL, s)) != cudaSuccess)
+            return cfail(e, "finalize");
+        st.launches += 2;
+        rc = no_alloc ? int(PAID_ERR_POOL)
+                      : fail(ctx, PAID_ERR_POOL,
+                             "region pool full (capacity " + std::to_string(cap) + ")");
+        break;
+    case kNoRoom:
+        if ((e = launch_mark_unadmitted(w, L.admitted, n, POOL, s)) != cudaSuccess)
+            return cfail(e, "finalize");
+        st.launches += 1;
+        rc = rfail(PAID_ERR_POOL, "region pool too small for one integral's start");
+        break;
+    case kHardCap:
+        if ((e = launch_mark_unadmitted(w, L.admitted, n, ROUNDCAP, s)) != cudaSuccess)
+            return cfail(e, "finalize");
+        st.launches += 1;
+        rc = rfail(PAID_ERR_TIMEOUT, "round cap reached");
+        break;
+    default:
+        return rfail(PAID_ERR_CUDA, "device loop ended without a stop decision");
+    }
+    if (L.stop != kDone && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cfail(e, "finalize sync");
     return rc;
 }
 
@@ -486,7 +618,7 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
     if ((e = launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s, 0, a)) != cudaSuccess)
         return cuda_fail(ctx, e, "setup");
     ctx->stats.launches = 1;
-    return run_rounds(ctx, w, cap, n, a, a, a * n0, a * n0, o.init_level, s);
+    return run_loop(ctx, w, a, a * n0, a * n0, o.init_level, s);
 }
 
 int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb,
@@ -503,9 +635,11 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 16, s, w, n, cap);
     if (rc != PAID_OK || n == 0) return rc;
     cudaError_t e;
+    // the slot scan reads its slot count from the loop state
     if ((e = launch_setup(w, -1, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess ||
+        (e = launch_state_init(w, n, 0, 0, n, -1, o.max_rounds, s)) != cudaSuccess ||
         (e = launch_seed(w, proposal, rate, 0, s)) != cudaSuccess ||
-        (e = launch_scan(w, n, s)) != cudaSuccess)
+        (e = launch_scan(w, n, 0, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "seed");
     if ((e = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals), cudaMemcpyDeviceToHost,
                              s)) != cudaSuccess ||
@@ -515,8 +649,8 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     if (int64_t(t.pool) > cap)
         return fail(ctx, PAID_ERR_OOM, "workspace too small for the seeded partition");
     if ((e = launch_seed(w, proposal, rate, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
-    ctx->stats.launches = 5;
-    return run_rounds(ctx, w, cap, n, n, n, int64_t(t.eval), int64_t(t.pool), -1, s);
+    ctx->stats.launches = 6;
+    return run_loop(ctx, w, n, int64_t(t.eval), int64_t(t.pool), -1, s);
 }
 
 int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
@@ -551,7 +685,8 @@ int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npair
     if (rc != PAID_OK || n == 0) return rc;
     cudaError_t e;
     if ((e = launch_setup(w, 4, ctx->nff, 1, s)) != cudaSuccess ||
-        (e = launch_eval(w, 0, n * 256, ctx->opt.rule_n, 0, ctx->lat, s)) != cudaSuccess ||
+        (e = launch_state_init(w, n, n * 256, n * 256, n, 4, 1, s)) != cudaSuccess ||
+        (e = launch_eval(w, n * 256, ctx->opt.rule_n, 0, ctx->lat, s)) != cudaSuccess ||
         (e = launch_cell_map(w, out, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "cell errors");
     ctx->stats.region_evals = n * 256;
@@ -699,61 +834,6 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
         launch_setup(w, o.init_level, ctx->nff, o.eval_fp32 ? 0 : 1, s) != cudaSuccess)
         return PAID_ERR_CUDA;
 
-    paid_stats& st = ctx->stats;
-    st.launches = 1;
-    int64_t n_active = n, n_eval = n * n0, pool = n * n0;
-    int cur = 0;
-    int rc = PAID_OK;
-    for (int round = 0;; ++round) {
-        st.region_evals += n_eval;
-        st.peak_pool = std::max(st.peak_pool, pool);
-        if (launch_eval(w, cur, n_eval, o.rule_n, o.eval_fp32, ctx->lat, s) != cudaSuccess ||
-            launch_reduce_test(w, cur, n_active, round, o.max_rounds, o.cover, s) != cudaSuccess ||
-            launch_scan(w, n_active, s) != cudaSuccess)
-            return PAID_ERR_CUDA;
-        st.eval_launches += n_eval > 0 ? 1 : 0;
-        st.launches += (n_eval > 0 ? 1 : 0) + 3;
-        if (cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals), cudaMemcpyDeviceToHost,
-                            s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return PAID_ERR_CUDA;
-        RoundTotals t = *ctx->h_totals;
-        bool throttled = false;
-        if (int64_t(t.pool) > cap) {   // integrals split in order while the growth fits
-            if (launch_throttle(w, n_active, (unsigned long long)(cap - pool), s) != cudaSuccess ||
-                launch_scan(w, n_active, s) != cudaSuccess ||
-                cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
-                                cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return PAID_ERR_CUDA;
-            t = *ctx->h_totals;
-            st.launches += 3;
-            ++st.throttled_rounds;
-            throttled = true;
-        }
-        st.rounds = round + 1;
-        st.escalated = int64_t(t.escalated);
-        if (t.active == 0) {
-            if (t.roundcap > 0) rc = PAID_ERR_TIMEOUT;
-            break;
-        }
-        if (int64_t(t.pool) > cap ||
-            (throttled && int64_t(t.active) == n_active && int64_t(t.eval) == 0)) {
-            if (launch_finalize(w, cur, n_active, POOL, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return PAID_ERR_CUDA;
-            st.launches += 1;
-            rc = PAID_ERR_POOL;
-            break;
-        }
-        if (launch_split(w, cur, n_active, s) != cudaSuccess) return PAID_ERR_CUDA;
-        st.launches += 1;
-        n_active = int64_t(t.active);
-        n_eval = int64_t(t.eval);
-        pool = int64_t(t.pool);
-        cur ^= 1;
-    }
-    st.node_evals = st.region_evals * (2 * o.rule_n + 1) * (2 * o.rule_n + 1);
-    st.pool_capacity = cap;
-    return rc;
+    ctx->stats.launches = 1;
+    return run_loop(ctx, w, n, n * n0, n * n0, o.init_level, s, true);
 }

@@ -693,8 +693,10 @@ __device__ __forceinline__ bool is_df_region(uint32_t mt)
 // per SM without spills.
 template <int N>
 __global__ void __launch_bounds__(kYsStride, N == 4 ? 3 : 1)
-k_eval_df(Work w, int cur, int64_t n_eval, Lattice lat)
+k_eval_df(Work w, Lattice lat)
 {
+    const int cur = w.ls->cur;
+    const int64_t n_eval = w.ls->n_eval;
     constexpr bool SMEM = N == 4;
     constexpr int NF = 2 * N + 1;
     const int v = N == 4 ? 0 : 1;
@@ -736,8 +738,10 @@ k_eval_df(Work w, int cur, int64_t n_eval, Lattice lat)
 // integrals escalated to float-float are left to k_eval_df); integrals set to
 // FP64 and the test kinds use the FP64 path.
 template <int N>
-__global__ void __launch_bounds__(128) k_eval_fp32(Work w, int cur, int64_t n_eval, Lattice lat)
+__global__ void __launch_bounds__(128) k_eval_fp32(Work w, Lattice lat)
 {
+    const int cur = w.ls->cur;
+    const int64_t n_eval = w.ls->n_eval;
     const int v = N == 4 ? 0 : 1;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_eval; t += stride) {
@@ -778,8 +782,10 @@ __global__ void __launch_bounds__(128) k_eval_fp32(Work w, int cur, int64_t n_ev
 }
 
 template <int N>
-__global__ void __launch_bounds__(128) k_eval_fp64(Work w, int cur, int64_t n_eval, Lattice lat)
+__global__ void __launch_bounds__(128) k_eval_fp64(Work w, Lattice lat)
 {
+    const int cur = w.ls->cur;
+    const int64_t n_eval = w.ls->n_eval;
     const int v = N == 4 ? 0 : 1;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_eval; t += stride) {
@@ -812,26 +818,26 @@ __global__ void __launch_bounds__(128) k_eval_fp64(Work w, int cur, int64_t n_ev
     }
 }
 
-cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
-                        Lattice lat, cudaStream_t s, cudaEvent_t mid)
+cudaError_t launch_eval(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,
+                        cudaStream_t s, cudaEvent_t mid)
 {
-    if (n_eval <= 0) return cudaSuccess;
+    if (hint_eval <= 0) return cudaSuccess;
     const int threads = 128;
-    int64_t blocks = (n_eval + threads - 1) / threads;
+    int64_t blocks = (hint_eval + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (fp32) {
-        const int dblocks = int(std::min<int64_t>((n_eval + kYsStride - 1) / kYsStride, 152 * 48));
-        if (rule_n == 4) k_eval_fp32<4><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
-        else             k_eval_fp32<6><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+        const int dblocks = int(std::min<int64_t>((hint_eval + kYsStride - 1) / kYsStride, 152 * 48));
+        if (rule_n == 4) k_eval_fp32<4><<<int(blocks), threads, 0, s>>>(w, lat);
+        else             k_eval_fp32<6><<<int(blocks), threads, 0, s>>>(w, lat);
         if (mid) {
             const cudaError_t e = cudaEventRecord(mid, s);
             if (e != cudaSuccess) return e;
         }
-        if (rule_n == 4) k_eval_df<4><<<dblocks, kYsStride, 0, s>>>(w, cur, n_eval, lat);
-        else             k_eval_df<6><<<dblocks, kYsStride, 0, s>>>(w, cur, n_eval, lat);
+        if (rule_n == 4) k_eval_df<4><<<dblocks, kYsStride, 0, s>>>(w, lat);
+        else             k_eval_df<6><<<dblocks, kYsStride, 0, s>>>(w, lat);
     } else {
-        if (rule_n == 4) k_eval_fp64<4><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
-        else             k_eval_fp64<6><<<int(blocks), threads, 0, s>>>(w, cur, n_eval, lat);
+        if (rule_n == 4) k_eval_fp64<4><<<int(blocks), threads, 0, s>>>(w, lat);
+        else             k_eval_fp64<6><<<int(blocks), threads, 0, s>>>(w, lat);
     }
     return cudaGetLastError();
 }

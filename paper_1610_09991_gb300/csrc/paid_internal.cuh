@@ -15,6 +15,10 @@
 //     nse[C] float   bound on the FP32 rounding noise of the region's sums
 //                    (0 for regions evaluated in FP64)
 //   eval list  uint2[C] (pool position, integral) of regions awaiting evaluation
+//   loop state LoopState: the round's counts and the buffer in use, read by
+//              every round kernel and advanced by k_control, so that a round
+//              needs no host-side arguments (the same launches run from the
+//              host loop or inside a CUDA graph's conditional WHILE node)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -103,6 +107,32 @@ struct RoundTotals {
     unsigned long long pad[2];
 };
 
+// Why the device loop stopped.
+enum LoopStop : int { kRunning = 0, kDone = 1, kStuck = 2, kNoRoom = 3, kHardCap = 4 };
+
+// The state of the refinement loop, in device memory.
+struct LoopState {
+    long long n_active;        // active slots of the coming round
+    long long n_eval;          // regions on its eval list
+    long long pool;            // regions in its pool
+    long long admitted;        // integrals [0, admitted) have entered the pool
+    long long n_total;
+    long long cap;             // pool capacity (regions per buffer)
+    long long wave_g0, wave_g1;    // integrals admitted by the last control step
+    unsigned long long wave_pool, wave_eval, wave_act;   // their bases
+    long long region_evals;    // statistics
+    long long peak_pool;
+    long long throttled_rounds;
+    int cur;                   // pool buffer of the coming round
+    int round;                 // index of the coming round
+    int rounds_done;
+    int L0;                    // admission start level (< 0: no admission)
+    int hard_rounds;           // loop bound: stop after this many rounds
+    int stop;                  // LoopStop
+    int throttled;             // the current round was throttled
+    int pad;
+};
+
 // Pointers into the workspace.
 struct Work {
     DevBatch* batches;
@@ -125,6 +155,7 @@ struct Work {
     unsigned long long* blk_eval;
     uint32_t* blk_act;
     RoundTotals* totals;
+    LoopState* ls;
     uint64_t* key[2];
     double* val[2];
     double* err[2];
@@ -133,13 +164,19 @@ struct Work {
 };
 
 // ---- host-side launch wrappers (defined in the .cu files) -----------------
+// Round kernels take their counts and the buffer in use from w.ls; the `hint`
+// arguments only size the grids (the exact count, or an upper bound when the
+// launch is captured into a graph that runs it for every round).
 // paid_eval.cu
 cudaError_t init_rule_tables(int device);
 // fp32 = 1: the FP32 / FP64 kernel, then the float-float kernel; `mid`, when
 // given, is recorded between the two
-cudaError_t launch_eval(const Work& w, int cur, int64_t n_eval, int rule_n, int fp32,
-                        Lattice lat, cudaStream_t s, cudaEvent_t mid = nullptr);
+cudaError_t launch_eval(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,
+                        cudaStream_t s, cudaEvent_t mid = nullptr);
 // paid_pool.cu
+// Initial loop state: counts of the first round, buffer 0, round 0.
+cudaError_t launch_state_init(const Work& w, int64_t n_active, int64_t n_eval, int64_t pool,
+                              int64_t admitted, int L0, int hard_rounds, cudaStream_t s);
 // Integrals [g0, g1) (g1 < 0: all): descriptors and, for L0 >= 0, their uniform
 // level-L0 regions appended at the given bases of pool[buf] / eval list /
 // active[buf].  L0 < 0: descriptors only (the partition comes from launch_seed).
@@ -147,20 +184,29 @@ cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t 
                          int64_t g1 = -1, int buf = 0, unsigned long long pool_base = 0,
                          unsigned long long eval_base = 0, unsigned long long act_base = 0,
                          int round = 0);
+// the admission wave chosen by the last control step (w.ls->wave_*)
+cudaError_t launch_setup_wave(const Work& w, int64_t hint_wave, int nff, int fp64, cudaStream_t s);
 // pass 0: region counts into cnt_new / cnt_eval (slot = integral); pass 1 (after
 // launch_scan): keys, eval list, segments.  proposal null = uniform level 4.
 cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s);
 cudaError_t launch_features(int kind, int nq, const double* q, int npairs, const int32_t* lm,
                             double T, double mu, double tp, void* x, cudaStream_t s);
 cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s);
-cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int round,
-                               int max_rounds, double cover, cudaStream_t s);
-cudaError_t launch_scan(const Work& w, int64_t n_active, cudaStream_t s);
-cudaError_t launch_split(const Work& w, int cur, int64_t n_active, cudaStream_t s);
-cudaError_t launch_finalize(const Work& w, int cur, int64_t n_active, int status, cudaStream_t s);
+cudaError_t launch_reduce_test(const Work& w, int64_t hint_active, int max_rounds, double cover,
+                               cudaStream_t s);
+// rescan = 1: only when the last scan's pool total exceeds the capacity (after
+// launch_throttle), and then it marks the round as throttled
+cudaError_t launch_scan(const Work& w, int64_t hint_active, int rescan, cudaStream_t s);
+cudaError_t launch_split(const Work& w, int64_t hint_active, cudaStream_t s);
+// finish every slot still refining with `status` (after a stop)
+cudaError_t launch_finalize(const Work& w, int64_t hint_active, int status, cudaStream_t s);
 cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int status, cudaStream_t s);
-// after launch_scan: integrals past `room` regions of cumulative growth keep
-// their regions unsplit this round (re-scan afterwards)
-cudaError_t launch_throttle(const Work& w, int64_t n_active, unsigned long long room, cudaStream_t s);
+// after launch_scan, when its pool total exceeds the capacity: integrals past
+// cap - pool regions of cumulative growth keep their regions unsplit this round
+cudaError_t launch_throttle(const Work& w, int64_t hint_active, cudaStream_t s);
+// one thread: statistics, next round's counts, buffer flip, admission wave and
+// the stop decision; inside a graph (in_graph = 1) a stop sets the WHILE
+// node's condition to 0
+cudaError_t launch_control(const Work& w, cudaGraphConditionalHandle h, int in_graph, cudaStream_t s);
 
 }  // namespace paid

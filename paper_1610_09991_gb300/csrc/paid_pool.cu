@@ -64,15 +64,13 @@ __device__ __forceinline__ int log_key(double x)
 }
 
 // ---------------------------------------------------------------------------
-// Integrals [g0, g1): descriptors, and (write_regions) their uniform level-L0
-// regions at pool[buf][pool_base + (g - g0) n0 ...], on the eval list from
-// eval_base and on the active list active[buf] from act_base.
-__global__ void k_setup(Work w, int64_t g0, int64_t g1, int L0, int nff, int fp64, int buf,
-                        unsigned long long pool_base, unsigned long long eval_base,
-                        unsigned long long act_base, int write_regions, int round)
+// Integral g of the range starting at g0: descriptors, and (write_regions) its
+// uniform level-L0 regions at pool[buf][pool_base + (g - g0) n0 ...], on the
+// eval list from eval_base and on the active list active[buf] from act_base.
+__device__ void setup_one(const Work& w, int64_t g, int64_t g0, int L0, int nff, int fp64, int buf,
+                          unsigned long long pool_base, unsigned long long eval_base,
+                          unsigned long long act_base, int write_regions, int round)
 {
-    const int64_t g = g0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= g1) return;
     const int64_t i = g - g0;
     int b = 0;   // batches are sorted by `first`
     {
@@ -112,6 +110,15 @@ __global__ void k_setup(Work w, int64_t g0, int64_t g1, int L0, int nff, int fp6
     }
     w.active[buf][act_base + i] = uint32_t(g);
     B.status[local] = RUNNING;
+}
+
+__global__ void k_setup(Work w, int64_t g0, int64_t g1, int L0, int nff, int fp64, int buf,
+                        unsigned long long pool_base, unsigned long long eval_base,
+                        unsigned long long act_base, int write_regions, int round)
+{
+    const int64_t g = g0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= g1) return;
+    setup_one(w, g, g0, L0, nff, fp64, buf, pool_base, eval_base, act_base, write_regions, round);
     if (g == 0) {
         w.totals->escalated = 0ull;
         w.totals->df_regions = 0ull;
@@ -129,6 +136,118 @@ cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t 
     const int64_t blocks = (g1 - g0 + threads - 1) / threads;
     k_setup<<<int(blocks), threads, 0, s>>>(w, g0, g1, L0, nff, fp64, buf, pool_base, eval_base,
                                             act_base, L0 >= 0 ? 1 : 0, round);
+    return cudaGetLastError();
+}
+
+// The admission wave of the last control step, into the buffer of the coming
+// round (grid-stride, so that a fixed grid serves every round of a graph).
+__global__ void k_setup_wave(Work w, int nff, int fp64)
+{
+    const LoopState& L = *w.ls;
+    const int64_t g0 = L.wave_g0, g1 = L.wave_g1;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t g = g0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < g1; g += stride)
+        setup_one(w, g, g0, L.L0, nff, fp64, L.cur, L.wave_pool, L.wave_eval, L.wave_act, 1,
+                  L.round);
+}
+
+cudaError_t launch_setup_wave(const Work& w, int64_t hint_wave, int nff, int fp64, cudaStream_t s)
+{
+    if (hint_wave <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((hint_wave + 255) / 256, 152 * 8);
+    k_setup_wave<<<int(blocks), 256, 0, s>>>(w, nff, fp64);
+    return cudaGetLastError();
+}
+
+// One thread: the loop state of the first round.
+__global__ void k_state_init(Work w, int64_t n_active, int64_t n_eval, int64_t pool,
+                             int64_t admitted, int L0, int hard_rounds)
+{
+    LoopState& L = *w.ls;
+    L.n_active = n_active;
+    L.n_eval = n_eval;
+    L.pool = pool;
+    L.admitted = admitted;
+    L.n_total = w.n;
+    L.cap = w.cap;
+    L.wave_g0 = L.wave_g1 = 0;
+    L.wave_pool = L.wave_eval = L.wave_act = 0ull;
+    L.region_evals = 0;
+    L.peak_pool = 0;
+    L.throttled_rounds = 0;
+    L.cur = 0;
+    L.round = 0;
+    L.rounds_done = 0;
+    L.L0 = L0;
+    L.hard_rounds = hard_rounds;
+    L.stop = kRunning;
+    L.throttled = 0;
+    L.pad = 0;
+}
+
+cudaError_t launch_state_init(const Work& w, int64_t n_active, int64_t n_eval, int64_t pool,
+                              int64_t admitted, int L0, int hard_rounds, cudaStream_t s)
+{
+    k_state_init<<<1, 1, 0, s>>>(w, n_active, n_eval, pool, admitted, L0, hard_rounds);
+    return cudaGetLastError();
+}
+
+// One thread, after the split: the next round's counts and buffer, the
+// statistics, streaming admission (more integrals while the pool is under
+// half full) and the stop decision.
+__global__ void k_control(Work w, cudaGraphConditionalHandle h, int in_graph)
+{
+    LoopState& L = *w.ls;
+    const RoundTotals t = *w.totals;
+    L.region_evals += L.n_eval;
+    L.peak_pool = max(L.peak_pool, L.pool);
+    L.throttled_rounds += L.throttled;
+    L.rounds_done = L.round + 1;
+    // throttled to no growth, nothing retired, nothing to evaluate: no progress
+    const bool stuck = L.throttled && (long long)t.active == L.n_active && t.eval == 0ull;
+    L.throttled = 0;
+    // the split wrote the next pool, eval list and active list into cur ^ 1
+    L.n_active = (long long)t.active;
+    L.n_eval = (long long)t.eval;
+    L.pool = (long long)t.pool;
+    L.cur ^= 1;
+    L.round += 1;
+    L.wave_g0 = L.wave_g1 = 0;
+    int stop = kRunning;
+    if (t.active == 0ull && L.admitted == L.n_total) {
+        stop = kDone;
+    } else if (stuck) {
+        stop = kStuck;
+    } else if (t.active == 0ull && L.round > L.hard_rounds) {
+        stop = kHardCap;   // the reduce-test ended every active integral at the bound
+    } else if (L.admitted < L.n_total && L.L0 >= 0) {
+        const long long n0 = 1ll << (2 * L.L0);
+        const long long est = max(16 * n0, 4 * (L.pool / max(1ll, L.n_active)));
+        long long c = L.cap / 2 > L.pool ? (L.cap / 2 - L.pool) / est : 0;
+        if (L.n_active == 0) c = max(c, 1ll);
+        c = min(c, L.n_total - L.admitted);
+        c = min(c, (L.cap - L.pool) / n0);
+        if (c > 0) {
+            L.wave_g0 = L.admitted;
+            L.wave_g1 = L.admitted + c;
+            L.wave_pool = (unsigned long long)L.pool;
+            L.wave_eval = (unsigned long long)L.n_eval;
+            L.wave_act = (unsigned long long)L.n_active;
+            L.admitted += c;
+            L.n_active += c;
+            L.n_eval += c * n0;
+            L.pool += c * n0;
+        } else if (L.n_active == 0) {
+            stop = kNoRoom;
+        }
+    }
+    L.stop = stop;
+    if (in_graph && stop != kRunning) cudaGraphSetConditional(h, 0u);
+}
+
+cudaError_t launch_control(const Work& w, cudaGraphConditionalHandle h, int in_graph, cudaStream_t s)
+{
+    k_control<<<1, 1, 0, s>>>(w, h, in_graph);
     return cudaGetLastError();
 }
 
@@ -316,15 +435,16 @@ cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s)
 constexpr int kWarpsPerBlock = 8;
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, double cover,
-              int force_status)
+k_reduce_test(Work w, int max_rounds, double cover, int force_status)
 {
+    const int cur = w.ls->cur;
+    const int64_t n_active = w.ls->n_active;
+    const int round = w.ls->round;
     __shared__ unsigned long long hsum[kWarpsPerBlock][kHistBins];
     __shared__ uint32_t hcnt[kWarpsPerBlock][kHistBins];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t s = int64_t(blockIdx.x) * kWarpsPerBlock + wib;
     if (s >= n_active) return;
-    if (force_status >= 0 && w.cnt_new[s] == 0) return;   // already finished
     const uint32_t g = w.active[cur][s];
     const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
     const uint32_t mt = w.meta[g];
@@ -356,7 +476,8 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
     if (force_status >= 0) st = force_status;
     else if (!isfinite(V) || !isfinite(E)) st = NONFINITE;
     else if (E <= tol) st = CONVERGED;
-    else if (round - int(w.born[g]) >= max_rounds) st = ROUNDCAP;   // rounds since admission
+    else if (round - int(w.born[g]) >= max_rounds || round >= w.ls->hard_rounds)
+        st = ROUNDCAP;   // rounds since admission, or the loop's own bound
     else if (fp32 && noise > kNoiseTol * tol) {
         // FP32 rounding noise would crowd the tolerance, and refinement does
         // not shrink it: re-evaluate at higher precision
@@ -427,13 +548,12 @@ k_reduce_test(Work w, int cur, int64_t n_active, int round, int max_rounds, doub
     }
 }
 
-cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int round,
-                               int max_rounds, double cover, cudaStream_t s)
+cudaError_t launch_reduce_test(const Work& w, int64_t hint_active, int max_rounds, double cover,
+                               cudaStream_t s)
 {
-    if (n_active <= 0) return cudaSuccess;
-    const int64_t blocks = (n_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, cur, n_active, round,
-                                                              max_rounds, cover, -1);
+    if (hint_active <= 0) return cudaSuccess;
+    const int64_t blocks = (hint_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, max_rounds, cover, -1);
     return cudaGetLastError();
 }
 
@@ -444,8 +564,12 @@ cudaError_t launch_reduce_test(const Work& w, int cur, int64_t n_active, int rou
 // eval count (4 children replace each marked region); escalated slots count
 // their full eval count there, which only makes the bound conservative.
 // With room = capacity - current pool the next pool stays within capacity.
-__global__ void k_throttle(Work w, int64_t n_active, unsigned long long room)
+__global__ void k_throttle(Work w)
 {
+    const LoopState& L = *w.ls;
+    if (!((long long)w.totals->pool > L.cap)) return;
+    const unsigned long long room = (unsigned long long)(L.cap - L.pool);
+    const int64_t n_active = L.n_active;
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= n_active) return;
     const uint32_t nnew = w.cnt_new[s];
@@ -460,10 +584,10 @@ __global__ void k_throttle(Work w, int64_t n_active, unsigned long long room)
     w.thr[s] = make_uint2(w.thr[s].x & ~0xffu, 0u);
 }
 
-cudaError_t launch_throttle(const Work& w, int64_t n_active, unsigned long long room, cudaStream_t s)
+cudaError_t launch_throttle(const Work& w, int64_t hint_active, cudaStream_t s)
 {
-    if (n_active <= 0) return cudaSuccess;
-    k_throttle<<<int((n_active + 255) / 256), 256, 0, s>>>(w, n_active, room);
+    if (hint_active <= 0) return cudaSuccess;
+    k_throttle<<<int((hint_active + 255) / 256), 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
@@ -496,19 +620,27 @@ cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int st
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const Work& w, int cur, int64_t n_active, int status, cudaStream_t s)
+cudaError_t launch_finalize(const Work& w, int64_t hint_active, int status, cudaStream_t s)
 {
-    if (n_active <= 0) return cudaSuccess;
-    const int64_t blocks = (n_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, cur, n_active, 0, 0, 0.0,
-                                                              status);
+    if (hint_active <= 0) return cudaSuccess;
+    const int64_t blocks = (hint_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, 0, 0.0, status);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Exclusive scan of (cnt_new, cnt_eval, cnt_new > 0) over the active slots.
-__global__ void __launch_bounds__(kScanBlock) k_scan_blocks(Work w, int64_t n_active)
+// rescan = 1 runs only when the last scan's pool total is over capacity.
+__device__ __forceinline__ bool over_capacity(const Work& w)
 {
+    return (long long)w.totals->pool > w.ls->cap;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_blocks(Work w, int rescan)
+{
+    if (rescan && !over_capacity(w)) return;
+    const int64_t n_active = w.ls->n_active;
+    if (int64_t(blockIdx.x) * kScanBlock >= n_active) return;
     __shared__ unsigned long long sp[32], se[32];
     __shared__ uint32_t sa[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -559,14 +691,22 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_blocks(Work w, int64_t n_ac
 }
 
 // Single block: exclusive scan of the block totals in place, grand totals out.
-__global__ void __launch_bounds__(kScanBlock) k_scan_top(Work w, int nblk)
+__global__ void __launch_bounds__(kScanBlock) k_scan_top(Work w, int rescan)
 {
     __shared__ unsigned long long sp[32], se[32];
     __shared__ unsigned long long sa[32];
     __shared__ unsigned long long carry[3];
+    __shared__ int go;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) { carry[0] = carry[1] = carry[2] = 0ull; }
+    if (threadIdx.x == 0) {
+        carry[0] = carry[1] = carry[2] = 0ull;
+        go = !rescan || over_capacity(w);
+        if (rescan && go) w.ls->throttled = 1;
+    }
     __syncthreads();
+    if (!go) return;
+    const int64_t n_active = w.ls->n_active;
+    const int nblk = int((n_active + kScanBlock - 1) / kScanBlock);
     for (int c0 = 0; c0 < nblk; c0 += kScanBlock) {
         const int i = c0 + threadIdx.x;
         unsigned long long p = 0, e = 0, a = 0;
@@ -611,19 +751,21 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_top(Work w, int nblk)
     }
 }
 
-cudaError_t launch_scan(const Work& w, int64_t n_active, cudaStream_t s)
+cudaError_t launch_scan(const Work& w, int64_t hint_active, int rescan, cudaStream_t s)
 {
-    const int64_t nblk = n_active > 0 ? (n_active + kScanBlock - 1) / kScanBlock : 0;
-    if (nblk > 0) k_scan_blocks<<<int(nblk), kScanBlock, 0, s>>>(w, n_active);
-    k_scan_top<<<1, kScanBlock, 0, s>>>(w, int(nblk));
+    const int64_t nblk = hint_active > 0 ? (hint_active + kScanBlock - 1) / kScanBlock : 0;
+    if (nblk > 0) k_scan_blocks<<<int(nblk), kScanBlock, 0, s>>>(w, rescan);
+    k_scan_top<<<1, kScanBlock, 0, s>>>(w, rescan);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Split marked regions into 4 children, copy the rest; build the eval list and
 // the next active list.  Reads pool[cur], writes pool[cur ^ 1].
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w, int cur, int64_t n_active)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w)
 {
+    const int cur = w.ls->cur;
+    const int64_t n_active = w.ls->n_active;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t s = int64_t(blockIdx.x) * kWarpsPerBlock + wib;
     if (s >= n_active) return;
@@ -715,11 +857,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w, int cur, 
     }
 }
 
-cudaError_t launch_split(const Work& w, int cur, int64_t n_active, cudaStream_t s)
+cudaError_t launch_split(const Work& w, int64_t hint_active, cudaStream_t s)
 {
-    if (n_active <= 0) return cudaSuccess;
-    const int64_t blocks = (n_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_split<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, cur, n_active);
+    if (hint_active <= 0) return cudaSuccess;
+    const int64_t blocks = (hint_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    k_split<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w);
     return cudaGetLastError();
 }
 

@@ -37,7 +37,7 @@ class paid_options(ctypes.Structure):
     _fields_ = [("rule_n", ctypes.c_int), ("init_level", ctypes.c_int),
                 ("eval_fp32", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("cover", ctypes.c_double), ("pool_capacity", ctypes.c_int64),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("device_loop", ctypes.c_int)]
 
 
 class paid_stats(ctypes.Structure):
@@ -48,7 +48,8 @@ class paid_stats(ctypes.Structure):
                 ("eval_ms", ctypes.c_double), ("reduce_ms", ctypes.c_double),
                 ("scan_ms", ctypes.c_double), ("split_ms", ctypes.c_double),
                 ("escalated", ctypes.c_int64), ("df_regions", ctypes.c_int64),
-                ("df_ms", ctypes.c_double), ("throttled_rounds", ctypes.c_int64)]
+                ("df_ms", ctypes.c_double), ("throttled_rounds", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64)]
 
 
 class paid_batch(ctypes.Structure):

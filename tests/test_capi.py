@@ -41,6 +41,7 @@ def test_host_side_calls_without_gpu(lib):
     assert paid.error_string(paid.ERR_POOL) == "region pool full"
     o = paid.options_default()
     assert (o.rule_n, o.init_level, o.eval_fp32, o.max_rounds) == (4, 2, 0, 4096)
+    assert (o.timing, o.device_loop) == (0, 1)
     assert lib.paid_options_default(None) == paid.ERR_ARG
     assert lib.paid_workspace_size(None, 10, 1000, None) == paid.ERR_ARG
     h = ctypes.c_void_p()
