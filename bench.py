@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "converged BZ loop integrals/s at rel tol 1e-6, learned+batched vs plain FP64"
+METRIC = "converged BZ loop integrals/s at rel tol 1e-6"
 UNIT = "integrals/s"
 # FP64 flops per integrand node of the FP64 region-evaluation kernel
 # (k_eval_fp64, N = 4, 81 nodes per region): per region 4117 DFMA (2 flops),
@@ -44,6 +44,12 @@ EVAL_DRAM_BYTES_PER_REGION = 18.3
 # launches of a run divided by the regions that kernel evaluated
 # (profiles/k_eval_df_first_shell.md).
 DF_FP32_FLOPS_PER_REGION = 2 * 7774.8 + 29243.1 + 3018.3   # 47,811
+# FP64 flops per region of the shared-partition kernel (k_eval_group, N = 4,
+# 81 pairs): 81 kernel evaluations, the 2 x 81 separable moments and the pair
+# map, counted from the source (per node ~104 flops for the energies and F,
+# 20 for the fine row sums, 20 x 25/81 for the coarse ones; per region 2394
+# for the moments, ~1620 for the pairs, ~1080 for the row / column set-up).
+GROUP_FP64_FLOPS_PER_REGION = 81 * 124 + 25 * 20 + 2394 + 1620 + 1080
 
 
 def parse_args():
@@ -54,9 +60,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
     ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep"],
                     default="flow_step")
-    ap.add_argument("--path", choices=["plain", "fp32", "learned"], default="learned",
+    ap.add_argument("--path", choices=["plain", "fp32", "learned", "group"], default="group",
                     help="plain: FP64 evaluation from the uniform start; fp32: FP32 / float-float "
-                         "evaluation; learned: fp32 plus the learned proposal's seeded start")
+                         "evaluation; learned: fp32 plus the learned proposal's seeded start; "
+                         "group: FP64, one shared partition per (kind, q) for all its pairs")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timed FP64 comparison step of an FP32 run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -276,9 +283,10 @@ def run_paid(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w, ff = workload(args.workload)
-    args.eval = "fp64" if args.path == "plain" else "fp32"
+    args.eval = "fp64" if args.path in ("plain", "group") else "fp32"
+    group = 1 if args.path == "group" else 0
     ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1,
-                    eval_fp32=1 if args.eval == "fp32" else 0)
+                    eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group)
     dev = torch.device("cuda", local)
     # N > 1: the temperature sweep is one fixed job split across the ranks by
     # q row (cost-balanced, no exchange; strong scaling); every other workload
@@ -384,7 +392,16 @@ def run_paid(args):
 
     eval_s = agg["eval_ms"] / 1e3
     roof = None
-    if FP64_FLOPS_PER_NODE and eval_s > 0 and args.eval == "fp64":
+    if group and eval_s > 0:
+        achieved = agg["region_evals"] * GROUP_FP64_FLOPS_PER_REGION / eval_s / 1e12
+        pk = peaks.get("fp64_fma_tflops")
+        roof = {"bound": "alu", "kernel": "k_eval_group", "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": achieved / pk if pk else None, "traffic": None,
+                "traffic_note": "compute-bound: 16 B of eval list / key read and 81 x 12 B of "
+                                "pair vectors written per region for ~15,600 FP64 flops",
+                "peak_source": "measured FP64 FMA micro-benchmark in this run (pipe_peaks.cu)",
+                "flops_per_region": GROUP_FP64_FLOPS_PER_REGION}
+    elif FP64_FLOPS_PER_NODE and eval_s > 0 and args.eval == "fp64":
         achieved = agg["node_evals"] * FP64_FLOPS_PER_NODE / eval_s / 1e12
         pk = peaks.get("fp64_fma_tflops")
         per_launch = agg["region_evals"] / max(1, agg["eval_launches"])
@@ -411,12 +428,15 @@ def run_paid(args):
         "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
         "dtype": "f64" if args.eval == "fp64" else "f32+f64", "data": "synthetic",
         "config": dict(workload_config(w_job, ff, args.eval),
+                       partition="one per (kind, q) group" if group else "one per integral",
                        parallelism="%d ranks, %s" % (world, "q rows split across ranks"
                                                      if scaling == "strong" else
                                                      "one instance per rank")),
         "clocks": clk, "roofline": roof, "gpu_launches": agg["launches"],
         "e2e": e2e,
         "path": {"plain": "plain FP64 GPU cubature from the uniform level-2 start",
+                 "group": "FP64 GPU cubature, one shared partition per (kind, q) serving all "
+                          "81 (l, m) pairs, each pair to its own tolerance",
                  "fp32": "batched GPU cubature, FP32 / float-float integrand, FP64 sums",
                  "learned": "learned proposal seeding + batched GPU cubature, FP32 / "
                             "float-float integrand, FP64 sums"}[args.path],
@@ -440,7 +460,7 @@ def run_paid(args):
         # launch per call (conditional WHILE node), no per-round host sync and
         # no per-kernel events
         cg = P.Context(*w.lattice, ffset=ff, device=local, device_loop=1,
-                       eval_fp32=1 if args.eval == "fp32" else 0)
+                       eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group)
 
         def gstep():
             flush.fill_(1)
@@ -470,7 +490,7 @@ def run_paid(args):
             "rounds_per_step": sum(x["rounds"] for x in gst) / args.steps,
             "values_identical_to_host_loop": bool(same)}
         del cg
-    if args.path != "plain" and not args.no_compare:
+    if args.path not in ("plain",) and not args.no_compare:
         # the plain FP64 GPU path on the same batch, one timed step
         c64 = P.Context(*w.lattice, ffset=ff, device=local, timing=1)
         c64.integrate_multi(dbs, stream=stream)        # warm-up (workspace)

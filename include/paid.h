@@ -99,6 +99,15 @@ typedef struct {
                                (a conditional WHILE node around one round's kernels; the host
                                waits once, at the end).  0: the host launches every round and
                                reads its counts back.  Default 1 */
+    int group_mode;         /* 1: one shared partition per (kind, q) of a batch serves all of the
+                               batch's (l, m) pairs (at most 81; kinds ph, pp, overlap; FP64).
+                               A region evaluates the kernel F once per node and every pair from
+                               81 separable moments; it is split while any pair of the group has
+                               not met its own tolerance.  Every integral still meets
+                               E <= max(abs_tol, rel_tol |V|) with E its own error sum; the
+                               region count reported is the group's.  max_regions bounds the
+                               group's regions and pool_capacity counts them (about 2 KB each).
+                               Default 0 (one partition per integral) */
 } paid_options;
 
 /* Statistics of the last integrate call on a context. */
@@ -183,6 +192,25 @@ typedef struct {
 
 int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb,
                          void* workspace, size_t ws_bytes, void* stream);
+
+/* The nested rule of Sec. 3 on given regions, for every pair of one
+ * (kind, q): the building block of the shared-partition mode, exposed so that
+ * a caller can evaluate a partition of its own.
+ *   kind: PAID_PH, PAID_PP or PAID_OVERLAP; T > 0.
+ *   q: device double [2]; lm: device int32 [npairs][2], 1 <= npairs <= 81.
+ *   regions: device int32 [nreg][3] = (level, ix, iy): the square with lower
+ *     corner -pi + 2 pi (ix, iy) / 2^level and side 2 pi / 2^level,
+ *     0 <= level <= 29, 0 <= ix, iy < 2^level.  An invalid region gives NaN.
+ *   q2N, dq: device double [nreg][npairs], written: Q_2N and Q_N - Q_2N of
+ *     pair p on region r, times the region's Jacobian (h/2)^2 / (2 pi)^2, so
+ *     that summing q2N over a partition of D gives the integral.
+ *   workspace: device, 256-byte aligned, at least paid_workspace_size(ctx, 1,
+ *     max(nreg, 16)) bytes.
+ * Returns PAID_OK (outputs complete, the stream synchronised), PAID_ERR_ARG,
+ * PAID_ERR_OOM (workspace too small) or PAID_ERR_CUDA. */
+int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int npairs,
+                      const int32_t* lm, int nreg, const int32_t* regions, double* q2N,
+                      double* dq, void* workspace, size_t ws_bytes, void* stream);
 
 /* paid_integrate_batch without a workspace argument, for callers that cannot
  * allocate device memory when they need the integrals: code that runs while

@@ -37,7 +37,7 @@ struct LoopGraph {
     cudaGraphExec_t exec = nullptr;
     const void* base = nullptr;        // workspace layout it was captured for
     int64_t n = 0, cap = 0;
-    int nb = 0;
+    int nb = 0, vstride = 0;
     int rule_n = 0, eval_fp32 = 0, max_rounds = 0;
     double cover = 0.0;
 };
@@ -67,11 +67,11 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t batches, totals, ls, trig, meta, born, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
         thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
-        err0, err1, nse0, nse1, evl, end;
+        err0, err1, nse0, nse1, evl, vval0, vval1, verr0, verr1, vsrc, end;
 };
 
 // Byte offsets of every workspace array for n integrals and capacity cap.
-Layout layout(int64_t n, int64_t cap)
+Layout layout(int64_t n, int64_t cap, bool group)
 {
     Layout L{};
     const int64_t nblk = (n + kScanBlock - 1) / kScanBlock + 1;
@@ -105,12 +105,19 @@ Layout layout(int64_t n, int64_t cap)
     L.nse0 = take(4 * cap);
     L.nse1 = take(4 * cap);
     L.evl = take(8 * cap);
+    if (group) {   // pair vectors (shared-partition mode)
+        L.vval0 = take(8 * kGroupPairs * cap);
+        L.vval1 = take(8 * kGroupPairs * cap);
+        L.verr0 = take(4 * kGroupPairs * cap);
+        L.verr1 = take(4 * kGroupPairs * cap);
+        L.vsrc = take(4 * cap);
+    }
     L.end = o;
     return L;
 }
 
-// Typed pointers into a workspace laid out by layout(n, cap).
-Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb)
+// Typed pointers into a workspace laid out by layout(n, cap, group).
+Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb, bool group, int nff)
 {
     Work w{};
     w.batches = reinterpret_cast<DevBatch*>(base + L.batches);
@@ -144,7 +151,31 @@ Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb)
     w.nse[0] = reinterpret_cast<float*>(base + L.nse0);
     w.nse[1] = reinterpret_cast<float*>(base + L.nse1);
     w.evl = reinterpret_cast<uint2*>(base + L.evl);
+    if (group) {
+        w.vval[0] = reinterpret_cast<double*>(base + L.vval0);
+        w.vval[1] = reinterpret_cast<double*>(base + L.vval1);
+        w.verr[0] = reinterpret_cast<float*>(base + L.verr0);
+        w.verr[1] = reinterpret_cast<float*>(base + L.verr1);
+        w.vsrc = reinterpret_cast<uint32_t*>(base + L.vsrc);
+        w.vstride = kGroupPairs;
+    }
+    w.nff = nff;
     return w;
+}
+
+// The largest pool capacity whose layout fits in ws_bytes.
+int64_t capacity_for(int64_t n, size_t ws_bytes, bool group)
+{
+    const size_t fixed = layout(n, 0, group).end;
+    // 64 bytes per region (7 arrays of 8 bytes, 2 of 4; group mode: + 2 x 81 x 12
+    // for the pair vectors + 4) plus up to 14 * 256 bytes of alignment
+    const size_t per = 64 + (group ? 2 * 12 * kGroupPairs + 4 : 0);
+    int64_t cap = ws_bytes > fixed + 14 * 256 ? int64_t((ws_bytes - fixed - 14 * 256) / per) : 0;
+    cap = std::min(cap, kMaxCapacity);
+    while (cap > 0 && layout(n, cap, group).end > ws_bytes) --cap;
+    // the estimate above reserves worst-case alignment; take what still fits
+    while (cap < kMaxCapacity && layout(n, cap + 1, group).end <= ws_bytes) ++cap;
+    return cap;
 }
 
 int fail(paid_ctx* ctx, int rc, const std::string& msg)
@@ -177,6 +208,8 @@ int check_options(const paid_options& o, std::string& why)
     if (o.pool_capacity < 0) { why = "pool_capacity must be >= 0"; return PAID_ERR_ARG; }
     if (o.timing != 0 && o.timing != 1) { why = "timing must be 0 or 1"; return PAID_ERR_ARG; }
     if (o.device_loop != 0 && o.device_loop != 1) { why = "device_loop must be 0 or 1"; return PAID_ERR_ARG; }
+    if (o.group_mode != 0 && o.group_mode != 1) { why = "group_mode must be 0 or 1"; return PAID_ERR_ARG; }
+    if (o.group_mode && o.eval_fp32) { why = "group_mode evaluates in FP64 (eval_fp32 = 0)"; return PAID_ERR_ARG; }
     return PAID_OK;
 }
 
@@ -195,6 +228,7 @@ int paid_options_default(paid_options* opt)
     opt->pool_capacity = 0;
     opt->timing = 0;
     opt->device_loop = 1;
+    opt->group_mode = 0;
     return PAID_OK;
 }
 
@@ -270,21 +304,14 @@ int paid_workspace_size(paid_ctx* ctx, int64_t n_integrals, int64_t pool_capacit
     const int64_t n0 = int64_t(1) << (2 * ctx->opt.init_level);
     if (pool_capacity < n_integrals * n0 || pool_capacity > kMaxCapacity)
         return fail(ctx, PAID_ERR_ARG, "pool_capacity must be >= n_integrals * 4^init_level and < 2^32");
-    *bytes = layout(n_integrals, pool_capacity).end;
+    *bytes = layout(n_integrals, pool_capacity, ctx->opt.group_mode != 0).end;
     return PAID_OK;
 }
 
 int paid_pool_capacity(paid_ctx* ctx, int64_t n_integrals, size_t ws_bytes, int64_t* capacity)
 {
     if (!ctx || !capacity || n_integrals < 0) return fail(ctx, PAID_ERR_ARG, "bad argument");
-    const size_t fixed = layout(n_integrals, 0).end;
-    // 64 bytes per region (7 arrays of 8 bytes, 2 of 4) plus up to 9 * 256 bytes of alignment
-    int64_t cap = ws_bytes > fixed + 9 * 256 ? int64_t((ws_bytes - fixed - 9 * 256) / 64) : 0;
-    cap = std::min(cap, kMaxCapacity);
-    while (cap > 0 && layout(n_integrals, cap).end > ws_bytes) --cap;
-    // the estimate above reserves worst-case alignment; take what still fits
-    while (cap < kMaxCapacity && layout(n_integrals, cap + 1).end <= ws_bytes) ++cap;
-    *capacity = cap;
+    *capacity = capacity_for(n_integrals, ws_bytes, ctx->opt.group_mode != 0);
     return PAID_OK;
 }
 
@@ -302,7 +329,7 @@ namespace {
 // Validates the batches, sizes the pool, lays out the workspace and uploads
 // the batch table.  n0 = regions per integral that the start needs at least.
 int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, size_t ws_bytes,
-            int64_t n0, cudaStream_t s, Work& w, int64_t& n, int64_t& cap)
+            int64_t n0, cudaStream_t s, Work& w, int64_t& n, int64_t& cap, bool group)
 {
     ctx->last_error.clear();
     ctx->stats = paid_stats{};
@@ -313,6 +340,7 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
     std::vector<DevBatch> hb;
     hb.reserve(nb);
     n = 0;
+    int64_t n_int = 0;
     for (int i = 0; i < nb; ++i) {
         const paid_batch& b = batches[i];
         if (b.kind < PAID_PH || b.kind > PAID_OVERLAP) return fail(ctx, PAID_ERR_ARG, "bad kind");
@@ -324,6 +352,10 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
             return fail(ctx, PAID_ERR_ARG, "tolerances must be >= 0");
         if (b.max_regions < nl0 || b.max_regions > kMaxRegionsPerIntegral)
             return fail(ctx, PAID_ERR_ARG, "max_regions must be in [4^init_level, 2^23]");
+        if (group && b.kind == PAID_MONOMIAL)
+            return fail(ctx, PAID_ERR_ARG, "group_mode takes the ph, pp and overlap kinds");
+        if (group && b.npairs > kGroupPairs)
+            return fail(ctx, PAID_ERR_ARG, "group_mode takes at most 81 pairs per batch");
         if (nbi == 0) continue;
         DevBatch d{};
         d.kind = b.kind;
@@ -335,7 +367,7 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
         d.rel_tol = b.rel_tol;
         d.abs_tol = b.abs_tol;
         d.max_regions = b.max_regions;
-        d.first = n;
+        d.first = n;   // units: integrals, or (group mode) q points
         d.q = b.q;
         d.lm = b.lm;
         d.values = b.values;
@@ -343,20 +375,20 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
         d.regions = b.regions;
         d.status = b.status;
         hb.push_back(d);
-        n += nbi;
+        n += group ? int64_t(b.nq) : nbi;
+        n_int += nbi;
     }
-    ctx->stats.n_integrals = n;
+    ctx->stats.n_integrals = n_int;
     if (n == 0) return PAID_OK;
     if (n > int64_t(0x7fffffff)) return fail(ctx, PAID_ERR_ARG, "too many integrals");
     if (!workspace) return fail(ctx, PAID_ERR_ARG, "null workspace");
     if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
         return fail(ctx, PAID_ERR_ARG, "workspace must be 256-byte aligned");
-    cap = 0;
-    paid_pool_capacity(ctx, n, ws_bytes, &cap);
+    cap = capacity_for(n, ws_bytes, group);
     if (o.pool_capacity > 0) cap = std::min(cap, o.pool_capacity);
     if (cap < n * n0) return fail(ctx, PAID_ERR_OOM, "workspace too small for the initial partition");
-    const Layout L = layout(n, cap);
-    w = make_work(static_cast<char*>(workspace), L, n, cap, int(hb.size()));
+    const Layout L = layout(n, cap, group);
+    w = make_work(static_cast<char*>(workspace), L, n, cap, int(hb.size()), group, ctx->nff);
     cudaError_t e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
@@ -369,23 +401,27 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
 // size the grids (exact counts in the host loop, bounds in the graph).  `ev`
 // (host loop with timing) gets marks between the kernel classes.
 cudaError_t launch_round(paid_ctx* ctx, const Work& w, int64_t hint_eval, int64_t hint_active,
-                         cudaGraphConditionalHandle h, int in_graph, cudaStream_t s,
-                         cudaEvent_t* ev)
+                         int64_t hint_pool, cudaGraphConditionalHandle h, int in_graph,
+                         cudaStream_t s, cudaEvent_t* ev)
 {
     const paid_options& o = ctx->opt;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     cudaError_t e;
+    const bool group = w.vstride > 0;
     if ((e = mark(0)) != cudaSuccess ||
-        (e = launch_eval(w, hint_eval, o.rule_n, o.eval_fp32, ctx->lat, s,
-                         ev && o.eval_fp32 ? ev[6] : nullptr)) != cudaSuccess ||
+        (e = group ? launch_eval_group(w, hint_eval, o.rule_n, ctx->lat, s)
+                   : launch_eval(w, hint_eval, o.rule_n, o.eval_fp32, ctx->lat, s,
+                                 ev && o.eval_fp32 ? ev[6] : nullptr)) != cudaSuccess ||
         (e = mark(1)) != cudaSuccess ||
-        (e = launch_reduce_test(w, hint_active, o.max_rounds, o.cover, s)) != cudaSuccess ||
+        (e = group ? launch_reduce_group(w, hint_active, o.max_rounds, o.cover, s)
+                   : launch_reduce_test(w, hint_active, o.max_rounds, o.cover, s)) != cudaSuccess ||
         (e = mark(2)) != cudaSuccess ||
         (e = launch_scan(w, hint_active, 0, s)) != cudaSuccess ||
         (e = launch_throttle(w, hint_active, s)) != cudaSuccess ||
         (e = launch_scan(w, hint_active, 1, s)) != cudaSuccess ||
         (e = mark(3)) != cudaSuccess ||
         (e = launch_split(w, hint_active, s)) != cudaSuccess ||
+        (e = launch_copy_vectors(w, hint_pool, s)) != cudaSuccess ||
         (e = mark(4)) != cudaSuccess ||
         (e = launch_control(w, h, in_graph, s)) != cudaSuccess)
         return e;
@@ -398,8 +434,9 @@ int64_t round_kernels(const paid_options& o, int64_t n_eval, int64_t n_active, b
 {
     const int64_t ev = n_eval > 0 ? (o.eval_fp32 ? 2 : 1) : 0;
     const int64_t slots = n_active > 0 ? 1 : 0;
-    // eval, reduce, scan (2), throttle, rescan (2), split, control, [wave]
-    return ev + slots + (slots + 1) + slots + (slots + 1) + slots + 1 + (in_graph ? 1 : 0);
+    // eval, reduce, scan (2), throttle, rescan (2), split, [vector copy], control, [wave]
+    return ev + slots + (slots + 1) + slots + (slots + 1) + slots + (o.group_mode ? slots : 0) + 1 +
+           (in_graph ? 1 : 0);
 }
 
 // The device-loop graph for this workspace layout and these options:
@@ -409,6 +446,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     const paid_options& o = ctx->opt;
     LoopGraph& G = ctx->loop;
     if (G.exec && G.base == w.batches && G.n == w.n && G.cap == w.cap && G.nb == w.nb &&
+        G.vstride == w.vstride &&
         G.rule_n == o.rule_n && G.eval_fp32 == o.eval_fp32 && G.max_rounds == o.max_rounds &&
         G.cover == o.cover) {
         *out = G.exec;
@@ -444,7 +482,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
         cudaGraphDestroy(g);
         return cuda_fail(ctx, e, "graph capture");
     }
-    const cudaError_t el = launch_round(ctx, w, w.cap, w.n, h, 1, ctx->capture, nullptr);
+    const cudaError_t el = launch_round(ctx, w, w.cap, w.n, w.cap, h, 1, ctx->capture, nullptr);
     cudaGraph_t captured = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(ctx->capture, &captured);
     if (el != cudaSuccess || ec != cudaSuccess) {
@@ -462,6 +500,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     G.n = w.n;
     G.cap = w.cap;
     G.nb = w.nb;
+    G.vstride = w.vstride;
     G.rule_n = o.rule_n;
     G.eval_fp32 = o.eval_fp32;
     G.max_rounds = o.max_rounds;
@@ -530,7 +569,8 @@ int run_loop(paid_ctx* ctx, const Work& w, int64_t admitted, int64_t n_eval, int
         L.n_active = admitted;
         for (;;) {
             const int64_t ne = L.n_eval, na = L.n_active;
-            if ((e = launch_round(ctx, w, ne, na, 0, 0, s, timed ? ev : nullptr)) != cudaSuccess)
+            if ((e = launch_round(ctx, w, ne, na, o.group_mode ? w.cap : 0, 0, 0, s,
+                                  timed ? ev : nullptr)) != cudaSuccess)
                 return cfail(e, "round");
             st.launches += round_kernels(o, ne, na, false);
             st.eval_launches += ne > 0 ? 1 : 0;
@@ -607,7 +647,7 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
     DeviceGuard guard(ctx->device);
     Work w{};
     int64_t n = 0, cap = 0;
-    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 1, s, w, n, cap);
+    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 1, s, w, n, cap, o.group_mode != 0);
     if (rc != PAID_OK || n == 0) return rc;
     if (cap < n0) return fail(ctx, PAID_ERR_OOM, "workspace too small for one integral's start");
     // first admission: as many integrals as the pool can take at ~16k regions
@@ -632,7 +672,8 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     DeviceGuard guard(ctx->device);
     Work w{};
     int64_t n = 0, cap = 0;
-    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 16, s, w, n, cap);
+    if (o.group_mode) return fail(ctx, PAID_ERR_ARG, "seeded starts take group_mode = 0");
+    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 16, s, w, n, cap, false);
     if (rc != PAID_OK || n == 0) return rc;
     cudaError_t e;
     // the slot scan reads its slot count from the loop state
@@ -681,7 +722,7 @@ int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npair
     b.status = reinterpret_cast<int32_t*>(out);
     Work w{};
     int64_t n = 0, cap = 0;
-    int rc = prepare(ctx, &b, 1, workspace, ws_bytes, 256, s, w, n, cap);
+    int rc = prepare(ctx, &b, 1, workspace, ws_bytes, 256, s, w, n, cap, false);
     if (rc != PAID_OK || n == 0) return rc;
     cudaError_t e;
     if ((e = launch_setup(w, 4, ctx->nff, 1, s)) != cudaSuccess ||
@@ -690,6 +731,50 @@ int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npair
         (e = launch_cell_map(w, out, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "cell errors");
     ctx->stats.region_evals = n * 256;
+    return PAID_OK;
+}
+
+int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int npairs,
+                      const int32_t* lm, int nreg, const int32_t* regions, double* q2N, double* dq,
+                      void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    ctx->last_error.clear();
+    if (kind != PAID_PH && kind != PAID_PP && kind != PAID_OVERLAP)
+        return fail(ctx, PAID_ERR_ARG, "kind must be ph, pp or overlap");
+    if (npairs < 1 || npairs > kGroupPairs || nreg < 0)
+        return fail(ctx, PAID_ERR_ARG, "npairs must be in 1..81 and nreg >= 0");
+    if (!(T > 0.0) || !is_finite_d(T)) return fail(ctx, PAID_ERR_ARG, "T must be > 0");
+    if (nreg == 0) return PAID_OK;
+    if (!q || !lm || !regions || !q2N || !dq || !workspace)
+        return fail(ctx, PAID_ERR_ARG, "null pointer");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+        return fail(ctx, PAID_ERR_ARG, "workspace must be 256-byte aligned");
+    const Layout Lw = layout(1, nreg, false);
+    if (Lw.end > ws_bytes) return fail(ctx, PAID_ERR_OOM, "workspace too small");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Work w = make_work(static_cast<char*>(workspace), Lw, 1, nreg, 1, false, ctx->nff);
+    DevBatch d{};
+    d.kind = kind;
+    d.nq = 1;
+    d.npairs = npairs;
+    d.T = T;
+    d.inv2T = 1.0 / (2.0 * T);
+    d.inv4T = 1.0 / (4.0 * T);
+    d.max_regions = nreg;
+    d.q = q;
+    d.lm = lm;
+    uint32_t* bad = reinterpret_cast<uint32_t*>(w.nse[1]);   // one flag per region
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(w.batches, &d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = launch_rule_setup(w, kind, q, regions, nreg, bad, s)) != cudaSuccess ||
+        (e = launch_state_init(w, 1, nreg, nreg, 1, 0, 1, s)) != cudaSuccess ||
+        (e = launch_eval_group(w, nreg, ctx->opt.rule_n, ctx->lat, s, q2N, dq)) != cudaSuccess ||
+        (e = launch_rule_flag(bad, nreg, npairs, q2N, dq, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "rule regions");
+    // like the integrate calls, return with the outputs complete
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "rule regions");
     return PAID_OK;
 }
 
@@ -792,22 +877,24 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     if (n > 0 && (!q || !lm || !values || !errors || !regions || !status)) return PAID_ERR_ARG;
     if (!(rel_tol >= 0.0) || !(abs_tol >= 0.0)) return PAID_ERR_ARG;
     if (max_regions < n0 || max_regions > kMaxRegionsPerIntegral) return PAID_ERR_ARG;
+    const bool group = o.group_mode != 0;
+    if (group && (kind == PAID_MONOMIAL || npairs > kGroupPairs)) return PAID_ERR_ARG;
     ctx->stats = paid_stats{};
     ctx->stats.n_integrals = n;
     if (n == 0) return PAID_OK;
+    const int64_t units = group ? int64_t(nq) : n;
 
     DeviceGuard guard(ctx->device);
     void* scratch = nullptr;
     if (static_scratch(ctx->device, &scratch) != cudaSuccess) return PAID_ERR_CUDA;
-    int64_t cap = 0;
-    paid_pool_capacity(ctx, n, kStaticScratchBytes, &cap);
+    int64_t cap = capacity_for(units, kStaticScratchBytes, group);
     if (o.pool_capacity > 0) cap = std::min(cap, o.pool_capacity);
-    if (cap < n * n0) return PAID_ERR_OOM;
+    if (cap < units * n0) return PAID_ERR_OOM;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const Layout L = layout(n, cap);
+    const Layout L = layout(units, cap, group);
     char* base = static_cast<char*>(scratch);
-    Work w = make_work(base, L, n, cap, 1);
+    Work w = make_work(base, L, units, cap, 1, group, ctx->nff);
 
     // The scratch keeps whatever the previous call left in it.  Every array
     // is written before it is read within a call; the totals block is cleared
@@ -835,5 +922,5 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
         return PAID_ERR_CUDA;
 
     ctx->stats.launches = 1;
-    return run_loop(ctx, w, n, n * n0, n * n0, o.init_level, s, true);
+    return run_loop(ctx, w, units, units * n0, units * n0, o.init_level, s, true);
 }

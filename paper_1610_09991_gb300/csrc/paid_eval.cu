@@ -46,6 +46,11 @@ __constant__ float2 c_sodf[2][kMaxLevel + 1][kMaxRuleN + 1];
 __constant__ float2 c_ffdf[9][3][3];              // c_ff as (hi, lo)
 __constant__ float c_wc32[2][kMaxRuleN + 1];
 __constant__ float c_ff32[9][3][3];
+// the non-zero terms of c_ff: f_n = sum_{k < c_ffn[n]} c_ffc[n][k] X_a Y_b, a = c_ffa, b = c_ffb
+__constant__ int c_ffn[9];
+__constant__ int c_ffa[9][2];
+__constant__ int c_ffb[9][2];
+__constant__ double c_ffc[9][2];
 
 // Clenshaw-Curtis weights for n intervals (n even), from the cosine-series
 // form of the rule: w_j = (c_j / n) (1 - sum_{k=1}^{n/2} b_k cos(2 k j pi/n)/(4k^2 - 1)).
@@ -60,6 +65,8 @@ static void cc_weights(int n, double* w)
         w[j] = ((j == 0 || j == n) ? 1.0 : 2.0) / n * acc;
     }
 }
+
+static cudaError_t group_kernel_attributes();
 
 cudaError_t init_rule_tables(int device)
 {
@@ -135,6 +142,22 @@ cudaError_t init_rule_tables(int device)
     if ((e = cudaMemcpyToSymbol(c_co, co, sizeof(co))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_so, so, sizeof(so))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_ff, ff, sizeof(ff))) != cudaSuccess) return e;
+    int ffn[9] = {}, ffa[9][2] = {}, ffb[9][2] = {};
+    double ffc[9][2] = {};
+    for (int n = 0; n < 9; ++n)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (ff[n][a][b] != 0.0) {
+                    ffa[n][ffn[n]] = a;
+                    ffb[n][ffn[n]] = b;
+                    ffc[n][ffn[n]] = ff[n][a][b];
+                    ++ffn[n];
+                }
+    if ((e = cudaMemcpyToSymbol(c_ffn, ffn, sizeof(ffn))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_ffa, ffa, sizeof(ffa))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_ffb, ffb, sizeof(ffb))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_ffc, ffc, sizeof(ffc))) != cudaSuccess) return e;
+    if ((e = group_kernel_attributes()) != cudaSuccess) return e;
     done[device] = true;
     return cudaSuccess;
 }
@@ -816,6 +839,204 @@ __global__ void __launch_bounds__(128) k_eval_fp64(Work w, Lattice lat)
         w.err[cur][pos] = fabs(q1 - q2);
         w.nse[cur][pos] = 0.0f;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-partition (group) evaluation: one region of a (kind, q) group gives
+// Q_N and Q_2N of every (l, m) pair of the group's batch at once.  With
+// g = (1, cos, sin) every form factor is f_n(k) = sum C_n[a][b] g_a(kx) g_b(ky),
+// so with k' = k + q (ph) or q - k (pp)
+//   f_l(k) f_m(k') = sum C_l[a][b] C_m[c][d] X_ac(kx) Y_bd(ky),
+//   X_ac = g_a(kx) g_c(kx'),   Y_bd = g_b(ky) g_d(ky'),
+// and the rule applied to every pair needs only the 81 moments
+//   M[ac][bd] = sum_i wx_i X_ac(x_i) R_i[bd],   R_i[bd] = sum_j wy_j F_ij Y_bd(y_j)
+// and their coarse-rule counterparts: the kernel F once per node, 2 x 729
+// FMA (fine) + 630 (coarse) for the moments, at most 4 terms per pair.
+// Block: NF = 2N+1 threads per region (thread i owns fine row i, and column
+// i for the shared column data), kGroupRegions<N> regions per block.
+template <int N> struct GroupShape;
+template <> struct GroupShape<4> { static constexpr int R = 14; };   // 126 threads
+template <> struct GroupShape<6> { static constexpr int R = 9; };    // 117 threads
+
+template <int N>
+struct GroupSmem {
+    static constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
+    double X[R][NF][9];      // X_ac at the fine rows
+    double Y[R][NF][9];      // Y_bd at the fine columns
+    double CY[R][NF][2];     // cos ky, cos ky' at the fine columns
+    double Rf[R][NF][9];     // fine row sums R_i[bd]
+    double Rc[R][N + 1][9];  // coarse row sums (even rows)
+    double Mf[R][9][9];      // fine moments
+    double Mc[R][9][9];      // coarse moments
+};
+
+template <int N>
+__global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1))
+k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
+{
+    constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GroupSmem<N>& S = *reinterpret_cast<GroupSmem<N>*>(smem_raw);
+    const int v = N == 4 ? 0 : 1;
+    const int cur = w.ls->cur;
+    const int64_t n_eval = w.ls->n_eval;
+    const int rho = threadIdx.x / NF, i = threadIdx.x % NF;
+    const double tA = -2.0 * lat.t, tB = -4.0 * lat.tp;
+    for (int64_t chunk = blockIdx.x; chunk * R < n_eval; chunk += gridDim.x) {
+        const int64_t t = chunk * R + rho;
+        const bool live = t < n_eval;
+        uint32_t pos = 0, g = 0, L = 0;
+        int kind = PH, P = 0;
+        const DevBatch* B = nullptr;
+        double A1 = 0.0, B1 = 0.0, A2 = 0.0, B2 = 0.0;
+        if (live) {
+            const uint2 e = w.evl[t];
+            pos = e.x;
+            g = e.y;
+            const uint64_t key = w.key[cur][pos];
+            L = key_level(key);
+            const uint32_t ix = key_ix(key), iy = key_iy(key);
+            const uint32_t mt = w.meta[g];
+            B = &w.batches[meta_batch(mt)];
+            kind = meta_kind(mt);
+            P = B->npairs;
+            const QTrig tq = w.trig[g];
+            const bool pp = kind == PP;
+            const double h = ldexp(1.0, -int(L));
+            double sxc, cxc, syc, cyc;
+            sincospi(fma(double(2 * ix + 1), h, -1.0), &sxc, &cxc);
+            sincospi(fma(double(2 * iy + 1), h, -1.0), &syc, &cyc);
+            const int ii = i <= N ? i : 2 * N - i;
+            const double co = c_co[v][L][ii];
+            const double so = i <= N ? c_so[v][L][ii] : -c_so[v][L][ii];
+            // row i (x) and column i (y) of the fine grid, and the shifted k'
+            const double cx = fma(cxc, co, -sxc * so), sx = fma(sxc, co, cxc * so);
+            const double cy = fma(cyc, co, -syc * so), sy = fma(syc, co, cyc * so);
+            const double cx2 = pp ? fma(tq.cqx, cx, tq.sqx * sx) : fma(cx, tq.cqx, -sx * tq.sqx);
+            const double sx2 = pp ? fma(tq.sqx, cx, -tq.cqx * sx) : fma(sx, tq.cqx, cx * tq.sqx);
+            const double cy2 = pp ? fma(tq.cqy, cy, tq.sqy * sy) : fma(cy, tq.cqy, -sy * tq.sqy);
+            const double sy2 = pp ? fma(tq.sqy, cy, -tq.cqy * sy) : fma(sy, tq.cqy, cy * tq.sqy);
+            const double gx[3] = {1.0, cx, sx}, gx2[3] = {1.0, cx2, sx2};
+            const double gy[3] = {1.0, cy, sy}, gy2[3] = {1.0, cy2, sy2};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    S.X[rho][i][3 * a + c] = gx[a] * gx2[c];
+                    S.Y[rho][i][3 * a + c] = gy[a] * gy2[c];
+                }
+            S.CY[rho][i][0] = cy;
+            S.CY[rho][i][1] = cy2;
+            // e = A + B cos ky along row i, for k and for k'
+            A1 = fma(tA, cx, -lat.mu);
+            B1 = fma(tB, cx, tA);
+            A2 = fma(tA, cx2, -lat.mu);
+            B2 = fma(tB, cx2, tA);
+        }
+        __syncthreads();
+        if (live) {
+            const double inv2T = B->inv2T, inv4T = B->inv4T;
+            double rf[9], rc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) { rf[k] = 0.0; rc[k] = 0.0; }
+#pragma unroll
+            for (int j = 0; j < NF; ++j) {
+                double F = 1.0;   // OVERLAP
+                if (kind != OVERLAP) {
+                    const double e1 = fma(B1, S.CY[rho][j][0], A1);
+                    const double e2 = fma(B2, S.CY[rho][j][1], A2);
+                    F = bubble_F(e1, kind == PP ? -e2 : e2, inv2T, inv4T);
+                }
+                const double wf = c_wf[v][j] * F;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) rf[k] = fma(wf, S.Y[rho][j][k], rf[k]);
+                if ((j & 1) == 0) {
+                    const double wc = c_wc[v][j >> 1] * F;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) rc[k] = fma(wc, S.Y[rho][j][k], rc[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = rf[k];
+            if ((i & 1) == 0)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) S.Rc[rho][i >> 1][k] = rc[k];
+        }
+        __syncthreads();
+        if (live && i < 9) {   // thread i: moments of ac = i
+            double mf[9], mc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) { mf[k] = 0.0; mc[k] = 0.0; }
+#pragma unroll
+            for (int r = 0; r < NF; ++r) {
+                const double xf = c_wf[v][r] * S.X[rho][r][i];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) mf[k] = fma(xf, S.Rf[rho][r][k], mf[k]);
+                if ((r & 1) == 0) {
+                    const double xc = c_wc[v][r >> 1] * S.X[rho][r][i];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) mc[k] = fma(xc, S.Rc[rho][r >> 1][k], mc[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) { S.Mf[rho][i][k] = mf[k]; S.Mc[rho][i][k] = mc[k]; }
+        }
+        __syncthreads();
+        if (live) {
+            const double scale = ldexp(0.25, -2 * int(L));
+            for (int p = i; p < P; p += NF) {
+                const int l = B->lm[2 * p], m = B->lm[2 * p + 1];
+                double q2 = 0.0, q1 = 0.0;
+                if (l >= 0 && m >= 0 && l < w.nff && m < w.nff) {
+                    for (int k1 = 0; k1 < c_ffn[l]; ++k1)
+                        for (int k2 = 0; k2 < c_ffn[m]; ++k2) {
+                            const double c = c_ffc[l][k1] * c_ffc[m][k2];
+                            const int ac = 3 * c_ffa[l][k1] + c_ffa[m][k2];
+                            const int bd = 3 * c_ffb[l][k1] + c_ffb[m][k2];
+                            q2 = fma(c, S.Mf[rho][ac][bd], q2);
+                            q1 = fma(c, S.Mc[rho][ac][bd], q1);
+                        }
+                }
+                q2 *= scale;
+                q1 *= scale;
+                if (rule_q2) {
+                    rule_q2[t * P + p] = q2;
+                    rule_d[t * P + p] = q1 - q2;
+                } else {
+                    const size_t o = size_t(pos) * size_t(w.vstride) + size_t(p);
+                    w.vval[cur][o] = q2;
+                    w.verr[cur][o] = float(fabs(q1 - q2));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static cudaError_t group_kernel_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_eval_group<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(GroupSmem<4>)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eval_group<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(sizeof(GroupSmem<6>)));
+    return e;
+}
+
+cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Lattice lat,
+                              cudaStream_t s, double* rule_q2, double* rule_d)
+{
+    if (hint_eval <= 0) return cudaSuccess;
+    if (rule_n == 4) {
+        constexpr int R = GroupShape<4>::R;
+        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, 152 * 32);
+        k_eval_group<4><<<int(blocks), R * 9, sizeof(GroupSmem<4>), s>>>(w, lat, rule_q2, rule_d);
+    } else {
+        constexpr int R = GroupShape<6>::R;
+        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, 152 * 32);
+        k_eval_group<6><<<int(blocks), R * 13, sizeof(GroupSmem<6>), s>>>(w, lat, rule_q2, rule_d);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_eval(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,

@@ -43,6 +43,9 @@ constexpr double kNoiseSigmas = 1.0;
 constexpr double kNoiseTol = 2.0;
 // threshold-bin marker in thr[].x: re-evaluate every region in FP64
 constexpr uint32_t kEscalate = 0xfeu;
+// Shared-partition (group) mode: most pairs per group, and the pair-vector
+// stride of a region in the pool
+constexpr int kGroupPairs = 81;
 
 enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3 };
 enum Status : int { CONVERGED = 0, BUDGET = 1, NONFINITE = 2, ROUNDCAP = 3, POOL = 4, RUNNING = -1 };
@@ -78,7 +81,8 @@ struct DevBatch {
     double T, inv2T, inv4T;
     double rel_tol, abs_tol;
     int64_t max_regions;
-    int64_t first;             // global index of the batch's first integral
+    int64_t first;             // global index of the batch's first unit (integral, or
+                               // in group mode its first (kind, q) group)
     const double* q;
     const int32_t* lm;
     double* values;
@@ -161,6 +165,16 @@ struct Work {
     double* err[2];
     float* nse[2];
     uint2* evl;
+    // group mode (vstride > 0): a unit is one (kind, q) group of a batch and
+    // every region carries the Q_2N and |Q_N - Q_2N| of each of the batch's
+    // pairs at vval/verr[pos * vstride + pair]; err[pos] holds the region's
+    // score for the selection (largest error over the pairs not yet
+    // converged, in units of each pair's tolerance)
+    double* vval[2];
+    float* verr[2];
+    uint32_t* vsrc;            // per next-pool slot: the region it copies (~0u: a new child)
+    int vstride;
+    int nff;
 };
 
 // ---- host-side launch wrappers (defined in the .cu files) -----------------
@@ -173,6 +187,11 @@ cudaError_t init_rule_tables(int device);
 // given, is recorded between the two
 cudaError_t launch_eval(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,
                         cudaStream_t s, cudaEvent_t mid = nullptr);
+// group mode: every pair of every region on the eval list (FP64).  With
+// rule_q2 / rule_d non-null, entry t's Q_2N and Q_N - Q_2N (times the region's
+// Jacobian) go to rule_q2 / rule_d[t * npairs + pair] instead of the pool.
+cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Lattice lat,
+                              cudaStream_t s, double* rule_q2 = nullptr, double* rule_d = nullptr);
 // paid_pool.cu
 // Initial loop state: counts of the first round, buffer 0, round 0.
 cudaError_t launch_state_init(const Work& w, int64_t n_active, int64_t n_eval, int64_t pool,
@@ -184,6 +203,13 @@ cudaError_t launch_setup(const Work& w, int L0, int nff, int fp64, cudaStream_t 
                          int64_t g1 = -1, int buf = 0, unsigned long long pool_base = 0,
                          unsigned long long eval_base = 0, unsigned long long act_base = 0,
                          int round = 0);
+// paid_rule_regions: unit 0 = the (kind, q) group, the caller's regions
+// (level, ix, iy) on the eval list; invalid regions are flagged in bad[] and
+// their outputs set to NaN by launch_rule_flag after the evaluation
+cudaError_t launch_rule_setup(const Work& w, int kind, const double* q, const int32_t* regions,
+                              int nreg, uint32_t* bad, cudaStream_t s);
+cudaError_t launch_rule_flag(const uint32_t* bad, int nreg, int npairs, double* q2, double* dq,
+                             cudaStream_t s);
 // the admission wave chosen by the last control step (w.ls->wave_*)
 cudaError_t launch_setup_wave(const Work& w, int64_t hint_wave, int nff, int fp64, cudaStream_t s);
 // pass 0: region counts into cnt_new / cnt_eval (slot = integral); pass 1 (after
@@ -194,10 +220,16 @@ cudaError_t launch_features(int kind, int nq, const double* q, int npairs, const
 cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s);
 cudaError_t launch_reduce_test(const Work& w, int64_t hint_active, int max_rounds, double cover,
                                cudaStream_t s);
+// group mode: reduce + test + selection, one block per active group
+cudaError_t launch_reduce_group(const Work& w, int64_t hint_active, int max_rounds, double cover,
+                                cudaStream_t s);
 // rescan = 1: only when the last scan's pool total exceeds the capacity (after
 // launch_throttle), and then it marks the round as throttled
 cudaError_t launch_scan(const Work& w, int64_t hint_active, int rescan, cudaStream_t s);
 cudaError_t launch_split(const Work& w, int64_t hint_active, cudaStream_t s);
+// group mode, after launch_split: the pair vectors of the regions the split
+// kept, into the next pool (hint_pool: bound on the next pool's regions)
+cudaError_t launch_copy_vectors(const Work& w, int64_t hint_pool, cudaStream_t s);
 // finish every slot still refining with `status` (after a stop)
 cudaError_t launch_finalize(const Work& w, int64_t hint_active, int status, cudaStream_t s);
 cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int status, cudaStream_t s);

@@ -22,6 +22,7 @@
 // One warp owns one integral in reduce/split; sums use a fixed lane order and
 // a xor-butterfly, and the histogram sums are integers, so a run is bitwise
 // reproducible.
+#include <algorithm>
 #include <cmath>
 
 #include <cuda_bf16.h>
@@ -83,11 +84,14 @@ __device__ void setup_one(const Work& w, int64_t g, int64_t g0, int L0, int nff,
     }
     const DevBatch& B = w.batches[b];
     const int64_t local = g - B.first;
-    const int64_t iq = local / B.npairs, ip = local % B.npairs;
+    const bool grp = w.vstride > 0;   // unit = (kind, q) group: every pair of the batch
+    const int64_t iq = grp ? local : local / B.npairs, ip = grp ? 0 : local % B.npairs;
     const double qx = B.q[2 * iq], qy = B.q[2 * iq + 1];
-    const int l = B.lm[2 * ip], m = B.lm[2 * ip + 1];
+    const int l = grp ? 0 : B.lm[2 * ip], m = grp ? 0 : B.lm[2 * ip + 1];
     int valid;
-    if (B.kind == MONOMIAL)
+    if (grp)
+        valid = 1;   // pairs are checked one by one in the group reduce
+    else if (B.kind == MONOMIAL)
         valid = l >= 0 && m >= 0 && l <= kMaxMonomialDegree && m <= kMaxMonomialDegree;
     else
         valid = l >= 0 && m >= 0 && l < nff && m < nff;
@@ -109,7 +113,10 @@ __device__ void setup_one(const Work& w, int64_t g, int64_t g0, int L0, int nff,
         }
     }
     w.active[buf][act_base + i] = uint32_t(g);
-    B.status[local] = RUNNING;
+    if (grp)
+        for (int p = 0; p < B.npairs; ++p) B.status[local * B.npairs + p] = RUNNING;
+    else
+        B.status[local] = RUNNING;
 }
 
 __global__ void k_setup(Work w, int64_t g0, int64_t g1, int L0, int nff, int fp64, int buf,
@@ -248,6 +255,53 @@ __global__ void k_control(Work w, cudaGraphConditionalHandle h, int in_graph)
 cudaError_t launch_control(const Work& w, cudaGraphConditionalHandle h, int in_graph, cudaStream_t s)
 {
     k_control<<<1, 1, 0, s>>>(w, h, in_graph);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// paid_rule_regions: one group (unit 0) and the caller's regions on the eval
+// list.  A region with level > kMaxLevel or an index outside 2^level is
+// evaluated as the level-0 square and flagged in bad[r].
+__global__ void k_rule_setup(Work w, int kind, const double* q, const int32_t* regions, int nreg,
+                             uint32_t* bad)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) {
+        double sx, cx, sy, cy;
+        sincos(q[0], &sx, &cx);
+        sincos(q[1], &sy, &cy);
+        w.trig[0] = QTrig{cx, sx, cy, sy};
+        w.meta[0] = make_meta(kind, 0, 0, 1, 0) | kMetaFp64;
+    }
+    if (r >= nreg) return;
+    const int L = regions[3 * r], ix = regions[3 * r + 1], iy = regions[3 * r + 2];
+    const bool ok = L >= 0 && L <= kMaxLevel && ix >= 0 && iy >= 0 &&
+                    int64_t(ix) < (int64_t(1) << L) && int64_t(iy) < (int64_t(1) << L);
+    w.key[0][r] = ok ? make_key(uint32_t(L), uint32_t(ix), uint32_t(iy)) : make_key(0, 0, 0);
+    w.evl[r] = make_uint2(uint32_t(r), 0u);
+    bad[r] = ok ? 0u : 1u;
+}
+
+__global__ void k_rule_flag(const uint32_t* bad, int nreg, int npairs, double* q2, double* dq)
+{
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= int64_t(nreg) * npairs) return;
+    if (bad[t / npairs]) { q2[t] = NAN; dq[t] = NAN; }
+}
+
+cudaError_t launch_rule_setup(const Work& w, int kind, const double* q, const int32_t* regions,
+                              int nreg, uint32_t* bad, cudaStream_t s)
+{
+    k_rule_setup<<<(nreg + 255) / 256, 256, 0, s>>>(w, kind, q, regions, nreg, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rule_flag(const uint32_t* bad, int nreg, int npairs, double* q2, double* dq,
+                             cudaStream_t s)
+{
+    const int64_t n = int64_t(nreg) * npairs;
+    if (n <= 0) return cudaSuccess;
+    k_rule_flag<<<int((n + 255) / 256), 256, 0, s>>>(bad, nreg, npairs, q2, dq);
     return cudaGetLastError();
 }
 
@@ -429,6 +483,41 @@ cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Threshold of the batched extract-max: walking the error histogram from its
+// largest bin, the regions whose summed error (in the histogram's integer
+// units) first reaches `target` are marked: whole bins below the threshold
+// bin, and the first `cap` regions (in pool order) of the threshold bin.
+// `allowed` (the region budget) caps the count, whole bins first.
+__device__ void select_regions(const Work& w, int64_t s, const unsigned long long* hsum,
+                               const uint32_t* hcnt, double target_units, int64_t allowed,
+                               int kmax, uint32_t cnt)
+{
+    const unsigned long long target =
+        target_units >= 9.0e18 ? ~0ull : (unsigned long long)fmax(target_units, 0.0);
+    unsigned long long cum = 0;
+    int64_t marked = 0;
+    int tb = kHistBins - 1;
+    for (int b = 0; b < kHistBins; ++b) {
+        cum += hsum[b];
+        marked += hcnt[b];
+        if (cum >= target) { tb = b; break; }
+    }
+    uint32_t cap;
+    if (marked > allowed) {           // region budget binds: whole bins while they fit
+        int64_t acc = 0;
+        int b = 0;
+        while (b < tb && acc + hcnt[b] <= allowed) { acc += hcnt[b]; ++b; }
+        tb = b;
+        cap = uint32_t(allowed - acc);
+        marked = allowed;
+    } else {
+        cap = hcnt[tb];
+    }
+    w.thr[s] = make_uint2(uint32_t(tb) | (uint32_t(kmax) << 8), cap);
+    w.cnt_new[s] = cnt + 3u * uint32_t(marked);
+    w.cnt_eval[s] = 4u * uint32_t(marked);
+}
+
 // ---------------------------------------------------------------------------
 // Per-integral reduction, convergence test and split selection.
 // force_status >= 0: finalize every slot that is still refining with that status.
@@ -518,34 +607,8 @@ k_reduce_test(Work w, int max_rounds, double cover, int force_status)
         }
     }
     __syncwarp();
-    if (lane == 0) {
-        const double tgt_d = (E - cover * tol) * unit;
-        const unsigned long long target =
-            tgt_d >= 9.0e18 ? ~0ull : (unsigned long long)fmax(tgt_d, 0.0);
-        unsigned long long cum = 0;
-        int64_t marked = 0;
-        int tb = kHistBins - 1;
-        for (int b = 0; b < kHistBins; ++b) {
-            cum += hsum[wib][b];
-            marked += hcnt[wib][b];
-            if (cum >= target) { tb = b; break; }
-        }
-        uint32_t cap;
-        const int64_t lim = allowed;
-        if (marked > lim) {           // region budget binds: whole bins while they fit
-            int64_t acc = 0;
-            int b = 0;
-            while (b < tb && acc + hcnt[wib][b] <= lim) { acc += hcnt[wib][b]; ++b; }
-            tb = b;
-            cap = uint32_t(lim - acc);
-            marked = lim;
-        } else {
-            cap = hcnt[wib][tb];
-        }
-        w.thr[s] = make_uint2(uint32_t(tb) | (uint32_t(kmax) << 8), cap);
-        w.cnt_new[s] = cnt + 3u * uint32_t(marked);
-        w.cnt_eval[s] = 4u * uint32_t(marked);
-    }
+    if (lane == 0)
+        select_regions(w, s, hsum[wib], hcnt[wib], (E - cover * tol) * unit, allowed, kmax, cnt);
 }
 
 cudaError_t launch_reduce_test(const Work& w, int64_t hint_active, int max_rounds, double cover,
@@ -554,6 +617,151 @@ cudaError_t launch_reduce_test(const Work& w, int64_t hint_active, int max_round
     if (hint_active <= 0) return cudaSuccess;
     const int64_t blocks = (hint_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, max_rounds, cover, -1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Shared-partition (group) reduce + test + selection, one block per active
+// group (kind, q) of a batch with P pairs.  Per pair c: V_c = sum Q_2N and
+// E_c = sum |Q_N - Q_2N| over the group's regions (each warp sums a fixed
+// residue class of regions, the warps' partial sums are added in warp order:
+// deterministic), tol_c = max(abs_tol, rel_tol |V_c|).  The group is done when
+// every valid pair has E_c <= tol_c.  Otherwise each region's score
+//   s_r = max over the pairs not yet converged of err_c,r / tol_c
+// goes to err[r], and the per-integral selection runs on the scores with unit
+// tolerance: the largest scores until their sum covers sum_r s_r - cover, so
+// that for every pair the unsplit regions carry at most cover * tol_c of its
+// error.  Finished groups write every pair's value, error, region count and
+// status (CONVERGED for the pairs that meet their tolerance).
+constexpr int kGroupWarps = 8;
+
+__global__ void __launch_bounds__(kGroupWarps * 32)
+k_reduce_group(Work w, int max_rounds, double cover, int force_status)
+{
+    __shared__ double pv[kGroupWarps][kGroupPairs], pe[kGroupWarps][kGroupPairs];
+    __shared__ double inv_tol[kGroupPairs];
+    __shared__ double ps[kGroupWarps], pm[kGroupWarps];
+    __shared__ unsigned long long hsum[kHistBins];
+    __shared__ uint32_t hcnt[kHistBins];
+    const LoopState& Ls = *w.ls;
+    const int cur = Ls.cur, round = Ls.round;
+    const int64_t s = blockIdx.x;
+    if (s >= Ls.n_active) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t g = w.active[cur][s];
+    const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
+    const DevBatch& B = w.batches[meta_batch(w.meta[g])];
+    const int P = B.npairs;
+    const size_t S = size_t(w.vstride);
+    const double* vval = w.vval[cur];
+    const float* verr = w.verr[cur];
+    const uint64_t* key = w.key[cur];
+
+    // pass 1: per-pair sums
+    {
+        double v[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
+        for (uint32_t j = wid; j < cnt; j += kGroupWarps) {
+            const size_t r = size_t(base + j) * S;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int c = lane + 32 * k;
+                if (c < P) { v[k] += vval[r + c]; e[k] += double(verr[r + c]); }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int c = lane + 32 * k;
+            if (c < P) { pv[wid][c] = v[k]; pe[wid][c] = e[k]; }
+        }
+    }
+    __syncthreads();
+    double V = 0.0, E = 0.0, tol = 0.0;
+    bool valid = false, finite = true, conv = true;
+    if (tid < P) {
+        for (int k = 0; k < kGroupWarps; ++k) { V += pv[k][tid]; E += pe[k][tid]; }
+        const int l = B.lm[2 * tid], m = B.lm[2 * tid + 1];
+        valid = l >= 0 && m >= 0 && l < w.nff && m < w.nff;
+        finite = isfinite(V) && isfinite(E);
+        tol = fmax(B.abs_tol, B.rel_tol * fabs(V));
+        conv = E <= tol;
+        inv_tol[tid] = (valid && finite && !conv) ? 1.0 / fmax(tol, 1e-300) : 0.0;
+    }
+    const bool any_nonfinite = __syncthreads_or(valid && !finite);
+    const bool all_conv = __syncthreads_and(!valid || (finite && conv));
+    const int64_t allowed = (B.max_regions - int64_t(cnt)) / 3;
+
+    int st = RUNNING;
+    if (force_status >= 0) st = force_status;
+    else if (any_nonfinite) st = NONFINITE;
+    else if (all_conv) st = CONVERGED;
+    else if (round - int(w.born[g]) >= max_rounds || round >= Ls.hard_rounds) st = ROUNDCAP;
+    else if (allowed <= 0) st = BUDGET;
+
+    // pass 2: region scores (lane 0 of each warp keeps the warp's sum and max)
+    double ssum = 0.0, smax = 0.0;
+    if (st == RUNNING) {
+        for (uint32_t j = wid; j < cnt; j += kGroupWarps) {
+            const size_t r = size_t(base + j) * S;
+            double sc = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int c = lane + 32 * k;
+                if (c < P) sc = fmax(sc, double(verr[r + c]) * inv_tol[c]);
+            }
+            sc = warp_max(sc);
+            if (lane == 0) {
+                w.err[cur][base + j] = sc;
+                ssum += sc;
+                if (key_level(key[base + j]) < uint32_t(kMaxLevel)) smax = fmax(smax, sc);
+            }
+        }
+        if (lane == 0) { ps[wid] = ssum; pm[wid] = smax; }
+    }
+    __syncthreads();
+    double Ssum = 0.0, Smax = 0.0;
+    if (st == RUNNING) {
+        for (int k = 0; k < kGroupWarps; ++k) { Ssum += ps[k]; Smax = fmax(Smax, pm[k]); }
+        if (!(Smax > 0.0)) st = BUDGET;   // nothing left to split
+    }
+
+    if (st != RUNNING) {
+        if (tid < P) {
+            const int64_t o = (int64_t(g) - B.first) * P + tid;
+            B.values[o] = valid ? V : NAN;
+            B.errors[o] = valid ? E : NAN;
+            B.regions[o] = cnt;
+            B.status[o] = !valid || !finite ? NONFINITE : (conv ? CONVERGED : st);
+        }
+        if (tid == 0) {
+            if (st == ROUNDCAP && force_status < 0) atomicAdd(&w.totals->roundcap, 1ull);
+            w.cnt_new[s] = 0;
+            w.cnt_eval[s] = 0;
+        }
+        return;
+    }
+
+    // pass 3: histogram of the scores in quarter octaves below the largest
+    for (int b = tid; b < kHistBins; b += blockDim.x) { hsum[b] = 0ull; hcnt[b] = 0u; }
+    __syncthreads();
+    const int kmax = log_key(Smax);
+    const double unit = ldexp(1.0, 40) / Smax;
+    for (uint32_t j = tid; j < cnt; j += blockDim.x) {
+        const double e = w.err[cur][base + j];
+        if (e > 0.0 && key_level(key[base + j]) < uint32_t(kMaxLevel)) {
+            const int bin = min(kHistBins - 1, kmax - log_key(e));
+            atomicAdd(&hsum[bin], (unsigned long long)(e * unit));
+            atomicAdd(&hcnt[bin], 1u);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) select_regions(w, s, hsum, hcnt, (Ssum - cover) * unit, allowed, kmax, cnt);
+}
+
+cudaError_t launch_reduce_group(const Work& w, int64_t hint_active, int max_rounds, double cover,
+                                cudaStream_t s)
+{
+    if (hint_active <= 0) return cudaSuccess;
+    k_reduce_group<<<int(hint_active), kGroupWarps * 32, 0, s>>>(w, max_rounds, cover, -1);
     return cudaGetLastError();
 }
 
@@ -607,10 +815,14 @@ __global__ void k_mark_unadmitted(Work w, int64_t g0, int64_t g1, int status)
     }
     const DevBatch& B = w.batches[b];
     const int64_t local = g - B.first;
-    B.values[local] = NAN;
-    B.errors[local] = NAN;
-    B.regions[local] = 0;
-    B.status[local] = status;
+    const int width = w.vstride > 0 ? B.npairs : 1;   // outputs of the unit
+    for (int p = 0; p < width; ++p) {
+        const int64_t o = local * width + p;
+        B.values[o] = NAN;
+        B.errors[o] = NAN;
+        B.regions[o] = 0;
+        B.status[o] = status;
+    }
 }
 
 cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int status, cudaStream_t s)
@@ -623,8 +835,12 @@ cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int st
 cudaError_t launch_finalize(const Work& w, int64_t hint_active, int status, cudaStream_t s)
 {
     if (hint_active <= 0) return cudaSuccess;
-    const int64_t blocks = (hint_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, 0, 0.0, status);
+    if (w.vstride > 0) {
+        k_reduce_group<<<int(hint_active), kGroupWarps * 32, 0, s>>>(w, 0, 0.0, status);
+    } else {
+        const int64_t blocks = (hint_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, 0, 0.0, status);
+    }
     return cudaGetLastError();
 }
 
@@ -837,6 +1053,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w)
             val_n[p] = v;
             err_n[p] = e;
             nse_n[p] = nz;
+            if (w.vsrc) w.vsrc[p] = base + j;
         }
         if (mark) {
             const uint32_t L = key_level(k), ix = key_ix(k), iy = key_iy(k);
@@ -845,6 +1062,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w)
             for (uint32_t c = 0; c < 4; ++c) {
                 key_n[p + c] = make_key(L + 1, 2 * ix + (c >> 1), 2 * iy + (c & 1));
                 w.evl[q + c] = make_uint2(uint32_t(p + c), g);
+                if (w.vsrc) w.vsrc[p + c] = 0xffffffffu;
             }
         }
         run += tot;
@@ -855,6 +1073,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w)
         w.seg_count[g] = nnew;
         w.active[nxt][abase] = g;
     }
+}
+
+// Group mode: every kept region's pair vectors to its slot in the next pool
+// (one thread per (slot, pair) element: coalesced on both sides).
+__global__ void k_copy_vectors(Work w)
+{
+    const int cur = w.ls->cur, nxt = cur ^ 1;
+    const size_t S = size_t(w.vstride);
+    const size_t total = size_t(w.totals->pool) * S;
+    const size_t stride = size_t(gridDim.x) * blockDim.x;
+    for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const size_t p = idx / S, c = idx - p * S;
+        const uint32_t src = w.vsrc[p];
+        if (src == 0xffffffffu) continue;
+        w.vval[nxt][idx] = w.vval[cur][size_t(src) * S + c];
+        w.verr[nxt][idx] = w.verr[cur][size_t(src) * S + c];
+    }
+}
+
+cudaError_t launch_copy_vectors(const Work& w, int64_t hint_pool, cudaStream_t s)
+{
+    if (hint_pool <= 0 || w.vstride <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((hint_pool * w.vstride + 255) / 256, 152 * 16);
+    k_copy_vectors<<<int(blocks), 256, 0, s>>>(w);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_split(const Work& w, int64_t hint_active, cudaStream_t s)

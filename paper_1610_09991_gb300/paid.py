@@ -30,14 +30,15 @@ EXPORTS = ("paid_options_default", "paid_create", "paid_destroy", "paid_workspac
            "paid_integrate_multi_seeded", "paid_cell_errors", "paid_last_stats",
            "paid_error_string", "paid_last_error", "paid_mlp_param_count",
            "paid_mlp_workspace_size", "paid_mlp_init", "paid_mlp_features", "paid_mlp_forward",
-           "paid_mlp_grad", "paid_mlp_adamw")
+           "paid_mlp_grad", "paid_mlp_adamw", "paid_rule_regions")
 
 
 class paid_options(ctypes.Structure):
     _fields_ = [("rule_n", ctypes.c_int), ("init_level", ctypes.c_int),
                 ("eval_fp32", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("cover", ctypes.c_double), ("pool_capacity", ctypes.c_int64),
-                ("timing", ctypes.c_int), ("device_loop", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("device_loop", ctypes.c_int),
+                ("group_mode", ctypes.c_int)]
 
 
 class paid_stats(ctypes.Structure):
@@ -100,6 +101,7 @@ def load(path: str = LIB_PATH):
         lib.paid_integrate_multi_seeded.argtypes = [P, ctypes.POINTER(paid_batch), I, P, D, P,
                                                     ctypes.c_size_t, P]
         lib.paid_cell_errors.argtypes = [P, I, I, P, I, P, D, P, P, ctypes.c_size_t, P]
+        lib.paid_rule_regions.argtypes = [P, I, D, P, I, P, I, P, P, P, P, ctypes.c_size_t, P]
         lib.paid_mlp_param_count.argtypes = [ctypes.POINTER(I64)]
         lib.paid_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(ctypes.c_size_t)]
         lib.paid_mlp_init.argtypes = [P, ctypes.c_uint64, P]
@@ -226,6 +228,30 @@ class Context:
         """As integrate_multi, with the initial partition from proposal maps
         (cuda float32 [n, 256], global batch order; None = uniform level 4)."""
         return self._integrate(batches, pool_capacity, stream, (proposal, float(rate)))
+
+    def rule_regions(self, kind, q, lm, T, regions, stream=None):
+        """The nested rule on given regions for every pair of one (kind, q).
+
+        q: cuda float64 [2]; lm: cuda int32 [npairs, 2]; regions: cuda int32
+        [nreg, 3] = (level, ix, iy).  Returns (q2N, dq), cuda float64
+        [nreg, npairs]: Q_2N and Q_N - Q_2N times the region's Jacobian."""
+        torch = _torch()
+        nreg, npairs = regions.shape[0], lm.shape[0]
+        q2 = torch.empty((nreg, npairs), dtype=torch.float64, device=self.torch_device)
+        dq = torch.empty_like(q2)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.torch_device)
+        # (a group-mode context reports a larger layout: still enough)
+        need = self.workspace_size(1, max(nreg, 16))
+        ws = self._ws if self._ws is not None and self._ws.numel() >= need else \
+            torch.empty(need, dtype=torch.uint8, device=self.torch_device)
+        rc = self._lib.paid_rule_regions(self._h, int(kind), float(T), q.data_ptr(), npairs,
+                                         lm.data_ptr(), nreg, regions.data_ptr(), q2.data_ptr(),
+                                         dq.data_ptr(), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                         ctypes.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, self.last_error())
+        return q2, dq
 
     def cell_errors(self, kind, q, lm, T, stream=None):
         """Relative log10 error maps of the uniform level-4 grid: cuda float32 [n, 256]."""

@@ -1,0 +1,198 @@
+"""Shared-partition (group) mode against the FP64 oracle.
+
+Region level: the group kernel's Q_N and Q_2N of every pair on a region,
+computed from separable moments, against the oracle's direct nested rule on
+the same region (Sec. 3), pair by pair.  The two sum the same nodes in a
+different order, so they agree to rounding.
+
+Integral level: every integral of a group meets its own tolerance on the
+group's shared partition, so the group results satisfy the same parity
+criterion against the per-integral oracle as the per-integral mode
+(test_gpu_parity.py): 2 max(rel_tol |v|, abs_tol) + 1e-12, disagreements
+decided by the converged brute-force trapezoid.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_09991_gb300 import workloads as W
+from tests.test_gpu_parity import assert_parity, batch_ident, flat_ident
+
+pytestmark = pytest.mark.gpu
+
+LAT = W.LATTICE
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def paid(torch):
+    from paper_1610_09991_gb300 import build as B
+    B.build()
+    from paper_1610_09991_gb300 import paid as P
+    return P
+
+
+def _dev(torch, a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def _run(paid, torch, ctx, batches, pool_capacity=None):
+    dbs = [dict(kind=b.kind, T=b.T, q=_dev(torch, b.q, torch.float64),
+                lm=_dev(torch, b.lm, torch.int32), rel_tol=b.rel_tol, abs_tol=b.abs_tol,
+                max_regions=b.max_regions) for b in batches]
+    outs = ctx.integrate_multi(dbs, pool_capacity=pool_capacity)
+    torch.cuda.synchronize()
+    return [tuple(x.cpu().numpy() for x in (r.values, r.errors, r.regions, r.status)) for r in outs]
+
+
+@pytest.mark.parametrize("kind,T", [(W.PH, 0.05), (W.PP, 0.05), (W.PH, 0.7), (W.OVERLAP, 1.0)])
+def test_rule_regions_match_the_oracle_rule(paid, torch, kind, T):
+    rng = np.random.default_rng(17 + kind)
+    ctx = paid.Context(*LAT, ffset=9)
+    lm = W.all_pairs(9)
+    regs = [(0, 0, 0), (1, 1, 0), (2, 3, 1)]
+    for L in (3, 5, 8, 12, 20, 29):
+        for _ in range(3):
+            regs.append((L, int(rng.integers(0, 2 ** L)), int(rng.integers(0, 2 ** L))))
+    regs.append((30, 0, 0))       # invalid level
+    regs.append((2, 4, 0))        # index outside 2^level
+    regions = np.array(regs, dtype=np.int32)
+    for q in (np.array([0.3, -2.1]), np.array([math.pi, 0.0])):
+        q2, dq = ctx.rule_regions(kind, _dev(torch, q, torch.float64), _dev(torch, lm, torch.int32),
+                                  T, _dev(torch, regions, torch.int32))
+        q2, dq = q2.cpu().numpy(), dq.cpu().numpy()
+        assert np.all(np.isnan(q2[-2:])) and np.all(np.isnan(dq[-2:]))
+        for r, (L, ix, iy) in enumerate(regs[:-2]):
+            ref = np.array([oracle.region_eval(kind, q, int(l), int(m), T, LAT, L, ix, iy)
+                            for l, m in lm])          # (Q_N, Q_2N) per pair
+            scale = np.abs(ref).max() + 1e-300
+            assert np.all(np.abs(q2[r] - ref[:, 1]) <= 1e-12 * scale), (L, ix, iy)
+            assert np.all(np.abs(dq[r] - (ref[:, 0] - ref[:, 1])) <= 1e-12 * scale), (L, ix, iy)
+
+
+def test_rule_regions_rule_n6(paid, torch):
+    ctx = paid.Context(*LAT, ffset=9, rule_n=6)
+    lm = W.all_pairs(9)[::4]
+    q = np.array([1.1, 0.4])
+    regs = np.array([(0, 0, 0), (4, 3, 9), (11, 1000, 17)], dtype=np.int32)
+    q2, dq = ctx.rule_regions(W.PP, _dev(torch, q, torch.float64), _dev(torch, lm, torch.int32),
+                              0.1, _dev(torch, regs, torch.int32))
+    q2, dq = q2.cpu().numpy(), dq.cpu().numpy()
+    for r, (L, ix, iy) in enumerate(regs):
+        ref = np.array([oracle.region_eval(W.PP, q, int(l), int(m), 0.1, LAT, int(L), int(ix),
+                                           int(iy), rule_n=6) for l, m in lm])
+        scale = np.abs(ref).max() + 1e-300
+        assert np.all(np.abs(q2[r] - ref[:, 1]) <= 1e-12 * scale)
+        assert np.all(np.abs(dq[r] - (ref[:, 0] - ref[:, 1])) <= 1e-12 * scale)
+
+
+def test_group_first_shell_matches_oracle(paid, torch):
+    w = W.config_first_shell()
+    b = w.batches[0]
+    ctx = paid.Context(*w.lattice, ffset=5, group_mode=1)
+    (g,) = _run(paid, torch, ctx, [b])
+    o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol, b.max_regions)
+    assert np.all(g[3] == 0)
+    assert assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b)) >= b.n - 1
+    # every integral within its own tolerance; one region count per group
+    assert np.all(g[1] <= np.maximum(b.abs_tol, b.rel_tol * np.abs(g[0])))
+    r = g[2].reshape(16, 25)
+    assert np.all(r == r[:, :1]) and np.all((r - 16) % 3 == 0)
+    st = ctx.last_stats()
+    assert st["region_evals"] >= r[:, 0].sum()
+
+
+@pytest.mark.parametrize("T", [0.05, 0.5])
+def test_group_flow_step_small_grid_matches_oracle(paid, torch, T):
+    w = W.config_flow_step(T=T, nq=4)
+    ctx = paid.Context(*w.lattice, ffset=9, group_mode=1)
+    gs = _run(paid, torch, ctx, w.batches)
+    for b, g in zip(w.batches, gs):
+        assert np.all(np.isin(g[3], [0, 1]))
+        o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
+                                   b.max_regions)
+        n = assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b))
+        assert n >= 0.9 * b.n
+
+
+def test_group_full_flow_step_sampled(paid, torch):
+    # all 93,312 integrals of the flow step in 1152 groups, checked on a seeded
+    # sample that the oracle computes one by one, and by the pp symmetry
+    w = W.config_flow_step()
+    ctx = paid.Context(*w.lattice, ffset=9, group_mode=1)
+    gs = _run(paid, torch, ctx, w.batches)
+    g = tuple(np.concatenate([x[i] for x in gs]) for i in range(4))
+    flat = W.flatten(w)
+    idx = W.sample_indices(w.n, 240, seed=1234)
+    o = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
+                              flat["T"][idx], LAT, 1e-6, 1e-10, 100000)
+    assert_parity(tuple(x[idx] for x in g), o, 1e-6, 1e-10, flat_ident(flat, idx))
+    v, e, r, s = g
+    assert np.all(np.isin(s, [0, 1]))
+    conv = s == 0
+    assert np.all(e[conv] <= np.maximum(1e-10, 1e-6 * np.abs(v[conv])))
+    vpp = v[w.batches[0].n:].reshape(576, 9, 9)
+    tol = 2 * np.maximum(1e-6 * np.abs(vpp), 1e-10) + 1e-12
+    assert np.all(np.abs(vpp - vpp.transpose(0, 2, 1)) <= tol + tol.transpose(0, 2, 1))
+
+
+def test_group_device_loop_matches_host_loop(paid, torch):
+    w = W.config_flow_step(T=0.1, nq=2)
+    a = _run(paid, torch, paid.Context(*LAT, ffset=9, group_mode=1, device_loop=1), w.batches)
+    b = _run(paid, torch, paid.Context(*LAT, ffset=9, group_mode=1, device_loop=0), w.batches)
+    for x, y in zip(a, b):
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v)
+
+
+def test_group_streaming_small_pool(paid, torch):
+    b = W.Batch(W.PH, 0.2, W.q_grid_bz(4), W.all_pairs(9)[::5], 1e-6, 1e-10, 100000)
+    ctx = paid.Context(*LAT, ffset=9, group_mode=1)
+    (full,) = _run(paid, torch, ctx, [b])
+    peak = ctx.last_stats()["peak_pool"]
+    cap = max(peak // 3, 2000)
+    (g,) = _run(paid, torch, ctx, [b], pool_capacity=cap)
+    st = ctx.last_stats()
+    assert ctx.last_rc == paid.OK and st["peak_pool"] <= cap < peak
+    assert np.array_equal(g[3], full[3])
+    tol = np.maximum(1e-6 * np.abs(full[0]), 1e-10)
+    assert np.all(np.abs(g[0] - full[0]) <= 2 * tol + 1e-12)
+
+
+def test_group_edge_cases(paid, torch):
+    ctx = paid.Context(*LAT, ffset=5, group_mode=1)
+    q = np.array([(0.3, 1.2), (-2.0, 0.5)])
+    lm = np.array([(0, 0), (9, 1), (2, 2)], dtype=np.int32)      # (9, 1) is invalid
+    (g,) = _run(paid, torch, ctx, [W.Batch(W.PH, 0.5, q, lm)])
+    assert list(g[3]) == [0, 2, 0, 0, 2, 0] and np.isnan(g[0][1])
+    (g,) = _run(paid, torch, ctx, [W.Batch(W.PH, float("nan"), q[:1], lm[:1])])
+    assert g[3][0] == 2
+    # tiny budget: the group stops at <= max_regions, pairs that met their
+    # tolerance report CONVERGED, the others BUDGET
+    (g,) = _run(paid, torch, ctx, [W.Batch(W.PH, 0.01, q[:1], np.array([(1, 2), (0, 0)]),
+                                           1e-12, 1e-16, 100)])
+    assert np.all(np.isin(g[3], [0, 1])) and np.any(g[3] == 1) and np.all(g[2] <= 100)
+    # the monomial kind has no form-factor structure: refused in group mode
+    with pytest.raises(paid.PaidError):
+        _run(paid, torch, ctx, [W.Batch(W.MONOMIAL, 1.0, np.zeros((1, 2)), np.array([(2, 4)]))])
+
+
+def test_group_static_entry(paid, torch):
+    b = W.Batch(W.PP, 0.5, W.q_grid_bz(2), W.all_pairs(9), 1e-6, 1e-10, 20000)
+    ctx = paid.Context(*LAT, ffset=9, group_mode=1)
+    (g,) = _run(paid, torch, ctx, [b])
+    r = ctx.integrate_batch_static(b.kind, _dev(torch, b.q, torch.float64),
+                                   _dev(torch, b.lm, torch.int32), b.T, b.rel_tol, b.abs_tol,
+                                   b.max_regions)
+    torch.cuda.synchronize()
+    assert np.array_equal(r.values.cpu().numpy(), g[0])
+    assert np.array_equal(r.status.cpu().numpy(), g[3])
