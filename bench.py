@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "converged BZ loop integrals/s at rel tol 1e-6"
+METRIC = "converged BZ loop integrals/s at rel tol 1e-6, learned+batched vs plain FP64"
 UNIT = "integrals/s"
 # FP64 flops per integrand node of the FP64 region-evaluation kernel
 # (k_eval_fp64, N = 4, 81 nodes per region): per region 4117 DFMA (2 flops),
@@ -60,10 +60,15 @@ def parse_args():
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
     ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep"],
                     default="flow_step")
-    ap.add_argument("--path", choices=["plain", "fp32", "learned", "group"], default="group",
-                    help="plain: FP64 evaluation from the uniform start; fp32: FP32 / float-float "
-                         "evaluation; learned: fp32 plus the learned proposal's seeded start; "
-                         "group: FP64, one shared partition per (kind, q) for all its pairs")
+    ap.add_argument("--path", choices=["group", "learned", "plain", "fp32", "learned_fp32"],
+                    default="group",
+                    help="group: one shared partition per (kind, q) for all its pairs, FP64, "
+                         "uniform start; learned: group with the learned proposal's seeded "
+                         "start; plain: one partition per integral, FP64, uniform start; "
+                         "fp32: per integral, FP32 / float-float evaluation; learned_fp32: "
+                         "fp32 with the seeded start")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the extra timed steps of the learned_fp32 path")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timed FP64 comparison step of an FP32 run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -283,8 +288,9 @@ def run_paid(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w, ff = workload(args.workload)
-    args.eval = "fp64" if args.path in ("plain", "group") else "fp32"
-    group = 1 if args.path == "group" else 0
+    args.eval = "fp64" if args.path in ("plain", "group", "learned") else "fp32"
+    group = 1 if args.path in ("group", "learned") else 0
+    learned = args.path in ("learned", "learned_fp32")
     ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1,
                     eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group)
     dev = torch.device("cuda", local)
@@ -305,11 +311,13 @@ def run_paid(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peaks = fp64_peak(local)
     prop_info, prop, rate = None, None, None
-    if args.path == "learned":
+    if learned:
         from paper_1610_09991_gb300 import proposal as PR
         prop, hist, t_train = PR.train_default(device=local, n_draws=24, nq=8, epochs=20)
         t0 = time.perf_counter()
-        rate, calib = PR.calibrate_default(prop, device=local)
+        rate, calib = PR.calibrate_default(prop, device=local,
+                                           eval_fp32=1 if args.eval == "fp32" else 0,
+                                           group_mode=group)
         t_cal = time.perf_counter() - t0
         prop_info = {"train_seconds": t_train, "calibrate_seconds": t_cal,
                      "training_rows": 24 * 2 * 64 * 81, "draws": "seeds 0..23 of "
@@ -437,9 +445,12 @@ def run_paid(args):
         "path": {"plain": "plain FP64 GPU cubature from the uniform level-2 start",
                  "group": "FP64 GPU cubature, one shared partition per (kind, q) serving all "
                           "81 (l, m) pairs, each pair to its own tolerance",
+                 "learned": "learned proposal seeding + batched FP64 GPU cubature, one shared "
+                            "partition per (kind, q) serving all 81 (l, m) pairs, each pair "
+                            "to its own tolerance",
                  "fp32": "batched GPU cubature, FP32 / float-float integrand, FP64 sums",
-                 "learned": "learned proposal seeding + batched GPU cubature, FP32 / "
-                            "float-float integrand, FP64 sums"}[args.path],
+                 "learned_fp32": "learned proposal seeding + batched GPU cubature, FP32 / "
+                                 "float-float integrand, FP64 sums"}[args.path],
         "proposal": prop_info,
         "budget_integrals_per_step": agg["budget"] / args.steps,
         "region_evals_per_s": agg["region_evals"] * world / elapsed,
@@ -455,6 +466,9 @@ def run_paid(args):
     }
     vals = torch.cat([o.values for o in outs]).cpu().numpy()
     stats = torch.cat([o.status for o in outs]).cpu().numpy()
+    # each context below sizes its own pool from the free memory
+    del step_outs, outs
+    ctx.release_workspace()
     if not args.no_device_loop:
         # the same steps with the refinement loop on the device: one CUDA graph
         # launch per call (conditional WHILE node), no per-round host sync and
@@ -481,7 +495,7 @@ def run_paid(args):
         torch.cuda.synchronize()
         tg = g0.elapsed_time(g1) / 1e3
         gconv = sum(int((torch.cat([o.status for o in go]) == 0).sum()) for go in gouts)
-        same = all(torch.equal(torch.cat([a.values for a in go]), torch.cat([b.values for b in outs]))
+        same = all(np.array_equal(torch.cat([a.values for a in go]).cpu().numpy(), vals)
                    for go in gouts)
         line["device_loop"] = {
             "value": gconv * world / tg, "unit": UNIT, "ms_per_step": 1e3 * tg / args.steps,
@@ -489,7 +503,9 @@ def run_paid(args):
             "kernels_per_step": sum(x["launches"] for x in gst) / args.steps,
             "rounds_per_step": sum(x["rounds"] for x in gst) / args.steps,
             "values_identical_to_host_loop": bool(same)}
-        del cg
+        del gouts
+        cg.close()
+        torch.cuda.empty_cache()
     if args.path not in ("plain",) and not args.no_compare:
         # the plain FP64 GPU path on the same batch, one timed step
         c64 = P.Context(*w.lattice, ffset=ff, device=local, timing=1)
@@ -504,6 +520,9 @@ def run_paid(args):
         v64 = torch.cat([o.values for o in o64]).cpu().numpy()
         s64 = torch.cat([o.status for o in o64]).cpu().numpy()
         st64 = c64.last_stats()
+        del o64
+        c64.close()
+        torch.cuda.empty_cache()
         line["plain_fp64"] = {"value": float((s64 == 0).sum()) * world / t64, "unit": UNIT,
                               "ms_per_step": 1e3 * t64, "region_evals": st64["region_evals"],
                               "eval_ms": st64["eval_ms"]}
@@ -514,6 +533,46 @@ def run_paid(args):
         line["accuracy_vs_fp64_gpu"] = accuracy(vals, stats, v64, s64, w.batches[0].rel_tol,
                                                 w.batches[0].abs_tol, "FP64 GPU path, every integral",
                                                 ident_all, w.lattice)
+        if args.path == "group" and not args.no_learned:
+            # the learned proposal's form: one partition per integral seeded by
+            # the trained network, FP32 / float-float integrand, FP64 sums
+            from paper_1610_09991_gb300 import proposal as PR
+            lprop, lhist, lt = PR.train_default(device=local, n_draws=24, nq=8, epochs=20)
+            lrate, _ = PR.calibrate_default(lprop, device=local, eval_fp32=1, group_mode=0)
+            cl = P.Context(*w.lattice, ffset=ff, device=local, timing=1, eval_fp32=1)
+
+            def lstep():
+                flush.fill_(1)
+                return cl.integrate_multi_seeded(dbs, PR.predict(lprop, cl, dbs), lrate,
+                                                 stream=stream)
+
+            for _ in range(max(1, args.warmup)):
+                lstep()
+            torch.cuda.synchronize()
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            louts = [lstep() for _ in range(args.steps)]
+            l1.record(stream)
+            torch.cuda.synchronize()
+            tl = l0.elapsed_time(l1) / 1e3
+            lconv = sum(int((torch.cat([o.status for o in lo]) == 0).sum()) for lo in louts)
+            lv = torch.cat([o.values for o in louts[-1]]).cpu().numpy()
+            ls = torch.cat([o.status for o in louts[-1]]).cpu().numpy()
+            lval = lconv * world / tl
+            line["learned_fp32"] = {
+                "path": "learned proposal seeding + one partition per integral, FP32 / "
+                        "float-float integrand, FP64 sums",
+                "value": lval, "unit": UNIT, "ms_per_step": 1e3 * tl / args.steps,
+                "speedup_vs_plain_fp64": lval / line["plain_fp64"]["value"],
+                "train_seconds": lt, "rate": lrate,
+                "loss_first_epoch": lhist[0], "loss_last_epoch": lhist[-1],
+                "accuracy_vs_fp64_gpu": accuracy(lv, ls, v64, s64, w.batches[0].rel_tol,
+                                                 w.batches[0].abs_tol,
+                                                 "FP64 GPU path, every integral", ident_all,
+                                                 w.lattice)}
+            del louts
+            cl.close()
+            torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, (idx, vo, so) = cpu_baseline(w, args.cpu_sample)
         line["cpu_baseline"] = cb

@@ -275,6 +275,9 @@ int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npair
  *             (rate log10 4)) more levels, b = log10(rel_tol / 256), k in
  *             [-2, 3]; cells predicted below b are merged back to level 3 or 2
  *             where all their siblings agree).
+ * With options.group_mode, a (kind, q) group is seeded from the cell-wise
+ * largest value over its pairs' maps (every cell as deep as its most
+ * demanding pair asks).
  * Everything else as paid_integrate_multi. */
 int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb,
                                 const float* proposal, double rate, void* workspace,

@@ -67,7 +67,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t batches, totals, ls, trig, meta, born, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
         thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
-        err0, err1, nse0, nse1, evl, vval0, vval1, verr0, verr1, vsrc, end;
+        err0, err1, nse0, nse1, evl, vval0, vval1, verr0, verr1, vsrc, gmap, end;
 };
 
 // Byte offsets of every workspace array for n integrals and capacity cap.
@@ -111,6 +111,7 @@ Layout layout(int64_t n, int64_t cap, bool group)
         L.verr0 = take(4 * kGroupPairs * cap);
         L.verr1 = take(4 * kGroupPairs * cap);
         L.vsrc = take(4 * cap);
+        L.gmap = take(4 * 256 * n);
     }
     L.end = o;
     return L;
@@ -157,6 +158,7 @@ Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb, bool
         w.verr[0] = reinterpret_cast<float*>(base + L.verr0);
         w.verr[1] = reinterpret_cast<float*>(base + L.verr1);
         w.vsrc = reinterpret_cast<uint32_t*>(base + L.vsrc);
+        w.gmap = reinterpret_cast<float*>(base + L.gmap);
         w.vstride = kGroupPairs;
     }
     w.nff = nff;
@@ -368,6 +370,7 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
         d.abs_tol = b.abs_tol;
         d.max_regions = b.max_regions;
         d.first = n;   // units: integrals, or (group mode) q points
+        d.ifirst = n_int;
         d.q = b.q;
         d.lm = b.lm;
         d.values = b.values;
@@ -672,14 +675,17 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     DeviceGuard guard(ctx->device);
     Work w{};
     int64_t n = 0, cap = 0;
-    if (o.group_mode) return fail(ctx, PAID_ERR_ARG, "seeded starts take group_mode = 0");
-    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 16, s, w, n, cap, false);
+    const bool group = o.group_mode != 0;
+    int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 16, s, w, n, cap, group);
     if (rc != PAID_OK || n == 0) return rc;
     cudaError_t e;
+    // group mode seeds each group from the cell-wise maximum of its pairs' maps
+    const float* seed_map = group && proposal ? w.gmap : proposal;
     // the slot scan reads its slot count from the loop state
     if ((e = launch_setup(w, -1, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess ||
         (e = launch_state_init(w, n, 0, 0, n, -1, o.max_rounds, s)) != cudaSuccess ||
-        (e = launch_seed(w, proposal, rate, 0, s)) != cudaSuccess ||
+        (group && (e = launch_group_map(w, proposal, s)) != cudaSuccess) ||
+        (e = launch_seed(w, seed_map, rate, 0, s)) != cudaSuccess ||
         (e = launch_scan(w, n, 0, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "seed");
     if ((e = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals), cudaMemcpyDeviceToHost,
@@ -689,7 +695,7 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     const RoundTotals t = *ctx->h_totals;
     if (int64_t(t.pool) > cap)
         return fail(ctx, PAID_ERR_OOM, "workspace too small for the seeded partition");
-    if ((e = launch_seed(w, proposal, rate, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
+    if ((e = launch_seed(w, seed_map, rate, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
     ctx->stats.launches = 6;
     return run_loop(ctx, w, n, int64_t(t.eval), int64_t(t.pool), -1, s);
 }

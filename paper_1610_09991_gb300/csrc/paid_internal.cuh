@@ -83,6 +83,7 @@ struct DevBatch {
     int64_t max_regions;
     int64_t first;             // global index of the batch's first unit (integral, or
                                // in group mode its first (kind, q) group)
+    int64_t ifirst;            // global index of the batch's first integral
     const double* q;
     const int32_t* lm;
     double* values;
@@ -173,6 +174,7 @@ struct Work {
     double* vval[2];
     float* verr[2];
     uint32_t* vsrc;            // per next-pool slot: the region it copies (~0u: a new child)
+    float* gmap;               // per group: the seed map (256 cells), see launch_group_map
     int vstride;
     int nff;
 };
@@ -215,6 +217,9 @@ cudaError_t launch_setup_wave(const Work& w, int64_t hint_wave, int nff, int fp6
 // pass 0: region counts into cnt_new / cnt_eval (slot = integral); pass 1 (after
 // launch_scan): keys, eval list, segments.  proposal null = uniform level 4.
 cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s);
+// group mode: each group's seed map = the cell-wise largest predicted error
+// over its pairs' maps (proposal [n_integrals][256], global integral order)
+cudaError_t launch_group_map(const Work& w, const float* proposal, cudaStream_t s);
 cudaError_t launch_features(int kind, int nq, const double* q, int npairs, const int32_t* lm,
                             double T, double mu, double tp, void* x, cudaStream_t s);
 cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s);

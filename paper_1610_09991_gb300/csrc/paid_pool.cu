@@ -416,6 +416,29 @@ __global__ void __launch_bounds__(256) k_seed(Work w, const float* proposal, flo
     }
 }
 
+// Group mode: the seed map of group g is the cell-wise maximum of its pairs'
+// predicted relative log errors, so every cell is seeded as deep as its most
+// demanding pair asks.
+__global__ void k_group_map(Work w, const float* proposal)
+{
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= w.n * 256) return;
+    const int64_t g = t >> 8;
+    const int c = int(t & 255);
+    const DevBatch& B = w.batches[meta_batch(w.meta[g])];
+    const int64_t row0 = B.ifirst + (g - B.first) * B.npairs;
+    float m = -INFINITY;
+    for (int p = 0; p < B.npairs; ++p) m = fmaxf(m, proposal[(row0 + p) * 256 + c]);
+    w.gmap[t] = m;
+}
+
+cudaError_t launch_group_map(const Work& w, const float* proposal, cudaStream_t s)
+{
+    if (w.n <= 0 || !proposal) return cudaSuccess;
+    k_group_map<<<int((w.n * 256 + 255) / 256), 256, 0, s>>>(w, proposal);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s)
 {
     if (w.n <= 0) return cudaSuccess;

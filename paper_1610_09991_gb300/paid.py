@@ -165,6 +165,13 @@ class Context:
         if getattr(self, "_h", None):
             self._lib.paid_destroy(self._h)
             self._h = None
+        self._ws = None
+
+    def release_workspace(self):
+        """Drop the cached workspace (results already returned stay valid) and
+        hand the memory back to the device for other allocations."""
+        self._ws = None
+        _torch().cuda.empty_cache()
 
     def __del__(self):
         try:

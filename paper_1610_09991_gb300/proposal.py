@@ -80,14 +80,17 @@ def train_default(device=0, n_draws=24, nq=8, epochs=30, seed=0, log=None):
     return prop, hist, time.perf_counter() - t0
 
 
-def calibrate_default(prop, device=0, n_draws=24, nq=4, t_range=(0.02, 0.3), eval_fp32=1):
+def calibrate_default(prop, device=0, n_draws=24, nq=4, t_range=(0.02, 0.3), eval_fp32=1,
+                      group_mode=0):
     """Seeding rate calibrated on the training draws whose T lies in t_range
-    (smaller q grid); returns (rate, {rate: summed region evaluations})."""
+    (smaller q grid) for the given evaluation mode; returns
+    (rate, {rate: summed region evaluations})."""
     tot = {}
     for tp, mu, T in W.parameter_draws(n_draws, 0):
         if not (t_range[0] <= T <= t_range[1]):
             continue
-        ctx = P.Context(1.0, tp, mu, ffset=9, device=device, eval_fp32=eval_fp32)
+        ctx = P.Context(1.0, tp, mu, ffset=9, device=device, eval_fp32=eval_fp32,
+                        group_mode=group_mode)
         _, ev = calibrate_rate(prop, ctx, draw_batches(T, nq, device=device))
         for r, e in ev.items():
             tot[r] = tot.get(r, 0) + e

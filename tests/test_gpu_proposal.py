@@ -156,3 +156,59 @@ def test_trained_proposal_gains_over_unseeded_start(paid, torch):
     # calibration keeps the seed shallow)
     assert st_seed["rounds"] < st_plain["rounds"]
     assert st_seed["region_evals"] <= 1.10 * st_plain["region_evals"]
+
+
+@pytest.mark.parametrize("mode", ["uniform4", "exact", "random"])
+def test_group_seeded_start_keeps_parity(paid, torch, mode):
+    # shared-partition mode: a group is seeded from the cell-wise largest value
+    # of its pairs' maps; the result must not depend on the map's quality
+    b = W.Batch(W.PP, 0.05, W.q_grid_bz(2), W.all_pairs(9), 1e-6, 1e-10, 100000)
+    ctx = paid.Context(*LAT, ffset=9, group_mode=1)
+    q = torch.as_tensor(b.q, device="cuda")
+    lm = torch.as_tensor(b.lm, dtype=torch.int32, device="cuda")
+    if mode == "uniform4":
+        prop = None
+    elif mode == "exact":
+        prop = ctx.cell_errors(b.kind, q, lm, b.T)
+    else:
+        g = torch.Generator(device="cpu").manual_seed(5)
+        prop = (torch.rand((b.n, 256), generator=g) * -16.0).to("cuda")
+    (r,) = ctx.integrate_multi_seeded([dict(kind=b.kind, T=b.T, q=q, lm=lm, rel_tol=b.rel_tol,
+                                            abs_tol=b.abs_tol, max_regions=b.max_regions)],
+                                      prop, 2.0)
+    torch.cuda.synchronize()
+    g = tuple(x.cpu().numpy() for x in (r.values, r.errors, r.regions, r.status))
+    o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol, b.max_regions)
+    n = assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b))
+    if mode != "random":
+        assert n >= 0.9 * b.n
+
+
+def test_trained_proposal_in_group_mode(paid, torch):
+    from paper_1610_09991_gb300 import proposal as PR
+    prop, hist, secs = PR.train_default(n_draws=8, nq=6, epochs=20)
+    tp, mu, T = W.parameter_draws(1, 10000)[0]
+    ctx = paid.Context(1.0, tp, mu, ffset=9, group_mode=1)
+    bs = PR.draw_batches(T, 8)
+    rate, evals = PR.calibrate_rate(prop, ctx, bs)
+    plain = ctx.integrate_multi(bs)
+    st_plain = ctx.last_stats()
+    maps = PR.predict(prop, ctx, bs)
+    seeded = ctx.integrate_multi_seeded(bs, maps, rate)
+    st_seed = ctx.last_stats()
+    torch.cuda.synchronize()
+    for a, c in zip(seeded, plain):
+        va, sa = a.values.cpu().numpy(), a.status.cpu().numpy()
+        vc, sc = c.values.cpu().numpy(), c.status.cpu().numpy()
+        both = (sa == 0) & (sc == 0)
+        tol = np.maximum(1e-6 * np.abs(vc), 1e-10)
+        assert np.mean(np.abs(va - vc)[both] <= 2 * tol[both] + 1e-12) > 0.999
+    print("group rate", rate, evals, "rounds plain/seeded", st_plain["rounds"], st_seed["rounds"],
+          "region evals", st_plain["region_evals"], st_seed["region_evals"])
+    # in group mode the seed skips early rounds but costs regions: a group is
+    # seeded as deep as its most demanding pair asks, cell by cell, while the
+    # unseeded group refines from the 16-region start only where the shared
+    # selection needs it (measured: 8 -> 6 rounds for ~19 % more region
+    # evaluations at the calibrated rate); the bound guards that trade
+    assert st_seed["rounds"] < st_plain["rounds"]
+    assert st_seed["region_evals"] <= 1.30 * st_plain["region_evals"]
