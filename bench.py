@@ -67,6 +67,8 @@ def parse_args():
                          "start; plain: one partition per integral, FP64, uniform start; "
                          "fp32: per integral, FP32 / float-float evaluation; learned_fp32: "
                          "fp32 with the seeded start")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="group paths: keep the default cover and evaluation grid")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the extra timed steps of the learned_fp32 path")
     ap.add_argument("--no-compare", action="store_true",
@@ -311,6 +313,18 @@ def run_paid(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peaks = fp64_peak(local)
     prop_info, prop, rate = None, None, None
+    tune = None
+    if group and not args.no_autotune:
+        # autotuner (outside the timed region): cover and the evaluation grid,
+        # timed on every 6th q point of each batch
+        t0 = time.perf_counter()
+        sample = [dict(d, q=d["q"][::6].contiguous()) for d in dbs]
+        o = ctx.autotune(sample)
+        tune = {"cover": o.cover, "eval_blocks": o.eval_blocks,
+                "seconds": time.perf_counter() - t0,
+                "sample": "every 6th q point of each batch (%d integrals)"
+                          % sum(int(d["q"].shape[0]) * int(d["lm"].shape[0]) for d in sample)}
+        ctx.release_workspace()
     if learned:
         from paper_1610_09991_gb300 import proposal as PR
         prop, hist, t_train = PR.train_default(device=local, n_draws=24, nq=8, epochs=20)
@@ -452,6 +466,7 @@ def run_paid(args):
                  "learned_fp32": "learned proposal seeding + batched GPU cubature, FP32 / "
                                  "float-float integrand, FP64 sums"}[args.path],
         "proposal": prop_info,
+        "autotune": tune,
         "budget_integrals_per_step": agg["budget"] / args.steps,
         "region_evals_per_s": agg["region_evals"] * world / elapsed,
         "node_evals_per_s": agg["node_evals"] * world / elapsed,
@@ -474,7 +489,8 @@ def run_paid(args):
         # launch per call (conditional WHILE node), no per-round host sync and
         # no per-kernel events
         cg = P.Context(*w.lattice, ffset=ff, device=local, device_loop=1,
-                       eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group)
+                       eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group,
+                       cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks)
 
         def gstep():
             flush.fill_(1)

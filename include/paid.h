@@ -108,6 +108,8 @@ typedef struct {
                                region count reported is the group's.  max_regions bounds the
                                group's regions and pool_capacity counts them (about 2 KB each).
                                Default 0 (one partition per integral) */
+    int eval_blocks;        /* group_mode: grid of the region-evaluation kernel (it strides over
+                               the eval list); 0 = 152 x 32 blocks.  Default 0 */
 } paid_options;
 
 /* Statistics of the last integrate call on a context. */
@@ -211,6 +213,37 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb,
 int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int npairs,
                       const int32_t* lm, int nreg, const int32_t* regions, double* q2N,
                       double* dq, void* workspace, size_t ws_bytes, void* stream);
+
+/* Diagnostics: the FP64 exp and division the shared-partition kernel uses
+ * (its own exp after Tang's table-driven method, its own division from the
+ * approximate reciprocal and Newton-Raphson steps), applied element-wise on
+ * device arrays so that tests can hold them to their error bounds.
+ *   which = 0: out[i] = exp(-x[i]), x[i] >= 0 (y unused, may be NULL);
+ *   which = 1: out[i] = x[i] / y[i], y[i] normal and non-zero.
+ * Returns PAID_OK (stream synchronised), PAID_ERR_ARG or PAID_ERR_CUDA. */
+int paid_check_math(paid_ctx* ctx, int which, int64_t n, const double* x, const double* y,
+                    double* out, void* stream);
+
+/* The context's current options (after paid_autotune, say). */
+int paid_get_options(paid_ctx* ctx, paid_options* out);
+
+/* Autotuner: picks options.cover (how many regions a round splits) and, in
+ * group_mode, options.eval_blocks (the evaluation grid) for this GPU by
+ * timing paid_integrate_multi on `sample` (a few batches the caller chose as
+ * representative; their outputs are overwritten) for every candidate:
+ * cover in {0.5, 0.75, 0.9, 1.0} x eval_blocks in {608, 1216, 4864} (group
+ * mode) or {default}.  The fastest candidate that completes becomes the
+ * context's setting.
+ *   cache_path  NULL, or a JSON Lines file: when it holds an entry for this
+ *               device name, rule_n, eval_fp32 and group_mode the entry is
+ *               applied without timing (sample may then be NULL); otherwise
+ *               the tuned choice is written there, replacing any older entry
+ *               with the same key.
+ *   workspace, ws_bytes, stream as for paid_integrate_multi.
+ * Returns PAID_OK, PAID_ERR_ARG or PAID_ERR_CUDA (no candidate completed; the
+ * options are left unchanged). */
+int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* cache_path,
+                  void* workspace, size_t ws_bytes, void* stream);
 
 /* paid_integrate_batch without a workspace argument, for callers that cannot
  * allocate device memory when they need the integrals: code that runs while

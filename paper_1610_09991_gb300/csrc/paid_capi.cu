@@ -38,7 +38,7 @@ struct LoopGraph {
     const void* base = nullptr;        // workspace layout it was captured for
     int64_t n = 0, cap = 0;
     int nb = 0, vstride = 0;
-    int rule_n = 0, eval_fp32 = 0, max_rounds = 0;
+    int rule_n = 0, eval_fp32 = 0, max_rounds = 0, eval_blocks = 0;
     double cover = 0.0;
 };
 
@@ -67,7 +67,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t batches, totals, ls, trig, meta, born, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
         thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
-        err0, err1, nse0, nse1, evl, vval0, vval1, verr0, verr1, vsrc, gmap, end;
+        err0, err1, nse0, nse1, evl, vval0, vval1, verr0, verr1, vsrc, gmap, gpart, gsum, gtol,
+        gsc, gstate, end;
 };
 
 // Byte offsets of every workspace array for n integrals and capacity cap.
@@ -112,6 +113,11 @@ Layout layout(int64_t n, int64_t cap, bool group)
         L.verr1 = take(4 * kGroupPairs * cap);
         L.vsrc = take(4 * cap);
         L.gmap = take(4 * 256 * n);
+        L.gpart = take(8 * size_t(kGroupSplit) * 2 * kGroupPairs * n);
+        L.gsum = take(8 * 2 * kGroupPairs * n);
+        L.gtol = take(8 * kGroupPairs * n);
+        L.gsc = take(8 * size_t(kGroupSplit) * 2 * n);
+        L.gstate = take(4 * n);
     }
     L.end = o;
     return L;
@@ -159,6 +165,11 @@ Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb, bool
         w.verr[1] = reinterpret_cast<float*>(base + L.verr1);
         w.vsrc = reinterpret_cast<uint32_t*>(base + L.vsrc);
         w.gmap = reinterpret_cast<float*>(base + L.gmap);
+        w.gpart = reinterpret_cast<double*>(base + L.gpart);
+        w.gsum = reinterpret_cast<double*>(base + L.gsum);
+        w.gtol = reinterpret_cast<double*>(base + L.gtol);
+        w.gsc = reinterpret_cast<double*>(base + L.gsc);
+        w.gstate = reinterpret_cast<int*>(base + L.gstate);
         w.vstride = kGroupPairs;
     }
     w.nff = nff;
@@ -212,6 +223,7 @@ int check_options(const paid_options& o, std::string& why)
     if (o.device_loop != 0 && o.device_loop != 1) { why = "device_loop must be 0 or 1"; return PAID_ERR_ARG; }
     if (o.group_mode != 0 && o.group_mode != 1) { why = "group_mode must be 0 or 1"; return PAID_ERR_ARG; }
     if (o.group_mode && o.eval_fp32) { why = "group_mode evaluates in FP64 (eval_fp32 = 0)"; return PAID_ERR_ARG; }
+    if (o.eval_blocks < 0) { why = "eval_blocks must be >= 0"; return PAID_ERR_ARG; }
     return PAID_OK;
 }
 
@@ -231,6 +243,7 @@ int paid_options_default(paid_options* opt)
     opt->timing = 0;
     opt->device_loop = 1;
     opt->group_mode = 0;
+    opt->eval_blocks = 0;
     return PAID_OK;
 }
 
@@ -412,7 +425,8 @@ cudaError_t launch_round(paid_ctx* ctx, const Work& w, int64_t hint_eval, int64_
     cudaError_t e;
     const bool group = w.vstride > 0;
     if ((e = mark(0)) != cudaSuccess ||
-        (e = group ? launch_eval_group(w, hint_eval, o.rule_n, ctx->lat, s)
+        (e = group ? launch_eval_group(w, hint_eval, o.rule_n, ctx->lat, s, nullptr, nullptr,
+                                       o.eval_blocks)
                    : launch_eval(w, hint_eval, o.rule_n, o.eval_fp32, ctx->lat, s,
                                  ev && o.eval_fp32 ? ev[6] : nullptr)) != cudaSuccess ||
         (e = mark(1)) != cudaSuccess ||
@@ -437,9 +451,10 @@ int64_t round_kernels(const paid_options& o, int64_t n_eval, int64_t n_active, b
 {
     const int64_t ev = n_eval > 0 ? (o.eval_fp32 ? 2 : 1) : 0;
     const int64_t slots = n_active > 0 ? 1 : 0;
-    // eval, reduce, scan (2), throttle, rescan (2), split, [vector copy], control, [wave]
-    return ev + slots + (slots + 1) + slots + (slots + 1) + slots + (o.group_mode ? slots : 0) + 1 +
-           (in_graph ? 1 : 0);
+    // eval, reduce (group: 4), scan (2), throttle, rescan (2), split, [vector copy], control,
+    // [wave]
+    return ev + (o.group_mode ? 4 : 1) * slots + (slots + 1) + slots + (slots + 1) + slots +
+           (o.group_mode ? slots : 0) + 1 + (in_graph ? 1 : 0);
 }
 
 // The device-loop graph for this workspace layout and these options:
@@ -451,6 +466,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     if (G.exec && G.base == w.batches && G.n == w.n && G.cap == w.cap && G.nb == w.nb &&
         G.vstride == w.vstride &&
         G.rule_n == o.rule_n && G.eval_fp32 == o.eval_fp32 && G.max_rounds == o.max_rounds &&
+        G.eval_blocks == o.eval_blocks &&
         G.cover == o.cover) {
         *out = G.exec;
         return PAID_OK;
@@ -507,6 +523,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     G.rule_n = o.rule_n;
     G.eval_fp32 = o.eval_fp32;
     G.max_rounds = o.max_rounds;
+    G.eval_blocks = o.eval_blocks;
     G.cover = o.cover;
     *out = exec;
     return PAID_OK;
@@ -781,6 +798,155 @@ int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int np
         return cuda_fail(ctx, e, "rule regions");
     // like the integrate calls, return with the outputs complete
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "rule regions");
+    return PAID_OK;
+}
+
+int paid_check_math(paid_ctx* ctx, int which, int64_t n, const double* x, const double* y,
+                    double* out, void* stream)
+{
+    if (!ctx || (which != 0 && which != 1) || n < 0) return PAID_ERR_ARG;
+    if (n > 0 && (!x || !out || (which == 1 && !y))) return PAID_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_check_math(which, n, x, y, out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PAID_OK : cuda_fail(ctx, e, "check math");
+}
+
+int paid_get_options(paid_ctx* ctx, paid_options* out)
+{
+    if (!ctx || !out) return PAID_ERR_ARG;
+    *out = ctx->opt;
+    return PAID_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Autotuner cache: JSON Lines, one object per tuned configuration,
+//   {"key": "<device>|rule_n=4|eval_fp32=0|group_mode=1", "cover": 1, "eval_blocks": 608, "ms": 9.1}
+std::string tune_key(const paid_ctx* ctx)
+{
+    cudaDeviceProp prop{};
+    std::string dev = cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess ? prop.name : "?";
+    for (char& c : dev)
+        if (c == '"' || c == '\\') c = '_';
+    const paid_options& o = ctx->opt;
+    return dev + "|rule_n=" + std::to_string(o.rule_n) + "|eval_fp32=" + std::to_string(o.eval_fp32) +
+           "|group_mode=" + std::to_string(o.group_mode);
+}
+
+std::vector<std::string> read_lines(const char* path)
+{
+    std::vector<std::string> lines;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return lines;
+    char buf[1024];
+    while (std::fgets(buf, sizeof(buf), f)) {
+        std::string l(buf);
+        while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+        if (!l.empty()) lines.push_back(l);
+    }
+    std::fclose(f);
+    return lines;
+}
+
+bool cached_choice(const char* path, const std::string& key, double& cover, int& blocks)
+{
+    const std::string tag = "\"key\": \"" + key + "\"";
+    for (const std::string& l : read_lines(path)) {
+        if (l.find(tag) == std::string::npos) continue;
+        const size_t pc = l.find("\"cover\": "), pb = l.find("\"eval_blocks\": ");
+        if (pc == std::string::npos || pb == std::string::npos) continue;
+        double c = 0.0;
+        int b = 0;
+        if (std::sscanf(l.c_str() + pc + 9, "%lf", &c) != 1 ||
+            std::sscanf(l.c_str() + pb + 15, "%d", &b) != 1)
+            continue;
+        if (!(c >= 0.0 && c <= 1.0) || b < 0) continue;
+        cover = c;
+        blocks = b;
+        return true;
+    }
+    return false;
+}
+
+void store_choice(const char* path, const std::string& key, double cover, int blocks, double ms)
+{
+    const std::string tag = "\"key\": \"" + key + "\"";
+    std::vector<std::string> keep;
+    for (const std::string& l : read_lines(path))
+        if (l.find(tag) == std::string::npos) keep.push_back(l);
+    char line[512];
+    std::snprintf(line, sizeof(line), "{%s, \"cover\": %.17g, \"eval_blocks\": %d, \"ms\": %.6g}",
+                  tag.c_str(), cover, blocks, ms);
+    keep.push_back(line);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const std::string& l : keep) std::fprintf(f, "%s\n", l.c_str());
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+extern "C" {
+
+int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* cache_path,
+                  void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    const std::string key = tune_key(ctx);
+    double cover = ctx->opt.cover;
+    int blocks = ctx->opt.eval_blocks;
+    if (cache_path && cached_choice(cache_path, key, cover, blocks)) {
+        ctx->opt.cover = cover;
+        ctx->opt.eval_blocks = blocks;
+        return PAID_OK;
+    }
+    if (nb <= 0 || !sample) return fail(ctx, PAID_ERR_ARG, "autotune needs a sample batch");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const paid_options saved = ctx->opt;
+    ctx->opt.timing = 0;
+    const double covers[] = {0.5, 0.75, 0.9, 1.0};
+    std::vector<int> grids = {0};
+    if (saved.group_mode) grids = {152 * 4, 152 * 8, 152 * 32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        ctx->opt = saved;
+        return fail(ctx, PAID_ERR_CUDA, "autotune events");
+    }
+    double best_ms = 1e300, best_cover = saved.cover;
+    int best_blocks = saved.eval_blocks;
+    bool warm = false;
+    for (int g : grids)
+        for (double c : covers) {
+            ctx->opt.cover = c;
+            ctx->opt.eval_blocks = g;
+            if (!warm) {   // first call: graph capture, tables, caches
+                paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+                warm = true;
+            }
+            cudaEventRecord(e0, s);
+            const int rc = paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (rc != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                continue;
+            if (ms < best_ms) { best_ms = ms; best_cover = c; best_blocks = g; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->opt = saved;
+    if (best_ms >= 1e300) return fail(ctx, PAID_ERR_CUDA, "autotune: no candidate completed");
+    ctx->opt.cover = best_cover;
+    ctx->opt.eval_blocks = best_blocks;
+    if (cache_path) store_choice(cache_path, key, best_cover, best_blocks, best_ms);
     return PAID_OK;
 }
 

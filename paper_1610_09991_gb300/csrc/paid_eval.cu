@@ -51,6 +51,7 @@ __constant__ int c_ffn[9];
 __constant__ int c_ffa[9][2];
 __constant__ int c_ffb[9][2];
 __constant__ double c_ffc[9][2];
+__constant__ double c_exp2d[64];                  // 2^(j/64), j = 0..63 (FP64 exp of the group path)
 
 // Clenshaw-Curtis weights for n intervals (n even), from the cosine-series
 // form of the rule: w_j = (c_j / n) (1 - sum_{k=1}^{n/2} b_k cos(2 k j pi/n)/(4k^2 - 1)).
@@ -157,6 +158,9 @@ cudaError_t init_rule_tables(int device)
     if ((e = cudaMemcpyToSymbol(c_ffa, ffa, sizeof(ffa))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_ffb, ffb, sizeof(ffb))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_ffc, ffc, sizeof(ffc))) != cudaSuccess) return e;
+    double e2d[64];
+    for (int j = 0; j < 64; ++j) e2d[j] = std::exp2(j / 64.0);
+    if ((e = cudaMemcpyToSymbol(c_exp2d, e2d, sizeof(e2d))) != cudaSuccess) return e;
     if ((e = group_kernel_attributes()) != cudaSuccess) return e;
     done[device] = true;
     return cudaSuccess;
@@ -842,6 +846,93 @@ __global__ void __launch_bounds__(128) k_eval_fp64(Work w, Lattice lat)
 }
 
 // ---------------------------------------------------------------------------
+// FP64 exp and division of the shared-partition kernel.
+//
+// exp(-a), a >= 0: P. T. P. Tang's table-driven method (ACM TOMS 15, 1989):
+// -a = n ln2/64 + r with n = round(-a 64/ln2) = 64 m + j, 0 <= j < 64, so
+// exp(-a) = 2^m 2^(j/64) exp(r), |r| <= ln2/128.  r comes from a two-constant
+// Cody-Waite reduction (L1 = ln2/64 to 32 significant bits, so n L1 is exact
+// for |n| < 2^21; L2 = ln2/64 - L1), exp(r) from its degree-5 Taylor
+// polynomial (truncation r^6/720 < 2^-54 on that interval) and 2^(j/64) from a
+// 64-entry table.  Results below 2^-1022 flush to zero; NaN propagates.
+__device__ __forceinline__ double exp_neg(double a, const double* tab)
+{
+    a = a > 800.0 ? 800.0 : a;
+    const double n = rint(a * -92.33248261689366);
+    double r = fma(n, -0x1.62e42ffp-7, -a);
+    r = fma(n, 0x1.718432a1b0e26p-41, r);
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(r, p, 1.0 / 6.0);
+    p = fma(r, p, 0.5);
+    p = fma(r, p, 1.0);
+    p = fma(r, p, 1.0);
+    const int ni = int(n);
+    const int m = ni >> 6;          // floor(n / 64)
+    const int j = ni & 63;
+    const double scale = m >= -1022 ? __longlong_as_double((long long)(m + 1023) << 52) : 0.0;
+    return tab[j] * p * scale;
+}
+
+// num / den for a normal, non-zero den: the approximate FP64 reciprocal of
+// the PTX ISA (rcp.approx.ftz.f64) refined by two Newton-Raphson steps
+// y <- y + y (1 - den y), then one residual correction of the quotient
+// q <- q + (num - den q) y.
+__device__ __forceinline__ double div_nr(double num, double den)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(den));
+    double e = fma(-den, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-den, y, 1.0);
+    y = fma(y, e, y);
+    const double q = num * y;
+    return fma(fma(-den, q, num), y, q);
+}
+
+// bubble_F with exp_neg and div_nr (same branches and formulas)
+__device__ __forceinline__ double bubble_F_tab(double e1, double e2, double inv2T, double inv4T,
+                                               const double* tab)
+{
+    const double diff = e1 - e2;
+    const double d = diff * inv2T;
+    const double x1 = e1 * inv2T, x2 = e2 * inv2T;
+    const double v1 = exp_neg(fabs(x1), tab), v2 = exp_neg(fabs(x2), tab);
+    const double u1 = v1 * v1, u2 = v2 * v2;
+    const double p = (1.0 + u1) * (1.0 + u2);
+    const bool near = fabs(d) <= 0.0625;
+    const bool neg1 = x1 < 0.0;
+    const bool same = neg1 == (x2 < 0.0);
+    double far = same ? (u2 - u1) : fma(-u1, u2, 1.0);
+    far = neg1 ? -far : far;
+    const double d2 = d * d;
+    const double sinhc = fma(d2, fma(d2, fma(d2, fma(d2, 1.0 / 362880.0, 1.0 / 5040.0),
+                                              1.0 / 120.0), 1.0 / 6.0), 1.0);
+    const double nearv = (4.0 * inv4T) * (v1 * v2) * sinhc;
+    const double num = near ? nearv : far;
+    const double den = near ? p : p * diff;
+    return div_nr(num, den);
+}
+
+// Diagnostics for paid_check_math: which = 0: exp_neg(x), 1: div_nr(x, y).
+__global__ void k_check_math(int which, int64_t n, const double* x, const double* y, double* out)
+{
+    __shared__ double tab[64];
+    if (threadIdx.x < 64) tab[threadIdx.x] = c_exp2d[threadIdx.x];
+    __syncthreads();
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = which == 0 ? exp_neg(x[i], tab) : div_nr(x[i], y[i]);
+}
+
+cudaError_t launch_check_math(int which, int64_t n, const double* x, const double* y, double* out,
+                              cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_check_math<<<int((n + 255) / 256), 256, 0, s>>>(which, n, x, y, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Shared-partition (group) evaluation: one region of a (kind, q) group gives
 // Q_N and Q_2N of every (l, m) pair of the group's batch at once.  With
 // g = (1, cos, sin) every form factor is f_n(k) = sum C_n[a][b] g_a(kx) g_b(ky),
@@ -868,6 +959,8 @@ struct GroupSmem {
     double Rc[R][N + 1][9];  // coarse row sums (even rows)
     double Mf[R][9][9];      // fine moments
     double Mc[R][9][9];      // coarse moments
+    double C[R][4];          // sin, cos of the region centre (x, y) times pi
+    double tab[64];          // 2^(j/64)
 };
 
 template <int N>
@@ -882,6 +975,7 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
     const int64_t n_eval = w.ls->n_eval;
     const int rho = threadIdx.x / NF, i = threadIdx.x % NF;
     const double tA = -2.0 * lat.t, tB = -4.0 * lat.tp;
+    if (threadIdx.x < 64) S.tab[threadIdx.x] = c_exp2d[threadIdx.x];
     for (int64_t chunk = blockIdx.x; chunk * R < n_eval; chunk += gridDim.x) {
         const int64_t t = chunk * R + rho;
         const bool live = t < n_eval;
@@ -889,23 +983,29 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
         int kind = PH, P = 0;
         const DevBatch* B = nullptr;
         double A1 = 0.0, B1 = 0.0, A2 = 0.0, B2 = 0.0;
+        uint64_t key = 0;
         if (live) {
             const uint2 e = w.evl[t];
             pos = e.x;
             g = e.y;
-            const uint64_t key = w.key[cur][pos];
+            key = w.key[cur][pos];
             L = key_level(key);
-            const uint32_t ix = key_ix(key), iy = key_iy(key);
+            if (i < 2) {   // the exact dyadic centre / pi: -1 + (2 ix + 1) 2^-L, x then y
+                const uint32_t ic = i == 0 ? key_ix(key) : key_iy(key);
+                sincospi(fma(double(2 * ic + 1), ldexp(1.0, -int(L)), -1.0), &S.C[rho][2 * i],
+                         &S.C[rho][2 * i + 1]);
+            }
+        }
+        __syncthreads();
+        if (live) {
             const uint32_t mt = w.meta[g];
             B = &w.batches[meta_batch(mt)];
             kind = meta_kind(mt);
             P = B->npairs;
             const QTrig tq = w.trig[g];
             const bool pp = kind == PP;
-            const double h = ldexp(1.0, -int(L));
-            double sxc, cxc, syc, cyc;
-            sincospi(fma(double(2 * ix + 1), h, -1.0), &sxc, &cxc);
-            sincospi(fma(double(2 * iy + 1), h, -1.0), &syc, &cyc);
+            const double sxc = S.C[rho][0], cxc = S.C[rho][1];
+            const double syc = S.C[rho][2], cyc = S.C[rho][3];
             const int ii = i <= N ? i : 2 * N - i;
             const double co = c_co[v][L][ii];
             const double so = i <= N ? c_so[v][L][ii] : -c_so[v][L][ii];
@@ -945,7 +1045,7 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 if (kind != OVERLAP) {
                     const double e1 = fma(B1, S.CY[rho][j][0], A1);
                     const double e2 = fma(B2, S.CY[rho][j][1], A2);
-                    F = bubble_F(e1, kind == PP ? -e2 : e2, inv2T, inv4T);
+                    F = bubble_F_tab(e1, kind == PP ? -e2 : e2, inv2T, inv4T, S.tab);
                 }
                 const double wf = c_wf[v][j] * F;
 #pragma unroll
@@ -1024,16 +1124,17 @@ static cudaError_t group_kernel_attributes()
 }
 
 cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Lattice lat,
-                              cudaStream_t s, double* rule_q2, double* rule_d)
+                              cudaStream_t s, double* rule_q2, double* rule_d, int max_blocks)
 {
     if (hint_eval <= 0) return cudaSuccess;
+    const int64_t cap = max_blocks > 0 ? max_blocks : 152 * 32;
     if (rule_n == 4) {
         constexpr int R = GroupShape<4>::R;
-        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, 152 * 32);
+        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, cap);
         k_eval_group<4><<<int(blocks), R * 9, sizeof(GroupSmem<4>), s>>>(w, lat, rule_q2, rule_d);
     } else {
         constexpr int R = GroupShape<6>::R;
-        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, 152 * 32);
+        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, cap);
         k_eval_group<6><<<int(blocks), R * 13, sizeof(GroupSmem<6>), s>>>(w, lat, rule_q2, rule_d);
     }
     return cudaGetLastError();

@@ -46,6 +46,8 @@ constexpr uint32_t kEscalate = 0xfeu;
 // Shared-partition (group) mode: most pairs per group, and the pair-vector
 // stride of a region in the pool
 constexpr int kGroupPairs = 81;
+// chunks per group segment in the group reduce (blocks per group)
+constexpr int kGroupSplit = 8;
 
 enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3 };
 enum Status : int { CONVERGED = 0, BUDGET = 1, NONFINITE = 2, ROUNDCAP = 3, POOL = 4, RUNNING = -1 };
@@ -175,6 +177,15 @@ struct Work {
     float* verr[2];
     uint32_t* vsrc;            // per next-pool slot: the region it copies (~0u: a new child)
     float* gmap;               // per group: the seed map (256 cells), see launch_group_map
+    // per active slot, temporaries of the group reduce: chunk sums of V and E
+    // ([slot][chunk][2][81]), V and E ([slot][2][81]), 1/tol of the pairs not
+    // yet converged ([slot][81]), chunk score sum and max ([slot][chunk][2]),
+    // status after the test
+    double* gpart;
+    double* gsum;
+    double* gtol;
+    double* gsc;
+    int* gstate;
     int vstride;
     int nff;
 };
@@ -192,8 +203,13 @@ cudaError_t launch_eval(const Work& w, int64_t hint_eval, int rule_n, int fp32, 
 // group mode: every pair of every region on the eval list (FP64).  With
 // rule_q2 / rule_d non-null, entry t's Q_2N and Q_N - Q_2N (times the region's
 // Jacobian) go to rule_q2 / rule_d[t * npairs + pair] instead of the pool.
+// max_blocks > 0 caps the grid (the kernel is grid-stride), else 152 x 32
 cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Lattice lat,
-                              cudaStream_t s, double* rule_q2 = nullptr, double* rule_d = nullptr);
+                              cudaStream_t s, double* rule_q2 = nullptr, double* rule_d = nullptr,
+                              int max_blocks = 0);
+// which = 0: the group kernel's exp(-x); 1: its division x / y (diagnostics)
+cudaError_t launch_check_math(int which, int64_t n, const double* x, const double* y, double* out,
+                              cudaStream_t s);
 // paid_pool.cu
 // Initial loop state: counts of the first round, buffer 0, round 0.
 cudaError_t launch_state_init(const Work& w, int64_t n_active, int64_t n_eval, int64_t pool,

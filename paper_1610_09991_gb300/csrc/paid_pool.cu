@@ -644,128 +644,222 @@ cudaError_t launch_reduce_test(const Work& w, int64_t hint_active, int max_round
 }
 
 // ---------------------------------------------------------------------------
-// Shared-partition (group) reduce + test + selection, one block per active
-// group (kind, q) of a batch with P pairs.  Per pair c: V_c = sum Q_2N and
-// E_c = sum |Q_N - Q_2N| over the group's regions (each warp sums a fixed
-// residue class of regions, the warps' partial sums are added in warp order:
-// deterministic), tol_c = max(abs_tol, rel_tol |V_c|).  The group is done when
-// every valid pair has E_c <= tol_c.  Otherwise each region's score
+// Shared-partition (group) reduce + test + selection for the active groups
+// (kind, q) of batches with P pairs.  Per pair c: V_c = sum Q_2N and
+// E_c = sum |Q_N - Q_2N| over the group's regions, tol_c = max(abs_tol,
+// rel_tol |V_c|).  The group is done when every valid pair has E_c <= tol_c.
+// Otherwise each region's score
 //   s_r = max over the pairs not yet converged of err_c,r / tol_c
 // goes to err[r], and the per-integral selection runs on the scores with unit
 // tolerance: the largest scores until their sum covers sum_r s_r - cover, so
 // that for every pair the unsplit regions carry at most cover * tol_c of its
 // error.  Finished groups write every pair's value, error, region count and
 // status (CONVERGED for the pairs that meet their tolerance).
+//
+// Four launches, so that a deep group does not keep one block streaming its
+// regions alone: each group's segment is cut into kGroupSplit chunks of
+// consecutive regions, and
+//   k_group_sums    (slot, chunk) blocks: per-pair partial sums of the chunk
+//   k_group_test    slot blocks: the chunk sums in chunk order (deterministic),
+//                   the test, finished groups' outputs, 1/tol_c of the rest
+//   k_group_scores  (slot, chunk) blocks: region scores, the chunk's score sum
+//                   and maximum
+//   k_group_select  slot blocks: the score histogram and the selection
 constexpr int kGroupWarps = 8;
 
-__global__ void __launch_bounds__(kGroupWarps * 32)
-k_reduce_group(Work w, int max_rounds, double cover, int force_status)
+__device__ __forceinline__ void chunk_range(uint32_t cnt, int k, uint32_t& j0, uint32_t& j1)
+{
+    const uint32_t len = (cnt + kGroupSplit - 1) / kGroupSplit;
+    j0 = min(cnt, uint32_t(k) * len);
+    j1 = min(cnt, j0 + len);
+}
+
+__global__ void __launch_bounds__(kGroupWarps * 32) k_group_sums(Work w)
 {
     __shared__ double pv[kGroupWarps][kGroupPairs], pe[kGroupWarps][kGroupPairs];
-    __shared__ double inv_tol[kGroupPairs];
-    __shared__ double ps[kGroupWarps], pm[kGroupWarps];
-    __shared__ unsigned long long hsum[kHistBins];
-    __shared__ uint32_t hcnt[kHistBins];
     const LoopState& Ls = *w.ls;
-    const int cur = Ls.cur, round = Ls.round;
-    const int64_t s = blockIdx.x;
+    const int64_t s = blockIdx.x / kGroupSplit;
+    const int k = int(blockIdx.x % kGroupSplit);
     if (s >= Ls.n_active) return;
+    const int cur = Ls.cur;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint32_t g = w.active[cur][s];
     const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
-    const DevBatch& B = w.batches[meta_batch(w.meta[g])];
-    const int P = B.npairs;
+    const int P = w.batches[meta_batch(w.meta[g])].npairs;
     const size_t S = size_t(w.vstride);
     const double* vval = w.vval[cur];
     const float* verr = w.verr[cur];
-    const uint64_t* key = w.key[cur];
-
-    // pass 1: per-pair sums
-    {
-        double v[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
-        for (uint32_t j = wid; j < cnt; j += kGroupWarps) {
-            const size_t r = size_t(base + j) * S;
+    uint32_t j0, j1;
+    chunk_range(cnt, k, j0, j1);
+    // values in FP64; error sums in FP32 per lane (a lane adds about
+    // cnt / 64 terms of one sign: relative rounding below 1e-5, far inside
+    // what a convergence test or a selection can resolve), then in FP64
+    double v[3] = {0.0, 0.0, 0.0};
+    float e[3] = {0.0f, 0.0f, 0.0f};
+    for (uint32_t j = j0 + wid; j < j1; j += kGroupWarps) {
+        const size_t r = size_t(base + j) * S;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int c = lane + 32 * k;
-                if (c < P) { v[k] += vval[r + c]; e[k] += double(verr[r + c]); }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int c = lane + 32 * k;
-            if (c < P) { pv[wid][c] = v[k]; pe[wid][c] = e[k]; }
+        for (int c3 = 0; c3 < 3; ++c3) {
+            const int c = lane + 32 * c3;
+            if (c < P) { v[c3] += vval[r + c]; e[c3] += verr[r + c]; }
         }
     }
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) {
+        const int c = lane + 32 * c3;
+        if (c < P) { pv[wid][c] = v[c3]; pe[wid][c] = double(e[c3]); }
+    }
     __syncthreads();
-    double V = 0.0, E = 0.0, tol = 0.0;
+    if (tid < P) {
+        double V = 0.0, E = 0.0;
+        for (int q = 0; q < kGroupWarps; ++q) { V += pv[q][tid]; E += pe[q][tid]; }
+        double* out = w.gpart + (size_t(s) * kGroupSplit + k) * 2 * kGroupPairs;
+        out[tid] = V;
+        out[kGroupPairs + tid] = E;
+    }
+}
+
+// Outputs of a finished group: per pair value, error, region count, status.
+__device__ void group_outputs(const Work& w, const DevBatch& B, uint32_t g, uint32_t cnt, int c,
+                              double V, double E, int st)
+{
+    const int l = B.lm[2 * c], m = B.lm[2 * c + 1];
+    const bool valid = l >= 0 && m >= 0 && l < w.nff && m < w.nff;
+    const bool finite = isfinite(V) && isfinite(E);
+    const bool conv = E <= fmax(B.abs_tol, B.rel_tol * fabs(V));
+    const int64_t o = (int64_t(g) - B.first) * B.npairs + c;
+    B.values[o] = valid ? V : NAN;
+    B.errors[o] = valid ? E : NAN;
+    B.regions[o] = cnt;
+    B.status[o] = !valid || !finite ? NONFINITE : (conv ? CONVERGED : st);
+}
+
+__global__ void __launch_bounds__(128)
+k_group_test(Work w, int max_rounds, int force_status)
+{
+    const LoopState& Ls = *w.ls;
+    const int64_t s = blockIdx.x;
+    if (s >= Ls.n_active) return;
+    const int cur = Ls.cur, round = Ls.round;
+    const int tid = threadIdx.x;
+    const uint32_t g = w.active[cur][s];
+    const uint32_t cnt = w.seg_count[g];
+    const DevBatch& B = w.batches[meta_batch(w.meta[g])];
+    const int P = B.npairs;
+    double V = 0.0, E = 0.0;
     bool valid = false, finite = true, conv = true;
     if (tid < P) {
-        for (int k = 0; k < kGroupWarps; ++k) { V += pv[k][tid]; E += pe[k][tid]; }
+        const double* part = w.gpart + size_t(s) * kGroupSplit * 2 * kGroupPairs;
+        for (int k = 0; k < kGroupSplit; ++k) {
+            V += part[k * 2 * kGroupPairs + tid];
+            E += part[k * 2 * kGroupPairs + kGroupPairs + tid];
+        }
         const int l = B.lm[2 * tid], m = B.lm[2 * tid + 1];
         valid = l >= 0 && m >= 0 && l < w.nff && m < w.nff;
         finite = isfinite(V) && isfinite(E);
-        tol = fmax(B.abs_tol, B.rel_tol * fabs(V));
+        const double tol = fmax(B.abs_tol, B.rel_tol * fabs(V));
         conv = E <= tol;
-        inv_tol[tid] = (valid && finite && !conv) ? 1.0 / fmax(tol, 1e-300) : 0.0;
+        w.gtol[size_t(s) * kGroupPairs + tid] =
+            (valid && finite && !conv) ? 1.0 / fmax(tol, 1e-300) : 0.0;
+        w.gsum[size_t(s) * 2 * kGroupPairs + tid] = V;
+        w.gsum[size_t(s) * 2 * kGroupPairs + kGroupPairs + tid] = E;
     }
     const bool any_nonfinite = __syncthreads_or(valid && !finite);
     const bool all_conv = __syncthreads_and(!valid || (finite && conv));
     const int64_t allowed = (B.max_regions - int64_t(cnt)) / 3;
-
     int st = RUNNING;
     if (force_status >= 0) st = force_status;
     else if (any_nonfinite) st = NONFINITE;
     else if (all_conv) st = CONVERGED;
     else if (round - int(w.born[g]) >= max_rounds || round >= Ls.hard_rounds) st = ROUNDCAP;
     else if (allowed <= 0) st = BUDGET;
-
-    // pass 2: region scores (lane 0 of each warp keeps the warp's sum and max)
-    double ssum = 0.0, smax = 0.0;
-    if (st == RUNNING) {
-        for (uint32_t j = wid; j < cnt; j += kGroupWarps) {
-            const size_t r = size_t(base + j) * S;
-            double sc = 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int c = lane + 32 * k;
-                if (c < P) sc = fmax(sc, double(verr[r + c]) * inv_tol[c]);
-            }
-            sc = warp_max(sc);
-            if (lane == 0) {
-                w.err[cur][base + j] = sc;
-                ssum += sc;
-                if (key_level(key[base + j]) < uint32_t(kMaxLevel)) smax = fmax(smax, sc);
-            }
-        }
-        if (lane == 0) { ps[wid] = ssum; pm[wid] = smax; }
+    if (tid == 0) w.gstate[s] = st;
+    if (st == RUNNING) return;
+    if (tid < P) group_outputs(w, B, g, cnt, tid, V, E, st);
+    if (tid == 0) {
+        if (st == ROUNDCAP && force_status < 0) atomicAdd(&w.totals->roundcap, 1ull);
+        w.cnt_new[s] = 0;
+        w.cnt_eval[s] = 0;
     }
+}
+
+__global__ void __launch_bounds__(kGroupWarps * 32) k_group_scores(Work w)
+{
+    __shared__ float itol[kGroupPairs];
+    __shared__ double ps[kGroupWarps], pm[kGroupWarps];
+    const LoopState& Ls = *w.ls;
+    const int64_t s = blockIdx.x / kGroupSplit;
+    const int k = int(blockIdx.x % kGroupSplit);
+    if (s >= Ls.n_active || w.gstate[s] != RUNNING) return;
+    const int cur = Ls.cur;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t g = w.active[cur][s];
+    const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
+    const int P = w.batches[meta_batch(w.meta[g])].npairs;
+    const size_t S = size_t(w.vstride);
+    const float* verr = w.verr[cur];
+    const uint64_t* key = w.key[cur];
+    // scores in FP32 (they only order the regions and size the selection);
+    // 1/tol saturates at the FP32 maximum
+    if (tid < P) itol[tid] = float(fmin(w.gtol[size_t(s) * kGroupPairs + tid], 3.0e38));
     __syncthreads();
-    double Ssum = 0.0, Smax = 0.0;
-    if (st == RUNNING) {
-        for (int k = 0; k < kGroupWarps; ++k) { Ssum += ps[k]; Smax = fmax(Smax, pm[k]); }
-        if (!(Smax > 0.0)) st = BUDGET;   // nothing left to split
+    uint32_t j0, j1;
+    chunk_range(cnt, k, j0, j1);
+    double ssum = 0.0, smax = 0.0;
+    for (uint32_t j = j0 + wid; j < j1; j += kGroupWarps) {
+        const size_t r = size_t(base + j) * S;
+        float sc = 0.0f;
+#pragma unroll
+        for (int c3 = 0; c3 < 3; ++c3) {
+            const int c = lane + 32 * c3;
+            if (c < P) sc = fmaxf(sc, verr[r + c] * itol[c]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sc = fmaxf(sc, __shfl_xor_sync(kFull, sc, o));
+        if (lane == 0) {
+            const double scd = double(fminf(sc, 1.0e30f));   // finite even for a zero tolerance
+            w.err[cur][base + j] = scd;
+            ssum += scd;
+            if (key_level(key[base + j]) < uint32_t(kMaxLevel)) smax = fmax(smax, scd);
+        }
     }
+    if (lane == 0) { ps[wid] = ssum; pm[wid] = smax; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < kGroupWarps; ++q) { a += ps[q]; b = fmax(b, pm[q]); }
+        w.gsc[(size_t(s) * kGroupSplit + k) * 2] = a;
+        w.gsc[(size_t(s) * kGroupSplit + k) * 2 + 1] = b;
+    }
+}
 
-    if (st != RUNNING) {
-        if (tid < P) {
-            const int64_t o = (int64_t(g) - B.first) * P + tid;
-            B.values[o] = valid ? V : NAN;
-            B.errors[o] = valid ? E : NAN;
-            B.regions[o] = cnt;
-            B.status[o] = !valid || !finite ? NONFINITE : (conv ? CONVERGED : st);
-        }
-        if (tid == 0) {
-            if (st == ROUNDCAP && force_status < 0) atomicAdd(&w.totals->roundcap, 1ull);
-            w.cnt_new[s] = 0;
-            w.cnt_eval[s] = 0;
-        }
+__global__ void __launch_bounds__(kGroupWarps * 32) k_group_select(Work w, double cover)
+{
+    __shared__ unsigned long long hsum[kHistBins];
+    __shared__ uint32_t hcnt[kHistBins];
+    const LoopState& Ls = *w.ls;
+    const int64_t s = blockIdx.x;
+    if (s >= Ls.n_active || w.gstate[s] != RUNNING) return;
+    const int cur = Ls.cur;
+    const int tid = threadIdx.x;
+    const uint32_t g = w.active[cur][s];
+    const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
+    const DevBatch& B = w.batches[meta_batch(w.meta[g])];
+    double Ssum = 0.0, Smax = 0.0;
+    for (int k = 0; k < kGroupSplit; ++k) {
+        Ssum += w.gsc[(size_t(s) * kGroupSplit + k) * 2];
+        Smax = fmax(Smax, w.gsc[(size_t(s) * kGroupSplit + k) * 2 + 1]);
+    }
+    if (!(Smax > 0.0)) {   // nothing left to split
+        if (tid < B.npairs)
+            group_outputs(w, B, g, cnt, tid, w.gsum[size_t(s) * 2 * kGroupPairs + tid],
+                          w.gsum[size_t(s) * 2 * kGroupPairs + kGroupPairs + tid], BUDGET);
+        if (tid == 0) { w.cnt_new[s] = 0; w.cnt_eval[s] = 0; }
         return;
     }
-
-    // pass 3: histogram of the scores in quarter octaves below the largest
     for (int b = tid; b < kHistBins; b += blockDim.x) { hsum[b] = 0ull; hcnt[b] = 0u; }
     __syncthreads();
+    const uint64_t* key = w.key[cur];
     const int kmax = log_key(Smax);
     const double unit = ldexp(1.0, 40) / Smax;
     for (uint32_t j = tid; j < cnt; j += blockDim.x) {
@@ -777,14 +871,21 @@ k_reduce_group(Work w, int max_rounds, double cover, int force_status)
         }
     }
     __syncthreads();
-    if (tid == 0) select_regions(w, s, hsum, hcnt, (Ssum - cover) * unit, allowed, kmax, cnt);
+    if (tid == 0) {
+        const int64_t allowed = (B.max_regions - int64_t(cnt)) / 3;
+        select_regions(w, s, hsum, hcnt, (Ssum - cover) * unit, allowed, kmax, cnt);
+    }
 }
 
 cudaError_t launch_reduce_group(const Work& w, int64_t hint_active, int max_rounds, double cover,
                                 cudaStream_t s)
 {
     if (hint_active <= 0) return cudaSuccess;
-    k_reduce_group<<<int(hint_active), kGroupWarps * 32, 0, s>>>(w, max_rounds, cover, -1);
+    const int nb = int(hint_active);
+    k_group_sums<<<nb * kGroupSplit, kGroupWarps * 32, 0, s>>>(w);
+    k_group_test<<<nb, 128, 0, s>>>(w, max_rounds, -1);
+    k_group_scores<<<nb * kGroupSplit, kGroupWarps * 32, 0, s>>>(w);
+    k_group_select<<<nb, kGroupWarps * 32, 0, s>>>(w, cover);
     return cudaGetLastError();
 }
 
@@ -859,7 +960,8 @@ cudaError_t launch_finalize(const Work& w, int64_t hint_active, int status, cuda
 {
     if (hint_active <= 0) return cudaSuccess;
     if (w.vstride > 0) {
-        k_reduce_group<<<int(hint_active), kGroupWarps * 32, 0, s>>>(w, 0, 0.0, status);
+        k_group_sums<<<int(hint_active) * kGroupSplit, kGroupWarps * 32, 0, s>>>(w);
+        k_group_test<<<int(hint_active), 128, 0, s>>>(w, 0, status);
     } else {
         const int64_t blocks = (hint_active + kWarpsPerBlock - 1) / kWarpsPerBlock;
         k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, 0, 0.0, status);

@@ -30,7 +30,8 @@ EXPORTS = ("paid_options_default", "paid_create", "paid_destroy", "paid_workspac
            "paid_integrate_multi_seeded", "paid_cell_errors", "paid_last_stats",
            "paid_error_string", "paid_last_error", "paid_mlp_param_count",
            "paid_mlp_workspace_size", "paid_mlp_init", "paid_mlp_features", "paid_mlp_forward",
-           "paid_mlp_grad", "paid_mlp_adamw", "paid_rule_regions")
+           "paid_mlp_grad", "paid_mlp_adamw", "paid_rule_regions", "paid_check_math",
+           "paid_get_options", "paid_autotune")
 
 
 class paid_options(ctypes.Structure):
@@ -38,7 +39,7 @@ class paid_options(ctypes.Structure):
                 ("eval_fp32", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("cover", ctypes.c_double), ("pool_capacity", ctypes.c_int64),
                 ("timing", ctypes.c_int), ("device_loop", ctypes.c_int),
-                ("group_mode", ctypes.c_int)]
+                ("group_mode", ctypes.c_int), ("eval_blocks", ctypes.c_int)]
 
 
 class paid_stats(ctypes.Structure):
@@ -102,6 +103,10 @@ def load(path: str = LIB_PATH):
                                                     ctypes.c_size_t, P]
         lib.paid_cell_errors.argtypes = [P, I, I, P, I, P, D, P, P, ctypes.c_size_t, P]
         lib.paid_rule_regions.argtypes = [P, I, D, P, I, P, I, P, P, P, P, ctypes.c_size_t, P]
+        lib.paid_check_math.argtypes = [P, I, I64, P, P, P, P]
+        lib.paid_get_options.argtypes = [P, ctypes.POINTER(paid_options)]
+        lib.paid_autotune.argtypes = [P, ctypes.POINTER(paid_batch), I, ctypes.c_char_p, P,
+                                      ctypes.c_size_t, P]
         lib.paid_mlp_param_count.argtypes = [ctypes.POINTER(I64)]
         lib.paid_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(ctypes.c_size_t)]
         lib.paid_mlp_init.argtypes = [P, ctypes.c_uint64, P]
@@ -260,6 +265,18 @@ class Context:
             raise PaidError(rc, self.last_error())
         return q2, dq
 
+    def check_math(self, which, x, y=None):
+        """paid_check_math on cuda float64 tensors: 0 = exp(-x), 1 = x / y."""
+        torch = _torch()
+        out = torch.empty_like(x)
+        stream = torch.cuda.current_stream(self.torch_device)
+        rc = self._lib.paid_check_math(self._h, int(which), x.numel(), x.data_ptr(),
+                                       y.data_ptr() if y is not None else None, out.data_ptr(),
+                                       ctypes.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, self.last_error())
+        return out
+
     def cell_errors(self, kind, q, lm, T, stream=None):
         """Relative log10 error maps of the uniform level-4 grid: cuda float32 [n, 256]."""
         torch = _torch()
@@ -290,7 +307,38 @@ class Context:
             raise PaidError(rc, "paid_mlp_features")
         return x
 
-    def _integrate(self, batches, pool_capacity, stream, seeded):
+    def get_options(self) -> paid_options:
+        """The context's current options (paid_get_options)."""
+        o = paid_options()
+        self._lib.paid_get_options(self._h, ctypes.byref(o))
+        self.options = o
+        return o
+
+    def autotune(self, batches, cache_path=None, stream=None):
+        """paid_autotune on device-resident sample batches (dicts as for
+        integrate_multi; their outputs are scratch).  With cache_path, an entry
+        for this GPU and mode is applied without timing.  Returns the tuned
+        options."""
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream(self.torch_device)
+        path = cache_path.encode() if cache_path else None
+        arr, outs, n, maxr = self._batch_array(batches or [])
+        nbytes = 0
+        ws = None
+        if n:
+            cap = self.default_capacity(n, maxr)
+            ws = self.workspace(n, cap)
+            nbytes = self.workspace_size(n, cap)
+        rc = self._lib.paid_autotune(self._h, arr if batches else None, len(batches or []), path,
+                                     ctypes.c_void_p(ws.data_ptr()) if ws is not None else None,
+                                     nbytes, ctypes.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, self.last_error())
+        return self.get_options()
+
+    def _batch_array(self, batches):
+        """ctypes paid_batch array and fresh output tensors for dict batches."""
         torch = _torch()
         dev = self.torch_device
         arr = (paid_batch * max(1, len(batches)))()
@@ -318,8 +366,13 @@ class Context:
             a.regions, a.status = r.regions.data_ptr(), r.status.data_ptr()
             n += nq * npairs
             maxr = max(maxr, a.max_regions)
+        return arr, outs, n, maxr
+
+    def _integrate(self, batches, pool_capacity, stream, seeded):
+        torch = _torch()
+        arr, outs, n, maxr = self._batch_array(batches)
         if stream is None:
-            stream = torch.cuda.current_stream(dev)
+            stream = torch.cuda.current_stream(self.torch_device)
         cap = pool_capacity or self.default_capacity(n, maxr)
         while True:
             ws = self.workspace(n, cap)

@@ -196,3 +196,55 @@ def test_group_static_entry(paid, torch):
     torch.cuda.synchronize()
     assert np.array_equal(r.values.cpu().numpy(), g[0])
     assert np.array_equal(r.status.cpu().numpy(), g[3])
+
+
+def test_own_exp_and_division_error_bounds(paid, torch):
+    # the group kernel's exp(-x) (Tang's table-driven method) and division
+    # (approximate reciprocal + Newton-Raphson) against correctly rounded
+    # references: at most 2 ulp, and the flush-to-zero / NaN behaviour
+    ctx = paid.Context(*LAT, ffset=9)
+    rng = np.random.default_rng(3)
+    x = np.concatenate([np.array([0.0, 1e-300, 1e-17, 5e-3, math.log(2) / 128, 1.0, 20.0,
+                                  700.0, 707.5, 745.2, 800.0, 1e6]),
+                        rng.uniform(0, 1, 20000), rng.uniform(0, 50, 20000),
+                        rng.uniform(0, 708, 20000), np.exp(rng.uniform(-40, 6, 20000))])
+    got = ctx.check_math(0, _dev(torch, x, torch.float64)).cpu().numpy()
+    ref = np.exp(-x)
+    normal = ref >= 2.0 ** -1022
+    ulp = np.spacing(ref[normal])
+    assert np.all(np.abs(got[normal] - ref[normal]) <= 2 * ulp)
+    assert np.all(got[~normal] <= 2.0 ** -1021)
+    nan = ctx.check_math(0, _dev(torch, np.array([np.nan]), torch.float64)).cpu().numpy()
+    assert np.isnan(nan[0])
+    a = rng.normal(size=40000) * np.exp(rng.uniform(-20, 20, 40000))
+    b = rng.choice([-1.0, 1.0], 40000) * np.exp(rng.uniform(-30, 30, 40000))
+    got = ctx.check_math(1, _dev(torch, a, torch.float64), _dev(torch, b, torch.float64))
+    ref = a / b
+    assert np.all(np.abs(got.cpu().numpy() - ref) <= 2 * np.spacing(np.abs(ref)))
+
+
+def test_autotune_picks_a_candidate_and_caches_it(paid, torch, tmp_path):
+    w = W.config_flow_step(T=0.05, nq=4)
+    dbs = [dict(kind=b.kind, T=b.T, q=_dev(torch, b.q, torch.float64),
+                lm=_dev(torch, b.lm, torch.int32), rel_tol=b.rel_tol, abs_tol=b.abs_tol,
+                max_regions=b.max_regions) for b in w.batches]
+    path = str(tmp_path / "tune.jsonl")
+    ctx = paid.Context(*LAT, ffset=9, group_mode=1)
+    o = ctx.autotune(dbs, path)
+    assert o.cover in (0.5, 0.75, 0.9, 1.0) and o.eval_blocks in (608, 1216, 4864)
+    lines = open(path).read().splitlines()
+    assert len(lines) == 1 and "group_mode=1" in lines[0]
+    # a second context applies the cached choice without a sample
+    c2 = paid.Context(*LAT, ffset=9, group_mode=1)
+    o2 = c2.autotune(None, path)
+    assert (o2.cover, o2.eval_blocks) == (o.cover, o.eval_blocks)
+    # tuned options keep parity with the oracle on the sample
+    gs = _run(paid, torch, ctx, w.batches)
+    for b, g in zip(w.batches, gs):
+        o_ = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
+                                    b.max_regions)
+        assert assert_parity(g, o_, b.rel_tol, b.abs_tol, batch_ident(b)) >= 0.9 * b.n
+    # a per-integral context keeps its own entry (another key)
+    c3 = paid.Context(*LAT, ffset=9)
+    c3.autotune(dbs[:1], path)
+    assert len(open(path).read().splitlines()) == 2
