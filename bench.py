@@ -67,6 +67,9 @@ def parse_args():
                          "start; plain: one partition per integral, FP64, uniform start; "
                          "fp32: per integral, FP32 / float-float evaluation; learned_fp32: "
                          "fp32 with the seeded start")
+    ap.add_argument("--rule-n", type=int, choices=[4, 6], default=6,
+                    help="N of the nested rule for the reference arm and for GPU runs without "
+                         "the autotuner (the GPU arm's tuner chooses it otherwise)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="group paths: keep the default cover and evaluation grid")
     ap.add_argument("--no-learned", action="store_true",
@@ -93,7 +96,7 @@ def workload(name):
     return W.config_flow_step(), 9
 
 
-def workload_config(w, ff, eval_mode):
+def workload_config(w, ff, eval_mode, rule_n=4):
     b0 = w.batches[0]
     return {
         "workload": w.name,
@@ -106,7 +109,9 @@ def workload_config(w, ff, eval_mode):
         "rel_tol": b0.rel_tol,
         "abs_tol": b0.abs_tol,
         "max_regions": b0.max_regions,
-        "rule": "nested Clenshaw-Curtis 5x5 in 9x9",
+        "rule": "nested Clenshaw-Curtis %dx%d in %dx%d (N = %d)" % (rule_n + 1, rule_n + 1,
+                                                                    2 * rule_n + 1, 2 * rule_n + 1,
+                                                                    rule_n),
         "init_level": 2,
         "eval": eval_mode,
         "lattice": {"t": w.lattice[0], "tp": w.lattice[1], "mu": w.lattice[2]},
@@ -180,7 +185,7 @@ def fp64_peak(device):
 
 
 # --------------------------------------------------------------------------- oracle
-def cpu_baseline(w, sample, seed=1234):
+def cpu_baseline(w, sample, seed=1234, rule_n=4):
     import numpy as np
     import oracle
     from paper_1610_09991_gb300 import workloads as W
@@ -191,12 +196,12 @@ def cpu_baseline(w, sample, seed=1234):
     t0 = time.perf_counter()
     v, e, r, s = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
                                        flat["T"][idx], w.lattice, b0.rel_tol, b0.abs_tol,
-                                       b0.max_regions)
+                                       b0.max_regions, rule_n=rule_n)
     dt = time.perf_counter() - t0
     conv = int((s == 0).sum())
     return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d seeded integrals (seed %d) of the %d-integral batch, all %d host "
-                      "threads, %.1f s" % (len(idx), seed, w.n, cores, dt),
+                      "threads, rule N = %d, %.1f s" % (len(idx), seed, w.n, cores, rule_n, dt),
             "seconds": dt, "converged": conv, "regions_mean": float(r.mean())}, (idx, v, s)
 
 
@@ -250,7 +255,7 @@ def run_reference(args):
         t0 = time.perf_counter()
         v, e, r, s = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
                                            flat["T"][idx], w.lattice, b0.rel_tol, b0.abs_tol,
-                                           b0.max_regions)
+                                           b0.max_regions, rule_n=args.rule_n)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
@@ -262,10 +267,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, ff, "fp64"),
+            "config": workload_config(w, ff, "fp64", args.rule_n),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d seeded integrals per step (seeds 5000+k) of the "
-                                       "%d-integral batch, %d host threads" % (per_step, w.n, cores)},
+                                       "%d-integral batch, %d host threads, rule N = %d"
+                                       % (per_step, w.n, cores, args.rule_n)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -294,7 +300,8 @@ def run_paid(args):
     group = 1 if args.path in ("group", "learned") else 0
     learned = args.path in ("learned", "learned_fp32")
     ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1,
-                    eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group)
+                    eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group,
+                    rule_n=args.rule_n if group else 4)
     dev = torch.device("cuda", local)
     # N > 1: the temperature sweep is one fixed job split across the ranks by
     # q row (cost-balanced, no exchange; strong scaling); every other workload
@@ -320,7 +327,7 @@ def run_paid(args):
         t0 = time.perf_counter()
         sample = [dict(d, q=d["q"][::6].contiguous()) for d in dbs]
         o = ctx.autotune(sample)
-        tune = {"cover": o.cover, "eval_blocks": o.eval_blocks,
+        tune = {"rule_n": o.rule_n, "cover": o.cover, "eval_blocks": o.eval_blocks,
                 "seconds": time.perf_counter() - t0,
                 "sample": "every 6th q point of each batch (%d integrals)"
                           % sum(int(d["q"].shape[0]) * int(d["lm"].shape[0]) for d in sample)}
@@ -449,7 +456,7 @@ def run_paid(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
         "dtype": "f64" if args.eval == "fp64" else "f32+f64", "data": "synthetic",
-        "config": dict(workload_config(w_job, ff, args.eval),
+        "config": dict(workload_config(w_job, ff, args.eval, ctx.options.rule_n),
                        partition="one per (kind, q) group" if group else "one per integral",
                        parallelism="%d ranks, %s" % (world, "q rows split across ranks"
                                                      if scaling == "strong" else
@@ -490,7 +497,8 @@ def run_paid(args):
         # no per-kernel events
         cg = P.Context(*w.lattice, ffset=ff, device=local, device_loop=1,
                        eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group,
-                       cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks)
+                       cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks,
+                       rule_n=ctx.options.rule_n)
 
         def gstep():
             flush.fill_(1)
@@ -523,25 +531,40 @@ def run_paid(args):
         cg.close()
         torch.cuda.empty_cache()
     if args.path not in ("plain",) and not args.no_compare:
-        # the plain FP64 GPU path on the same batch, one timed step
+        # the plain FP64 GPU path (one partition per integral) on the same batch:
+        # with its own autotuned rule and cover, and with the library defaults
+        def timed_plain(c):
+            c.integrate_multi(dbs, stream=stream)        # warm-up (workspace)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = c.integrate_multi(dbs, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            v_ = torch.cat([x.values for x in o]).cpu().numpy()
+            s_ = torch.cat([x.status for x in o]).cpu().numpy()
+            st_ = c.last_stats()
+            blk = {"value": float((s_ == 0).sum()) * world / t, "unit": UNIT, "ms_per_step": 1e3 * t,
+                   "region_evals": st_["region_evals"], "eval_ms": st_["eval_ms"],
+                   "rule_n": c.options.rule_n, "cover": c.options.cover}
+            del o
+            c.close()
+            torch.cuda.empty_cache()
+            return blk, v_, s_
+
         c64 = P.Context(*w.lattice, ffset=ff, device=local, timing=1)
-        c64.integrate_multi(dbs, stream=stream)        # warm-up (workspace)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        o64 = c64.integrate_multi(dbs, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t64 = e0.elapsed_time(e1) / 1e3
-        v64 = torch.cat([o.values for o in o64]).cpu().numpy()
-        s64 = torch.cat([o.status for o in o64]).cpu().numpy()
-        st64 = c64.last_stats()
-        del o64
-        c64.close()
-        torch.cuda.empty_cache()
-        line["plain_fp64"] = {"value": float((s64 == 0).sum()) * world / t64, "unit": UNIT,
-                              "ms_per_step": 1e3 * t64, "region_evals": st64["region_evals"],
-                              "eval_ms": st64["eval_ms"]}
+        if not args.no_autotune:
+            t0 = time.perf_counter()
+            c64.autotune([dict(d, q=d["q"][::6].contiguous()) for d in dbs])
+            c64.release_workspace()
+            tune64 = time.perf_counter() - t0
+        line["plain_fp64"], v64, s64 = timed_plain(c64)
+        if not args.no_autotune:
+            line["plain_fp64"]["autotune_seconds"] = tune64
+            line["plain_fp64_default"], _, _ = timed_plain(
+                P.Context(*w.lattice, ffset=ff, device=local, timing=1))
+            line["speedup_vs_plain_fp64_default"] = value / line["plain_fp64_default"]["value"]
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
         flat = W.flatten(w)
         ident_all = lambda i: (int(flat["kind"][i]), flat["q"][i], int(flat["lm"][i][0]),
@@ -590,7 +613,7 @@ def run_paid(args):
             cl.close()
             torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, (idx, vo, so) = cpu_baseline(w, args.cpu_sample)
+        cb, (idx, vo, so) = cpu_baseline(w, args.cpu_sample, rule_n=ctx.options.rule_n)
         line["cpu_baseline"] = cb
         flat = W.flatten(w)
         ident_s = lambda i: (int(flat["kind"][idx[i]]), flat["q"][idx[i]], int(flat["lm"][idx[i]][0]),

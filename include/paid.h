@@ -227,15 +227,16 @@ int paid_check_math(paid_ctx* ctx, int which, int64_t n, const double* x, const 
 /* The context's current options (after paid_autotune, say). */
 int paid_get_options(paid_ctx* ctx, paid_options* out);
 
-/* Autotuner: picks options.cover (how many regions a round splits) and, in
- * group_mode, options.eval_blocks (the evaluation grid) for this GPU by
- * timing paid_integrate_multi on `sample` (a few batches the caller chose as
- * representative; their outputs are overwritten) for every candidate:
- * cover in {0.5, 0.75, 0.9, 1.0} x eval_blocks in {608, 1216, 4864} (group
- * mode) or {default}.  The fastest candidate that completes becomes the
- * context's setting.
+/* Autotuner: picks options.rule_n (the nested rule's N; the paper reports N = 6
+ * as its best-performing setting, Sec. 5), options.cover (how many regions a
+ * round splits) and, in group_mode, options.eval_blocks (the evaluation grid)
+ * for this GPU by timing paid_integrate_multi on `sample` (a few batches the
+ * caller chose as representative; their outputs are overwritten) for every
+ * candidate: rule_n in {4, 6} x cover in {0.5, 0.75, 0.9, 1.0} x eval_blocks
+ * in {608, 1216, 4864} (group mode) or {default}.  The fastest candidate that
+ * completes becomes the context's setting.
  *   cache_path  NULL, or a JSON Lines file: when it holds an entry for this
- *               device name, rule_n, eval_fp32 and group_mode the entry is
+ *               device name, eval_fp32 and group_mode the entry is
  *               applied without timing (sample may then be NULL); otherwise
  *               the tuned choice is written there, replacing any older entry
  *               with the same key.

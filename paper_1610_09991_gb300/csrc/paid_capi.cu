@@ -825,7 +825,8 @@ int paid_get_options(paid_ctx* ctx, paid_options* out)
 namespace {
 
 // Autotuner cache: JSON Lines, one object per tuned configuration,
-//   {"key": "<device>|rule_n=4|eval_fp32=0|group_mode=1", "cover": 1, "eval_blocks": 608, "ms": 9.1}
+//   {"key": "<device>|eval_fp32=0|group_mode=1", "rule_n": 6, "cover": 1, "eval_blocks": 608,
+//    "ms": 9.1}
 std::string tune_key(const paid_ctx* ctx)
 {
     cudaDeviceProp prop{};
@@ -833,8 +834,8 @@ std::string tune_key(const paid_ctx* ctx)
     for (char& c : dev)
         if (c == '"' || c == '\\') c = '_';
     const paid_options& o = ctx->opt;
-    return dev + "|rule_n=" + std::to_string(o.rule_n) + "|eval_fp32=" + std::to_string(o.eval_fp32) +
-           "|group_mode=" + std::to_string(o.group_mode);
+    return dev + "|eval_fp32=" + std::to_string(o.eval_fp32) + "|group_mode=" +
+           std::to_string(o.group_mode);
 }
 
 std::vector<std::string> read_lines(const char* path)
@@ -852,19 +853,24 @@ std::vector<std::string> read_lines(const char* path)
     return lines;
 }
 
-bool cached_choice(const char* path, const std::string& key, double& cover, int& blocks)
+bool cached_choice(const char* path, const std::string& key, int& rule_n, double& cover,
+                   int& blocks)
 {
     const std::string tag = "\"key\": \"" + key + "\"";
     for (const std::string& l : read_lines(path)) {
         if (l.find(tag) == std::string::npos) continue;
-        const size_t pc = l.find("\"cover\": "), pb = l.find("\"eval_blocks\": ");
-        if (pc == std::string::npos || pb == std::string::npos) continue;
+        const size_t pr = l.find("\"rule_n\": "), pc = l.find("\"cover\": "),
+                     pb = l.find("\"eval_blocks\": ");
+        if (pr == std::string::npos || pc == std::string::npos || pb == std::string::npos)
+            continue;
+        int r = 0, b = 0;
         double c = 0.0;
-        int b = 0;
-        if (std::sscanf(l.c_str() + pc + 9, "%lf", &c) != 1 ||
+        if (std::sscanf(l.c_str() + pr + 10, "%d", &r) != 1 ||
+            std::sscanf(l.c_str() + pc + 9, "%lf", &c) != 1 ||
             std::sscanf(l.c_str() + pb + 15, "%d", &b) != 1)
             continue;
-        if (!(c >= 0.0 && c <= 1.0) || b < 0) continue;
+        if ((r != 4 && r != 6) || !(c >= 0.0 && c <= 1.0) || b < 0) continue;
+        rule_n = r;
         cover = c;
         blocks = b;
         return true;
@@ -872,15 +878,17 @@ bool cached_choice(const char* path, const std::string& key, double& cover, int&
     return false;
 }
 
-void store_choice(const char* path, const std::string& key, double cover, int blocks, double ms)
+void store_choice(const char* path, const std::string& key, int rule_n, double cover, int blocks,
+                  double ms)
 {
     const std::string tag = "\"key\": \"" + key + "\"";
     std::vector<std::string> keep;
     for (const std::string& l : read_lines(path))
         if (l.find(tag) == std::string::npos) keep.push_back(l);
     char line[512];
-    std::snprintf(line, sizeof(line), "{%s, \"cover\": %.17g, \"eval_blocks\": %d, \"ms\": %.6g}",
-                  tag.c_str(), cover, blocks, ms);
+    std::snprintf(line, sizeof(line),
+                  "{%s, \"rule_n\": %d, \"cover\": %.17g, \"eval_blocks\": %d, \"ms\": %.6g}",
+                  tag.c_str(), rule_n, cover, blocks, ms);
     keep.push_back(line);
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
@@ -899,9 +907,11 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
 {
     if (!ctx) return PAID_ERR_ARG;
     const std::string key = tune_key(ctx);
+    int rule_n = ctx->opt.rule_n;
     double cover = ctx->opt.cover;
     int blocks = ctx->opt.eval_blocks;
-    if (cache_path && cached_choice(cache_path, key, cover, blocks)) {
+    if (cache_path && cached_choice(cache_path, key, rule_n, cover, blocks)) {
+        ctx->opt.rule_n = rule_n;
         ctx->opt.cover = cover;
         ctx->opt.eval_blocks = blocks;
         return PAID_OK;
@@ -911,6 +921,7 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const paid_options saved = ctx->opt;
     ctx->opt.timing = 0;
+    const int rules[] = {4, 6};
     const double covers[] = {0.5, 0.75, 0.9, 1.0};
     std::vector<int> grids = {0};
     if (saved.group_mode) grids = {152 * 4, 152 * 8, 152 * 32};
@@ -921,32 +932,35 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
         return fail(ctx, PAID_ERR_CUDA, "autotune events");
     }
     double best_ms = 1e300, best_cover = saved.cover;
-    int best_blocks = saved.eval_blocks;
+    int best_blocks = saved.eval_blocks, best_rule = saved.rule_n;
     bool warm = false;
-    for (int g : grids)
-        for (double c : covers) {
-            ctx->opt.cover = c;
-            ctx->opt.eval_blocks = g;
-            if (!warm) {   // first call: graph capture, tables, caches
-                paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
-                warm = true;
+    for (int rn : rules)
+        for (int g : grids)
+            for (double c : covers) {
+                ctx->opt.rule_n = rn;
+                ctx->opt.cover = c;
+                ctx->opt.eval_blocks = g;
+                if (!warm) {   // first call: graph capture, tables, caches
+                    paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+                    warm = true;
+                }
+                cudaEventRecord(e0, s);
+                const int rc = paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+                cudaEventRecord(e1, s);
+                float ms = 0.f;
+                if (rc != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                    continue;
+                if (ms < best_ms) { best_ms = ms; best_cover = c; best_blocks = g; best_rule = rn; }
             }
-            cudaEventRecord(e0, s);
-            const int rc = paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
-            cudaEventRecord(e1, s);
-            float ms = 0.f;
-            if (rc != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
-                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                continue;
-            if (ms < best_ms) { best_ms = ms; best_cover = c; best_blocks = g; }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->opt = saved;
     if (best_ms >= 1e300) return fail(ctx, PAID_ERR_CUDA, "autotune: no candidate completed");
+    ctx->opt.rule_n = best_rule;
     ctx->opt.cover = best_cover;
     ctx->opt.eval_blocks = best_blocks;
-    if (cache_path) store_choice(cache_path, key, best_cover, best_blocks, best_ms);
+    if (cache_path) store_choice(cache_path, key, best_rule, best_cover, best_blocks, best_ms);
     return PAID_OK;
 }
 

@@ -232,19 +232,34 @@ def test_autotune_picks_a_candidate_and_caches_it(paid, torch, tmp_path):
     ctx = paid.Context(*LAT, ffset=9, group_mode=1)
     o = ctx.autotune(dbs, path)
     assert o.cover in (0.5, 0.75, 0.9, 1.0) and o.eval_blocks in (608, 1216, 4864)
+    assert o.rule_n in (4, 6)
     lines = open(path).read().splitlines()
     assert len(lines) == 1 and "group_mode=1" in lines[0]
     # a second context applies the cached choice without a sample
     c2 = paid.Context(*LAT, ffset=9, group_mode=1)
     o2 = c2.autotune(None, path)
-    assert (o2.cover, o2.eval_blocks) == (o.cover, o.eval_blocks)
+    assert (o2.rule_n, o2.cover, o2.eval_blocks) == (o.rule_n, o.cover, o.eval_blocks)
     # tuned options keep parity with the oracle on the sample
     gs = _run(paid, torch, ctx, w.batches)
     for b, g in zip(w.batches, gs):
         o_ = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
-                                    b.max_regions)
+                                    b.max_regions, rule_n=o.rule_n)
         assert assert_parity(g, o_, b.rel_tol, b.abs_tol, batch_ident(b)) >= 0.9 * b.n
     # a per-integral context keeps its own entry (another key)
     c3 = paid.Context(*LAT, ffset=9)
     c3.autotune(dbs[:1], path)
     assert len(open(path).read().splitlines()) == 2
+
+
+def test_group_rule_n6_flow_step_matches_oracle(paid, torch):
+    # the paper's best-performing rule (N = 6: 7 x 7 inside 13 x 13) in group mode,
+    # against the oracle with the same rule and with the N = 4 rule
+    w = W.config_flow_step(T=0.05, nq=4)
+    ctx = paid.Context(*w.lattice, ffset=9, group_mode=1, rule_n=6, cover=1.0)
+    gs = _run(paid, torch, ctx, w.batches)
+    for b, g in zip(w.batches, gs):
+        assert np.all(np.isin(g[3], [0, 1]))
+        for rn in (6, 4):
+            o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
+                                       b.max_regions, rule_n=rn)
+            assert assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b)) >= 0.9 * b.n
