@@ -44,18 +44,19 @@ EVAL_DRAM_BYTES_PER_REGION = 18.3
 # launches of a run divided by the regions that kernel evaluated
 # (profiles/k_eval_df_first_shell.md).
 DF_FP32_FLOPS_PER_REGION = 2 * 7774.8 + 29243.1 + 3018.3   # 47,811
-# FP64 flops per region of the shared-partition kernel (k_eval_group, N = 4,
-# 81 pairs): 81 kernel evaluations, the 2 x 81 separable moments and the pair
-# map, counted from the source (per node ~104 flops for the energies and F,
-# 20 for the fine row sums, 20 x 25/81 for the coarse ones; per region 2394
-# for the moments, ~1620 for the pairs, ~1080 for the row / column set-up).
-GROUP_FP64_FLOPS_PER_REGION = 81 * 124 + 25 * 20 + 2394 + 1620 + 1080
+# FP64 flops per region of the shared-partition kernel (k_eval_group, 81 pairs)
+# by rule order N: DFMA counted as 2, DADD / DMUL as 1, from the ncu
+# instruction counters of one launch over 10^5 regions per N divided by the
+# regions (profiles/k_eval_group_flow_step_q4.md).
+GROUP_FP64_FLOPS_PER_REGION = {4: 2 * 4839 + 735 + 2216, 6: 2 * 8955 + 1441 + 4080,
+                               8: 2 * 14367 + 2403 + 6568, 10: 2 * 21075 + 3621 + 9680,
+                               12: 2 * 29079 + 5095 + 13416}
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
     ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep"],
@@ -67,9 +68,10 @@ def parse_args():
                          "start; plain: one partition per integral, FP64, uniform start; "
                          "fp32: per integral, FP32 / float-float evaluation; learned_fp32: "
                          "fp32 with the seeded start")
-    ap.add_argument("--rule-n", type=int, choices=[4, 6], default=6,
-                    help="N of the nested rule for the reference arm and for GPU runs without "
-                         "the autotuner (the GPU arm's tuner chooses it otherwise)")
+    ap.add_argument("--rule-n", type=int, choices=[4, 6, 8, 10, 12], default=12,
+                    help="N of the nested rule for the reference arm and for group-mode GPU runs "
+                         "without the autotuner (the GPU arm's tuner chooses it otherwise; on "
+                         "GB300 it picks 12)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="group paths: keep the default cover and evaluation grid")
     ap.add_argument("--no-learned", action="store_true",
@@ -422,14 +424,15 @@ def run_paid(args):
     eval_s = agg["eval_ms"] / 1e3
     roof = None
     if group and eval_s > 0:
-        achieved = agg["region_evals"] * GROUP_FP64_FLOPS_PER_REGION / eval_s / 1e12
+        fpr = GROUP_FP64_FLOPS_PER_REGION[ctx.options.rule_n]
+        achieved = agg["region_evals"] * fpr / eval_s / 1e12
         pk = peaks.get("fp64_fma_tflops")
         roof = {"bound": "alu", "kernel": "k_eval_group", "achieved": achieved, "peak": pk,
                 "unit": "TFLOP/s", "frac": achieved / pk if pk else None, "traffic": None,
-                "traffic_note": "compute-bound: 16 B of eval list / key read and 81 x 12 B of "
-                                "pair vectors written per region for ~15,600 FP64 flops",
+                "traffic_note": "compute-bound: ~20 B of eval list / key read and 81 x 12 B of "
+                                "pair vectors written per region for %d FP64 flops" % fpr,
                 "peak_source": "measured FP64 FMA micro-benchmark in this run (pipe_peaks.cu)",
-                "flops_per_region": GROUP_FP64_FLOPS_PER_REGION}
+                "flops_per_region": fpr, "rule_n": ctx.options.rule_n}
     elif FP64_FLOPS_PER_NODE and eval_s > 0 and args.eval == "fp64":
         achieved = agg["node_evals"] * FP64_FLOPS_PER_NODE / eval_s / 1e12
         pk = peaks.get("fp64_fma_tflops")
@@ -589,8 +592,9 @@ def run_paid(args):
                 lstep()
             torch.cuda.synchronize()
             l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            lsteps = min(args.steps, 2)   # ~3.3 s per step
             l0.record(stream)
-            louts = [lstep() for _ in range(args.steps)]
+            louts = [lstep() for _ in range(lsteps)]
             l1.record(stream)
             torch.cuda.synchronize()
             tl = l0.elapsed_time(l1) / 1e3
@@ -601,7 +605,7 @@ def run_paid(args):
             line["learned_fp32"] = {
                 "path": "learned proposal seeding + one partition per integral, FP32 / "
                         "float-float integrand, FP64 sums",
-                "value": lval, "unit": UNIT, "ms_per_step": 1e3 * tl / args.steps,
+                "value": lval, "unit": UNIT, "ms_per_step": 1e3 * tl / lsteps, "steps": lsteps,
                 "speedup_vs_plain_fp64": lval / line["plain_fp64"]["value"],
                 "train_seconds": lt, "rate": lrate,
                 "loss_first_epoch": lhist[0], "loss_last_epoch": lhist[-1],

@@ -86,7 +86,8 @@ typedef enum {
 
 /* Options; paid_options_default() fills the defaults named here. */
 typedef struct {
-    int rule_n;             /* N of the nested CC pair (coarse N, fine 2N intervals): 4 or 6. Default 4 */
+    int rule_n;             /* N of the nested CC pair (coarse N, fine 2N intervals): 4 or 6, and
+                               with group_mode also 8, 10 or 12. Default 4 */
     int init_level;         /* L0: initial uniform partition of D into 4^L0 regions, 0..8. Default 2 */
     int eval_fp32;          /* 1: integrand in FP32, sums in FP64. Default 0 (all FP64) */
     int max_rounds;         /* cap on refinement rounds of an integral, counted from the round
@@ -231,10 +232,11 @@ int paid_get_options(paid_ctx* ctx, paid_options* out);
  * as its best-performing setting, Sec. 5), options.cover (how many regions a
  * round splits) and, in group_mode, options.eval_blocks (the evaluation grid)
  * for this GPU by timing paid_integrate_multi on `sample` (a few batches the
- * caller chose as representative; their outputs are overwritten) for every
- * candidate: rule_n in {4, 6} x cover in {0.5, 0.75, 0.9, 1.0} x eval_blocks
- * in {608, 1216, 4864} (group mode) or {default}.  The fastest candidate that
- * completes becomes the context's setting.
+ * caller chose as representative; their outputs are overwritten), stagewise:
+ * rule_n in {4, 6} (group mode: {4, 6, 8, 10, 12}) at cover 1, then cover in
+ * {0.5, 0.75, 0.9, 1.0}, then eval_blocks in {608, 1216, 4864} (group mode),
+ * each with the choices made so far.  The fastest candidate that completes
+ * becomes the context's setting.
  *   cache_path  NULL, or a JSON Lines file: when it holds an entry for this
  *               device name, eval_fp32 and group_mode the entry is
  *               applied without timing (sample may then be NULL); otherwise

@@ -213,7 +213,11 @@ struct DeviceGuard {
 
 int check_options(const paid_options& o, std::string& why)
 {
-    if (o.rule_n != 4 && o.rule_n != 6) { why = "rule_n must be 4 or 6"; return PAID_ERR_ARG; }
+    const bool high = o.rule_n == 8 || o.rule_n == 10 || o.rule_n == 12;
+    if (o.rule_n != 4 && o.rule_n != 6 && !(high && o.group_mode)) {
+        why = "rule_n must be 4 or 6 (or 8, 10, 12 with group_mode)";
+        return PAID_ERR_ARG;
+    }
     if (o.init_level < 0 || o.init_level > 8) { why = "init_level must be in 0..8"; return PAID_ERR_ARG; }
     if (o.eval_fp32 != 0 && o.eval_fp32 != 1) { why = "eval_fp32 must be 0 or 1"; return PAID_ERR_ARG; }
     if (o.max_rounds < 1) { why = "max_rounds must be >= 1"; return PAID_ERR_ARG; }
@@ -869,7 +873,7 @@ bool cached_choice(const char* path, const std::string& key, int& rule_n, double
             std::sscanf(l.c_str() + pc + 9, "%lf", &c) != 1 ||
             std::sscanf(l.c_str() + pb + 15, "%d", &b) != 1)
             continue;
-        if ((r != 4 && r != 6) || !(c >= 0.0 && c <= 1.0) || b < 0) continue;
+        if (r < 4 || r > 12 || r % 2 != 0 || !(c >= 0.0 && c <= 1.0) || b < 0) continue;
         rule_n = r;
         cover = c;
         blocks = b;
@@ -921,7 +925,8 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const paid_options saved = ctx->opt;
     ctx->opt.timing = 0;
-    const int rules[] = {4, 6};
+    std::vector<int> rules = {4, 6};
+    if (saved.group_mode) rules.insert(rules.end(), {8, 10, 12});
     const double covers[] = {0.5, 0.75, 0.9, 1.0};
     std::vector<int> grids = {0};
     if (saved.group_mode) grids = {152 * 4, 152 * 8, 152 * 32};
@@ -934,25 +939,31 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
     double best_ms = 1e300, best_cover = saved.cover;
     int best_blocks = saved.eval_blocks, best_rule = saved.rule_n;
     bool warm = false;
-    for (int rn : rules)
-        for (int g : grids)
-            for (double c : covers) {
-                ctx->opt.rule_n = rn;
-                ctx->opt.cover = c;
-                ctx->opt.eval_blocks = g;
-                if (!warm) {   // first call: graph capture, tables, caches
-                    paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
-                    warm = true;
-                }
-                cudaEventRecord(e0, s);
-                const int rc = paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
-                cudaEventRecord(e1, s);
-                float ms = 0.f;
-                if (rc != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
-                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                    continue;
-                if (ms < best_ms) { best_ms = ms; best_cover = c; best_blocks = g; best_rule = rn; }
-            }
+    // time one candidate; keep it when it is the fastest so far
+    auto trial = [&](int rn, double c, int g) {
+        ctx->opt.rule_n = rn;
+        ctx->opt.cover = c;
+        ctx->opt.eval_blocks = g;
+        if (!warm) {   // first call: graph capture, tables, caches
+            paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+            warm = true;
+        }
+        cudaEventRecord(e0, s);
+        const int rc = paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (rc != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            return;
+        if (ms < best_ms) { best_ms = ms; best_cover = c; best_blocks = g; best_rule = rn; }
+    };
+    // stagewise: the rule order at cover 1 and the largest grid, then cover,
+    // then the grid, each with the choices made so far
+    for (int rn : rules) trial(rn, 1.0, grids.back());
+    const int rule_pick = best_rule;
+    for (double c : covers) trial(rule_pick, c, grids.back());
+    const double cover_pick = best_cover;
+    for (int g : grids) trial(rule_pick, cover_pick, g);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->opt = saved;

@@ -30,21 +30,22 @@
 
 namespace paid {
 
-// rule variant 0: N = 4 (5 x 5 coarse inside 9 x 9 fine); 1: N = 6 (7 inside 13)
-__constant__ double c_wf[2][2 * kMaxRuleN + 1];   // fine CC weights on [-1, 1]
-__constant__ double c_wc[2][kMaxRuleN + 1];       // coarse CC weights
-__constant__ double c_t[2][2 * kMaxRuleN + 1];    // fine nodes t_i = cos(i pi / 2N)
-__constant__ double c_co[2][kMaxLevel + 1][kMaxRuleN + 1];  // cos(pi 2^-L t_i), i <= N
-__constant__ double c_so[2][kMaxLevel + 1][kMaxRuleN + 1];  // sin(pi 2^-L t_i)
+// rule variant v = (N - 4) / 2: N = 4 (5 x 5 coarse inside 9 x 9 fine), 6 (7 inside
+// 13), and for the shared-partition kernel only 8, 10, 12 (13 inside 25)
+__constant__ double c_wf[kRuleVariants][2 * kMaxRuleN + 1];   // fine CC weights on [-1, 1]
+__constant__ double c_wc[kRuleVariants][kMaxRuleN + 1];       // coarse CC weights
+__constant__ double c_t[kRuleVariants][2 * kMaxRuleN + 1];    // fine nodes t_i = cos(i pi / 2N)
+__constant__ double c_co[kRuleVariants][kMaxLevel + 1][kMaxRuleN + 1];  // cos(pi 2^-L t_i), i <= N
+__constant__ double c_so[kRuleVariants][kMaxLevel + 1][kMaxRuleN + 1];  // sin(pi 2^-L t_i)
 __constant__ double c_ff[9][3][3];                // f_n = sum_ab C[a][b] X_a Y_b
-__constant__ float c_wf32[2][2 * kMaxRuleN + 1];  // FP32 copies for the FP32 path
-__constant__ float2 c_wfdf[2][2 * kMaxRuleN + 1]; // (hi, lo) pairs for the float-float path
-__constant__ float2 c_wcdf[2][kMaxRuleN + 1];
+__constant__ float c_wf32[2][2 * kMaxRuleNLow + 1];  // FP32 copies for the FP32 path
+__constant__ float2 c_wfdf[2][2 * kMaxRuleNLow + 1]; // (hi, lo) pairs for the float-float path
+__constant__ float2 c_wcdf[2][kMaxRuleNLow + 1];
 __constant__ float2 c_exp2tab[64];                // 2^(j/64) as (hi, lo), j = 0..63
-__constant__ float2 c_codf[2][kMaxLevel + 1][kMaxRuleN + 1];  // c_co / c_so as (hi, lo)
-__constant__ float2 c_sodf[2][kMaxLevel + 1][kMaxRuleN + 1];
+__constant__ float2 c_codf[2][kMaxLevel + 1][kMaxRuleNLow + 1];  // c_co / c_so as (hi, lo)
+__constant__ float2 c_sodf[2][kMaxLevel + 1][kMaxRuleNLow + 1];
 __constant__ float2 c_ffdf[9][3][3];              // c_ff as (hi, lo)
-__constant__ float c_wc32[2][kMaxRuleN + 1];
+__constant__ float c_wc32[2][kMaxRuleNLow + 1];
 __constant__ float c_ff32[9][3][3];
 // the non-zero terms of c_ff: f_n = sum_{k < c_ffn[n]} c_ffc[n][k] X_a Y_b, a = c_ffa, b = c_ffb
 __constant__ int c_ffn[9];
@@ -74,10 +75,12 @@ cudaError_t init_rule_tables(int device)
     static bool done[64] = {false};
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     if (done[device]) return cudaSuccess;
-    double wf[2][2 * kMaxRuleN + 1] = {}, wc[2][kMaxRuleN + 1] = {}, t[2][2 * kMaxRuleN + 1] = {};
-    double co[2][kMaxLevel + 1][kMaxRuleN + 1] = {}, so[2][kMaxLevel + 1][kMaxRuleN + 1] = {};
-    const int Ns[2] = {4, 6};
-    for (int v = 0; v < 2; ++v) {
+    double wf[kRuleVariants][2 * kMaxRuleN + 1] = {}, wc[kRuleVariants][kMaxRuleN + 1] = {};
+    double t[kRuleVariants][2 * kMaxRuleN + 1] = {};
+    double co[kRuleVariants][kMaxLevel + 1][kMaxRuleN + 1] = {};
+    double so[kRuleVariants][kMaxLevel + 1][kMaxRuleN + 1] = {};
+    const int Ns[kRuleVariants] = {4, 6, 8, 10, 12};
+    for (int v = 0; v < kRuleVariants; ++v) {
         int N = Ns[v];
         cc_weights(2 * N, wf[v]);
         cc_weights(N, wc[v]);
@@ -101,26 +104,26 @@ cudaError_t init_rule_tables(int device)
     ff[6][2][2] = 2.0;                      // 2 sx sy
     ff[7][2][1] = 2.0;                      // 2 sx cy
     ff[8][1][2] = 2.0;                      // 2 cx sy
-    float wf32[2][2 * kMaxRuleN + 1], wc32[2][kMaxRuleN + 1], ff32[9][3][3];
+    float wf32[2][2 * kMaxRuleNLow + 1], wc32[2][kMaxRuleNLow + 1], ff32[9][3][3];
     for (int v = 0; v < 2; ++v) {
-        for (int i = 0; i < 2 * kMaxRuleN + 1; ++i) wf32[v][i] = float(wf[v][i]);
-        for (int i = 0; i < kMaxRuleN + 1; ++i) wc32[v][i] = float(wc[v][i]);
+        for (int i = 0; i < 2 * kMaxRuleNLow + 1; ++i) wf32[v][i] = float(wf[v][i]);
+        for (int i = 0; i < kMaxRuleNLow + 1; ++i) wc32[v][i] = float(wc[v][i]);
     }
     for (int a = 0; a < 9; ++a)
         for (int b = 0; b < 3; ++b)
             for (int c = 0; c < 3; ++c) ff32[a][b][c] = float(ff[a][b][c]);
-    float2 wfdf[2][2 * kMaxRuleN + 1], wcdf[2][kMaxRuleN + 1], e2t[64];
+    float2 wfdf[2][2 * kMaxRuleNLow + 1], wcdf[2][kMaxRuleNLow + 1], e2t[64];
     auto split = [](double x) { float hi = float(x); return make_float2(hi, float(x - double(hi))); };
     for (int v = 0; v < 2; ++v) {
-        for (int i = 0; i < 2 * kMaxRuleN + 1; ++i) wfdf[v][i] = split(wf[v][i]);
-        for (int i = 0; i < kMaxRuleN + 1; ++i) wcdf[v][i] = split(wc[v][i]);
+        for (int i = 0; i < 2 * kMaxRuleNLow + 1; ++i) wfdf[v][i] = split(wf[v][i]);
+        for (int i = 0; i < kMaxRuleNLow + 1; ++i) wcdf[v][i] = split(wc[v][i]);
     }
     for (int j = 0; j < 64; ++j) e2t[j] = split(std::exp2(j / 64.0));
-    float2 codf[2][kMaxLevel + 1][kMaxRuleN + 1], sodf[2][kMaxLevel + 1][kMaxRuleN + 1];
+    float2 codf[2][kMaxLevel + 1][kMaxRuleNLow + 1], sodf[2][kMaxLevel + 1][kMaxRuleNLow + 1];
     float2 ffdf[9][3][3];
     for (int v = 0; v < 2; ++v)
         for (int L = 0; L <= kMaxLevel; ++L)
-            for (int i = 0; i <= kMaxRuleN; ++i) {
+            for (int i = 0; i <= kMaxRuleNLow; ++i) {
                 codf[v][L][i] = split(co[v][L][i]);
                 sodf[v][L][i] = split(so[v][L][i]);
             }
@@ -948,6 +951,9 @@ cudaError_t launch_check_math(int which, int64_t n, const double* x, const doubl
 template <int N> struct GroupShape;
 template <> struct GroupShape<4> { static constexpr int R = 14; };   // 126 threads
 template <> struct GroupShape<6> { static constexpr int R = 9; };    // 117 threads
+template <> struct GroupShape<8> { static constexpr int R = 7; };    // 119 threads
+template <> struct GroupShape<10> { static constexpr int R = 6; };   // 126 threads
+template <> struct GroupShape<12> { static constexpr int R = 5; };   // 125 threads
 
 template <int N>
 struct GroupSmem {
@@ -970,7 +976,7 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
     constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GroupSmem<N>& S = *reinterpret_cast<GroupSmem<N>*>(smem_raw);
-    const int v = N == 4 ? 0 : 1;
+    const int v = rule_variant(N);
     const int cur = w.ls->cur;
     const int64_t n_eval = w.ls->n_eval;
     const int rho = threadIdx.x / NF, i = threadIdx.x % NF;
@@ -1113,14 +1119,31 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
     }
 }
 
+template <int N>
+static cudaError_t group_attr()
+{
+    return cudaFuncSetAttribute(k_eval_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(sizeof(GroupSmem<N>)));
+}
+
 static cudaError_t group_kernel_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_eval_group<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(sizeof(GroupSmem<4>)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_eval_group<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(sizeof(GroupSmem<6>)));
+    cudaError_t e = group_attr<4>();
+    if (e == cudaSuccess) e = group_attr<6>();
+    if (e == cudaSuccess) e = group_attr<8>();
+    if (e == cudaSuccess) e = group_attr<10>();
+    if (e == cudaSuccess) e = group_attr<12>();
     return e;
+}
+
+template <int N>
+static void group_launch(const Work& w, int64_t hint_eval, int64_t cap, Lattice lat, cudaStream_t s,
+                         double* rule_q2, double* rule_d)
+{
+    constexpr int R = GroupShape<N>::R;
+    const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, cap);
+    k_eval_group<N><<<int(blocks), R * (2 * N + 1), sizeof(GroupSmem<N>), s>>>(w, lat, rule_q2,
+                                                                               rule_d);
 }
 
 cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Lattice lat,
@@ -1128,14 +1151,12 @@ cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Latt
 {
     if (hint_eval <= 0) return cudaSuccess;
     const int64_t cap = max_blocks > 0 ? max_blocks : 152 * 32;
-    if (rule_n == 4) {
-        constexpr int R = GroupShape<4>::R;
-        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, cap);
-        k_eval_group<4><<<int(blocks), R * 9, sizeof(GroupSmem<4>), s>>>(w, lat, rule_q2, rule_d);
-    } else {
-        constexpr int R = GroupShape<6>::R;
-        const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, cap);
-        k_eval_group<6><<<int(blocks), R * 13, sizeof(GroupSmem<6>), s>>>(w, lat, rule_q2, rule_d);
+    switch (rule_n) {
+    case 4: group_launch<4>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    case 6: group_launch<6>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    case 8: group_launch<8>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    case 10: group_launch<10>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    default: group_launch<12>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
     }
     return cudaGetLastError();
 }

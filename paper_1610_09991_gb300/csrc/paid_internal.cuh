@@ -26,7 +26,10 @@
 namespace paid {
 
 constexpr int kMaxLevel = 29;          // deepest dyadic level (29-bit ix, iy)
-constexpr int kMaxRuleN = 6;           // largest supported N of the CC pair
+constexpr int kMaxRuleN = 12;          // largest supported N of the CC pair
+constexpr int kMaxRuleNLow = 6;        // largest N of the per-integral kernels
+constexpr int kRuleVariants = 5;       // N = 4, 6 (every kernel), 8, 10, 12 (group kernel)
+__host__ __device__ constexpr int rule_variant(int N) { return (N - 4) / 2; }
 constexpr int kHistBins = 64;          // error histogram: 4 bins per octave
 constexpr int kScanBlock = 1024;       // items per block of the slot scan
 constexpr double kPi = 3.14159265358979323846;

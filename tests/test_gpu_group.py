@@ -79,8 +79,9 @@ def test_rule_regions_match_the_oracle_rule(paid, torch, kind, T):
             assert np.all(np.abs(dq[r] - (ref[:, 0] - ref[:, 1])) <= 1e-12 * scale), (L, ix, iy)
 
 
-def test_rule_regions_rule_n6(paid, torch):
-    ctx = paid.Context(*LAT, ffset=9, rule_n=6)
+@pytest.mark.parametrize("N", [6, 8, 10, 12])
+def test_rule_regions_higher_order(paid, torch, N):
+    ctx = paid.Context(*LAT, ffset=9, rule_n=N, group_mode=1)
     lm = W.all_pairs(9)[::4]
     q = np.array([1.1, 0.4])
     regs = np.array([(0, 0, 0), (4, 3, 9), (11, 1000, 17)], dtype=np.int32)
@@ -89,7 +90,7 @@ def test_rule_regions_rule_n6(paid, torch):
     q2, dq = q2.cpu().numpy(), dq.cpu().numpy()
     for r, (L, ix, iy) in enumerate(regs):
         ref = np.array([oracle.region_eval(W.PP, q, int(l), int(m), 0.1, LAT, int(L), int(ix),
-                                           int(iy), rule_n=6) for l, m in lm])
+                                           int(iy), rule_n=N) for l, m in lm])
         scale = np.abs(ref).max() + 1e-300
         assert np.all(np.abs(q2[r] - ref[:, 1]) <= 1e-12 * scale)
         assert np.all(np.abs(dq[r] - (ref[:, 0] - ref[:, 1])) <= 1e-12 * scale)
@@ -232,7 +233,7 @@ def test_autotune_picks_a_candidate_and_caches_it(paid, torch, tmp_path):
     ctx = paid.Context(*LAT, ffset=9, group_mode=1)
     o = ctx.autotune(dbs, path)
     assert o.cover in (0.5, 0.75, 0.9, 1.0) and o.eval_blocks in (608, 1216, 4864)
-    assert o.rule_n in (4, 6)
+    assert o.rule_n in (4, 6, 8, 10, 12)
     lines = open(path).read().splitlines()
     assert len(lines) == 1 and "group_mode=1" in lines[0]
     # a second context applies the cached choice without a sample
@@ -251,15 +252,17 @@ def test_autotune_picks_a_candidate_and_caches_it(paid, torch, tmp_path):
     assert len(open(path).read().splitlines()) == 2
 
 
-def test_group_rule_n6_flow_step_matches_oracle(paid, torch):
-    # the paper's best-performing rule (N = 6: 7 x 7 inside 13 x 13) in group mode,
-    # against the oracle with the same rule and with the N = 4 rule
+@pytest.mark.parametrize("N", [6, 8, 10, 12])
+def test_group_higher_order_flow_step_matches_oracle(paid, torch, N):
+    # the paper's best-performing rule (N = 6: 7 x 7 inside 13 x 13) and N = 8
+    # (9 x 9 inside 17 x 17) in group mode, against the oracle with the same
+    # rule and with the N = 4 rule
     w = W.config_flow_step(T=0.05, nq=4)
-    ctx = paid.Context(*w.lattice, ffset=9, group_mode=1, rule_n=6, cover=1.0)
+    ctx = paid.Context(*w.lattice, ffset=9, group_mode=1, rule_n=N, cover=1.0)
     gs = _run(paid, torch, ctx, w.batches)
     for b, g in zip(w.batches, gs):
         assert np.all(np.isin(g[3], [0, 1]))
-        for rn in (6, 4):
+        for rn in (N, 4):
             o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
                                        b.max_regions, rule_n=rn)
             assert assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b)) >= 0.9 * b.n
