@@ -857,7 +857,8 @@ __global__ void __launch_bounds__(128) k_eval_fp64(Work w, Lattice lat)
 // Cody-Waite reduction (L1 = ln2/64 to 32 significant bits, so n L1 is exact
 // for |n| < 2^21; L2 = ln2/64 - L1), exp(r) from its degree-5 Taylor
 // polynomial (truncation r^6/720 < 2^-54 on that interval) and 2^(j/64) from a
-// 64-entry table.  Results below 2^-1022 flush to zero; NaN propagates.
+// 64-entry table; 2^m enters as an integer add to the exponent field.  Results
+// below 2^-1022 flush to zero; NaN propagates.
 __device__ __forceinline__ double exp_neg(double a, const double* tab)
 {
     a = a > 800.0 ? 800.0 : a;
@@ -872,8 +873,10 @@ __device__ __forceinline__ double exp_neg(double a, const double* tab)
     const int ni = int(n);
     const int m = ni >> 6;          // floor(n / 64)
     const int j = ni & 63;
-    const double scale = m >= -1022 ? __longlong_as_double((long long)(m + 1023) << 52) : 0.0;
-    return tab[j] * p * scale;
+    const double y = tab[j] * p;    // in [0.99, 2.02]: exponent field 1022 ... 1024
+    const long long b = __double_as_longlong(y) + ((long long)m << 52);
+    if (y != y) return y;           // NaN in, NaN out (the integer n of a NaN is arbitrary)
+    return (m >= -1022 && (b >> 52) > 0) ? __longlong_as_double(b) : 0.0;
 }
 
 // num / den for a normal, non-zero den: the approximate FP64 reciprocal of
@@ -892,13 +895,15 @@ __device__ __forceinline__ double div_nr(double num, double den)
     return fma(fma(-den, q, num), y, q);
 }
 
-// bubble_F with exp_neg and div_nr (same branches and formulas)
-__device__ __forceinline__ double bubble_F_tab(double e1, double e2, double inv2T, double inv4T,
-                                               const double* tab)
+// 2T F from the reduced energies x1 = e1/2T, x2 = e2/2T (the group kernel
+// folds 1/2T into its row coefficients and its region Jacobian): with
+// d = x1 - x2 = (e1 - e2)/2T,
+//   near (|d| <= 1/16):  2T F = v1 v2 (2 sinhc d) / ((1+u1)(1+u2))
+//   far:                 2T F = s [u2 - u1 | 1 - u1 u2] / ((1+u1)(1+u2) d)
+// (the same branches and identities as bubble_F, one factor 2T throughout).
+__device__ __forceinline__ double bubble_F2T(double x1, double x2, const double* tab)
 {
-    const double diff = e1 - e2;
-    const double d = diff * inv2T;
-    const double x1 = e1 * inv2T, x2 = e2 * inv2T;
+    const double d = x1 - x2;
     const double v1 = exp_neg(fabs(x1), tab), v2 = exp_neg(fabs(x2), tab);
     const double u1 = v1 * v1, u2 = v2 * v2;
     const double p = (1.0 + u1) * (1.0 + u2);
@@ -908,11 +913,10 @@ __device__ __forceinline__ double bubble_F_tab(double e1, double e2, double inv2
     double far = same ? (u2 - u1) : fma(-u1, u2, 1.0);
     far = neg1 ? -far : far;
     const double d2 = d * d;
-    const double sinhc = fma(d2, fma(d2, fma(d2, fma(d2, 1.0 / 362880.0, 1.0 / 5040.0),
-                                              1.0 / 120.0), 1.0 / 6.0), 1.0);
-    const double nearv = (4.0 * inv4T) * (v1 * v2) * sinhc;
-    const double num = near ? nearv : far;
-    const double den = near ? p : p * diff;
+    const double sinhc2 = fma(d2, fma(d2, fma(d2, fma(d2, 2.0 / 362880.0, 2.0 / 5040.0),
+                                               2.0 / 120.0), 2.0 / 6.0), 2.0);
+    const double num = near ? (v1 * v2) * sinhc2 : far;
+    const double den = near ? p : p * d;
     return div_nr(num, den);
 }
 
@@ -1033,26 +1037,25 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 }
             S.CY[rho][i][0] = cy;
             S.CY[rho][i][1] = cy2;
-            // e = A + B cos ky along row i, for k and for k'
-            A1 = fma(tA, cx, -lat.mu);
-            B1 = fma(tB, cx, tA);
-            A2 = fma(tA, cx2, -lat.mu);
-            B2 = fma(tB, cx2, tA);
+            // x = e / 2T = A + B cos ky along row i, for k and for k' (for pp the
+            // second energy enters with its sign flipped)
+            const double h1 = B->inv2T, h2 = pp ? -B->inv2T : B->inv2T;
+            A1 = fma(tA, cx, -lat.mu) * h1;
+            B1 = fma(tB, cx, tA) * h1;
+            A2 = fma(tA, cx2, -lat.mu) * h2;
+            B2 = fma(tB, cx2, tA) * h2;
         }
         __syncthreads();
         if (live) {
-            const double inv2T = B->inv2T, inv4T = B->inv4T;
             double rf[9], rc[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) { rf[k] = 0.0; rc[k] = 0.0; }
 #pragma unroll
             for (int j = 0; j < NF; ++j) {
-                double F = 1.0;   // OVERLAP
-                if (kind != OVERLAP) {
-                    const double e1 = fma(B1, S.CY[rho][j][0], A1);
-                    const double e2 = fma(B2, S.CY[rho][j][1], A2);
-                    F = bubble_F_tab(e1, kind == PP ? -e2 : e2, inv2T, inv4T, S.tab);
-                }
+                double F = 1.0;   // OVERLAP; the bubbles give 2T F (1/2T is in the Jacobian)
+                if (kind != OVERLAP)
+                    F = bubble_F2T(fma(B1, S.CY[rho][j][0], A1), fma(B2, S.CY[rho][j][1], A2),
+                                   S.tab);
                 const double wf = c_wf[v][j] * F;
 #pragma unroll
                 for (int k = 0; k < 9; ++k) rf[k] = fma(wf, S.Y[rho][j][k], rf[k]);
@@ -1089,7 +1092,7 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
         }
         __syncthreads();
         if (live) {
-            const double scale = ldexp(0.25, -2 * int(L));
+            const double scale = ldexp(0.25, -2 * int(L)) * (kind == OVERLAP ? 1.0 : B->inv2T);
             for (int p = i; p < P; p += NF) {
                 const int l = B->lm[2 * p], m = B->lm[2 * p + 1];
                 double q2 = 0.0, q1 = 0.0;
