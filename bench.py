@@ -48,9 +48,9 @@ DF_FP32_FLOPS_PER_REGION = 2 * 7774.8 + 29243.1 + 3018.3   # 47,811
 # by rule order N: DFMA counted as 2, DADD / DMUL as 1, from the ncu
 # instruction counters of one launch over 10^5 regions per N divided by the
 # regions (profiles/k_eval_group_flow_step_q4.md).
-GROUP_FP64_FLOPS_PER_REGION = {4: 2 * 4839 + 735 + 2216, 6: 2 * 8955 + 1441 + 4080,
-                               8: 2 * 14367 + 2403 + 6568, 10: 2 * 21075 + 3621 + 9680,
-                               12: 2 * 29079 + 5095 + 13416}
+GROUP_FP64_FLOPS_PER_REGION = {4: 2 * 4839 + 663 + 1766, 6: 2 * 8955 + 1285 + 3118,
+                               8: 2 * 14367 + 2131 + 4902, 10: 2 * 21075 + 3201 + 7118,
+                               12: 2 * 29079 + 4495 + 9766}
 
 
 def parse_args():
@@ -479,6 +479,7 @@ def run_paid(args):
         "autotune": tune,
         "budget_integrals_per_step": agg["budget"] / args.steps,
         "region_evals_per_s": agg["region_evals"] * world / elapsed,
+        "region_evals_per_step": agg["region_evals"] / args.steps,
         "node_evals_per_s": agg["node_evals"] * world / elapsed,
         "rounds_per_step": agg["rounds"] / args.steps,
         "peak_pool_regions": agg["peak_pool"],
