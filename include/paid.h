@@ -296,9 +296,10 @@ int paid_integrate_batch_static(paid_ctx* ctx, int kind,
  * ------------------------------------------------------------------------- */
 
 /* Targets for training: evaluate each integral's uniform level-4 grid once
- * (FP64) and write its map to out (device, float [nq*npairs][256], the batch
- * order of paid_integrate_batch).  Workspace as for paid_integrate_batch with
- * 4^4 initial regions per integral.  Returns PAID_OK / ERR_ARG / ERR_OOM / ERR_CUDA. */
+ * (FP64, with the context's rule, or N = 6 when the context's N is higher)
+ * and write its map to out (device, float [nq*npairs][256], the batch order
+ * of paid_integrate_batch).  Workspace as for paid_integrate_batch with 4^4
+ * initial regions per integral.  Returns PAID_OK / ERR_ARG / ERR_OOM / ERR_CUDA. */
 int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
                      const int32_t* lm, double T, float* out, void* workspace, size_t ws_bytes,
                      void* stream);

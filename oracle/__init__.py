@@ -217,3 +217,19 @@ def integrate_trace(kind, q, l, m, T, lat, rel_tol, abs_tol, max_regions,
     return dict(value=float(v[0]), error=float(e[0]), regions=int(nl[0]), status=int(st),
                 level=lev[:k].copy(), ix=ix[:k].copy(), iy=iy[:k].copy(),
                 valN=vN[:k].copy(), val2N=v2N[:k].copy(), err=er[:k].copy())
+
+
+def tu_flow_rhs(VP, VC, VD, Xpp, Xph):
+    """Right-hand sides of the truncated-unity flow equations for every transfer
+    momentum (Eqs. matmul-P, matmul-C, matmul-D of Sec. 2):
+
+        dP = V^P X^pp V^P,  dC = -V^C X^ph V^C,
+        dD = 2 V^D X^ph V^D - V^C X^ph V^D - V^D X^ph V^C,
+
+    with X the scale derivatives of the form-factor bubbles.  All arrays are
+    [nq, nff, nff] float64; the products are plain matrix products per q."""
+    VP, VC, VD, Xpp, Xph = (np.asarray(a, dtype=np.float64) for a in (VP, VC, VD, Xpp, Xph))
+    dP = VP @ Xpp @ VP
+    dC = -(VC @ Xph @ VC)
+    dD = 2.0 * (VD @ Xph @ VD) - VC @ Xph @ VD - VD @ Xph @ VC
+    return dP, dC, dD

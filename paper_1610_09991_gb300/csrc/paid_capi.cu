@@ -754,7 +754,8 @@ int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npair
     cudaError_t e;
     if ((e = launch_setup(w, 4, ctx->nff, 1, s)) != cudaSuccess ||
         (e = launch_state_init(w, n, n * 256, n * 256, n, 4, 1, s)) != cudaSuccess ||
-        (e = launch_eval(w, n * 256, ctx->opt.rule_n, 0, ctx->lat, s)) != cudaSuccess ||
+        (e = launch_eval(w, n * 256, std::min(ctx->opt.rule_n, kMaxRuleNLow), 0, ctx->lat, s)) !=
+            cudaSuccess ||
         (e = launch_cell_map(w, out, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "cell errors");
     ctx->stats.region_evals = n * 256;
