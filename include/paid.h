@@ -248,6 +248,19 @@ int paid_get_options(paid_ctx* ctx, paid_options* out);
 int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* cache_path,
                   void* workspace, size_t ws_bytes, void* stream);
 
+/* Truncated-unity products of the flow equations (Eqs. matmul-P, matmul-C,
+ * matmul-D, Sec. 2) for nq transfer momenta:
+ *   dP = VP Xpp VP,   dC = -VC Xph VC,   dD = 2 VD Xph VD - VC Xph VD - VD Xph VC
+ * All arguments are device arrays of nq row-major nff x nff FP64 matrices
+ * (1 <= nff <= 9); Xpp / Xph are the pp / ph bubble matrices in the output
+ * order of a batch whose pairs are all (l, m), l-major (idx = iq*nff*nff +
+ * l*nff + m).  The outputs must not alias the inputs.  Queued on `stream`
+ * (asynchronous; no allocation).  Returns PAID_OK, PAID_ERR_ARG or
+ * PAID_ERR_CUDA (launch error). */
+int paid_tu_flow_rhs(paid_ctx* ctx, int nq, int nff, const double* VP, const double* VC,
+                     const double* VD, const double* Xpp, const double* Xph, double* dP,
+                     double* dC, double* dD, void* stream);
+
 /* paid_integrate_batch without a workspace argument, for callers that cannot
  * allocate device memory when they need the integrals: code that runs while
  * a CUDA graph is being captured, runtimes that fix their device-memory budget

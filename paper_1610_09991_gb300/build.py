@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build", "paid")
 LIB = os.path.join(HERE, "libpaid.so")
 PEAKS_LIB = os.path.join(HERE, "libpipe_peaks.so")
-SOURCES = ["paid_eval.cu", "paid_pool.cu", "paid_capi.cu", "paid_mlp.cu"]
+SOURCES = ["paid_eval.cu", "paid_pool.cu", "paid_capi.cu", "paid_mlp.cu", "paid_tu.cu"]
 PEAKS_SOURCES = ["pipe_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

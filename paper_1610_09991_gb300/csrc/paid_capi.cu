@@ -976,6 +976,18 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
     return PAID_OK;
 }
 
+int paid_tu_flow_rhs(paid_ctx* ctx, int nq, int nff, const double* VP, const double* VC,
+                     const double* VD, const double* Xpp, const double* Xph, double* dP,
+                     double* dC, double* dD, void* stream)
+{
+    if (!ctx || nq < 0 || nff < 1 || nff > 9) return PAID_ERR_ARG;
+    if (nq > 0 && (!VP || !VC || !VD || !Xpp || !Xph || !dP || !dC || !dD)) return PAID_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    const cudaError_t e = launch_tu_rhs(nq, nff, VP, VC, VD, Xpp, Xph, dP, dC, dD,
+                                        static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PAID_OK : cuda_fail(ctx, e, "tu products");
+}
+
 int paid_mlp_features(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
                       const int32_t* lm, double T, uint16_t* x, void* stream)
 {

@@ -213,6 +213,10 @@ cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Latt
 // which = 0: the group kernel's exp(-x); 1: its division x / y (diagnostics)
 cudaError_t launch_check_math(int which, int64_t n, const double* x, const double* y, double* out,
                               cudaStream_t s);
+// paid_tu.cu: flow right-hand sides from the bubbles and couplings, per l
+cudaError_t launch_tu_rhs(int nq, int n, const double* VP, const double* VC, const double* VD,
+                          const double* Xpp, const double* Xph, double* dP, double* dC,
+                          double* dD, cudaStream_t s);
 // paid_pool.cu
 // Initial loop state: counts of the first round, buffer 0, round 0.
 cudaError_t launch_state_init(const Work& w, int64_t n_active, int64_t n_eval, int64_t pool,

@@ -31,7 +31,7 @@ EXPORTS = ("paid_options_default", "paid_create", "paid_destroy", "paid_workspac
            "paid_error_string", "paid_last_error", "paid_mlp_param_count",
            "paid_mlp_workspace_size", "paid_mlp_init", "paid_mlp_features", "paid_mlp_forward",
            "paid_mlp_grad", "paid_mlp_adamw", "paid_rule_regions", "paid_check_math",
-           "paid_get_options", "paid_autotune")
+           "paid_get_options", "paid_autotune", "paid_tu_flow_rhs")
 
 
 class paid_options(ctypes.Structure):
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
         lib.paid_rule_regions.argtypes = [P, I, D, P, I, P, I, P, P, P, P, ctypes.c_size_t, P]
         lib.paid_check_math.argtypes = [P, I, I64, P, P, P, P]
         lib.paid_get_options.argtypes = [P, ctypes.POINTER(paid_options)]
+        lib.paid_tu_flow_rhs.argtypes = [P, I, I, P, P, P, P, P, P, P, P, P]
         lib.paid_autotune.argtypes = [P, ctypes.POINTER(paid_batch), I, ctypes.c_char_p, P,
                                       ctypes.c_size_t, P]
         lib.paid_mlp_param_count.argtypes = [ctypes.POINTER(I64)]
@@ -276,6 +277,25 @@ class Context:
         if rc != OK:
             raise PaidError(rc, self.last_error())
         return out
+
+    def tu_flow_rhs(self, VP, VC, VD, Xpp, Xph, stream=None):
+        """paid_tu_flow_rhs on cuda float64 [nq, nff, nff] tensors; returns
+        (dP, dC, dD)."""
+        torch = _torch()
+        for a in (VP, VC, VD, Xpp, Xph):
+            if a.dtype != torch.float64 or not a.is_contiguous() or a.shape != VP.shape:
+                raise ValueError("contiguous float64 [nq, nff, nff] tensors expected")
+        nq, nff = VP.shape[0], VP.shape[1]
+        dP, dC, dD = (torch.empty_like(VP) for _ in range(3))
+        if stream is None:
+            stream = torch.cuda.current_stream(self.torch_device)
+        rc = self._lib.paid_tu_flow_rhs(self._h, nq, nff, VP.data_ptr(), VC.data_ptr(),
+                                        VD.data_ptr(), Xpp.data_ptr(), Xph.data_ptr(),
+                                        dP.data_ptr(), dC.data_ptr(), dD.data_ptr(),
+                                        ctypes.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, self.last_error())
+        return dP, dC, dD
 
     def cell_errors(self, kind, q, lm, T, stream=None):
         """Relative log10 error maps of the uniform level-4 grid: cuda float32 [n, 256]."""
