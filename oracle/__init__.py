@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PH, PP, MONOMIAL, OVERLAP = 0, 1, 2, 3
+PH, PP, MONOMIAL, OVERLAP, FLOW_PH, FLOW_PP = 0, 1, 2, 3, 4, 5
 CONVERGED, BUDGET, NONFINITE = 0, 1, 2
 MAX_LEVEL = 29
 
@@ -61,6 +61,10 @@ def _load():
             lib.oracle_kernel_ph.restype = _d
             lib.oracle_kernel_pp.argtypes = [_d, _d, _d]
             lib.oracle_kernel_pp.restype = _d
+            lib.oracle_kernel_flow_ph.argtypes = [_d, _d, _d]
+            lib.oracle_kernel_flow_ph.restype = _d
+            lib.oracle_kernel_flow_pp.argtypes = [_d, _d, _d]
+            lib.oracle_kernel_flow_pp.restype = _d
             lib.oracle_integrand_point.argtypes = [_i, _d, _d, _i, _i, _d, _d, _d, _d, _d, _d]
             lib.oracle_integrand_point.restype = _d
             lib.oracle_region_eval.argtypes = [_i, _d, _d, _i, _i, _d, _d, _d, _d, _i,
@@ -130,6 +134,16 @@ def kernel_ph(e1, e2, T):
 
 def kernel_pp(e1, e2, T):
     return _load().oracle_kernel_pp(e1, e2, T)
+
+
+def kernel_flow_ph(e1, e2, omega):
+    """d/dOmega of the ph frequency integral with the Omega regulator (Sec. 2)."""
+    return _load().oracle_kernel_flow_ph(e1, e2, omega)
+
+
+def kernel_flow_pp(e1, e2, omega):
+    """d/dOmega of the pp frequency integral with the Omega regulator (Sec. 2)."""
+    return _load().oracle_kernel_flow_pp(e1, e2, omega)
 
 
 def integrand_point(kind, q, l, m, T, lat, kx, ky):

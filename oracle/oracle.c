@@ -44,7 +44,7 @@
 
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_PH = 0, ORC_PP = 1, ORC_MONOMIAL = 2, ORC_OVERLAP = 3 };
+enum { ORC_PH = 0, ORC_PP = 1, ORC_MONOMIAL = 2, ORC_OVERLAP = 3, ORC_FLOW_PH = 4, ORC_FLOW_PP = 5 };
 enum { ORC_CONVERGED = 0, ORC_BUDGET = 1, ORC_NONFINITE = 2 };
 #define ORC_MAX_LEVEL 29
 #define ORC_MAX_RULE_N 16
@@ -144,12 +144,60 @@ double oracle_kernel_pp(double e1, double e2, double T)
     return fermi_diff(-e2, e1, T) / (e1 + e2);
 }
 
+/* ---------------------------------------------------------------------------
+ * Omega-regulated flow kernels: the inner frequency integrals of Eqs. chi_ph
+ * and chi_pp (Sec. 2) with G(k) = theta(k0) / (i k0 - e(k)),
+ * theta(k0) = k0^2 / (k0^2 + Omega^2), at zero temperature with measure
+ * dk0 / 2pi, differentiated with respect to Omega (the dot of the flow).
+ *
+ * Derivation (written out here because the paper only states that these
+ * integrals can be done analytically): theta^2 = 1 - 2 Omega^2 / (k0^2 + Omega^2)
+ * + Omega^4 / (k0^2 + Omega^2)^2, and 1 / ((i k0 - e1)(i k0 - e2)) =
+ * [1/(i k0 - e1) - 1/(i k0 - e2)] / (e1 - e2).  Each piece reduces to
+ *   int dk0/2pi 1 / ((k0^2 + a^2)(k0^2 + b^2)) = 1 / (2 a b (a + b))
+ * and its a-derivative (the odd parts of 1/(i k0 - e) integrate to zero), so
+ * the ph integral is the divided difference [H(e1) - H(e2)] / (e1 - e2) of
+ *   H(e) = int dk0/2pi theta^2 / (i k0 - e) = -e (2|e| + Omega) / (4 (|e| + Omega)^2),
+ * and its Omega derivative the divided difference of
+ *   Hdot(e) = e (3|e| + Omega) / (4 (|e| + Omega)^3).
+ * pp: theta is even and -i k0 - e2 = -(i k0 + e2), so the pp integral is minus
+ * the ph one at (e1, -e2).
+ *
+ * For e >= 0 with u = e + Omega, Hdot = (3/u - 5 Omega/u^2 + 2 Omega^2/u^3) / 4,
+ * and Hdot is odd, so for energies of one sign the divided difference is that
+ * of the three powers of 1/u at u_k = |e_k| + Omega, each by its exact identity
+ *   D[1/u] = -1/(u1 u2),  D[1/u^2] = -(u1 + u2)/(u1 u2)^2,
+ *   D[1/u^3] = -(u1^2 + u1 u2 + u2^2)/(u1 u2)^3;
+ * for opposite signs the two values of Hdot have opposite signs and the
+ * difference is taken directly. */
+static double flow_hdot(double e, double W)
+{
+    const double a = fabs(e), u = a + W;
+    return e * (3.0 * a + W) / (4.0 * u * u * u);
+}
+
+double oracle_kernel_flow_ph(double e1, double e2, double W)
+{
+    if ((e1 >= 0.0) != (e2 >= 0.0))
+        return (flow_hdot(e1, W) - flow_hdot(e2, W)) / (e1 - e2);
+    const double u1 = fabs(e1) + W, u2 = fabs(e2) + W, p = u1 * u2;
+    const double d1 = -1.0 / p;
+    const double d2 = -(u1 + u2) / (p * p);
+    const double d3 = -(u1 * u1 + u1 * u2 + u2 * u2) / (p * p * p);
+    return 0.25 * (3.0 * d1 - 5.0 * W * d2 + 2.0 * W * W * d3);
+}
+
+double oracle_kernel_flow_pp(double e1, double e2, double W)
+{
+    return -oracle_kernel_flow_ph(e1, -e2, W);
+}
+
 /* One integral's parameters. */
 typedef struct {
-    int kind;           /* ORC_PH, ORC_PP, ORC_MONOMIAL, ORC_OVERLAP */
+    int kind;           /* ORC_PH, ORC_PP, ORC_MONOMIAL, ORC_OVERLAP, ORC_FLOW_PH, ORC_FLOW_PP */
     double qx, qy;      /* transfer momentum */
     int l, m;           /* form-factor indices (MONOMIAL: exponents a, b) */
-    double T;           /* temperature */
+    double T;           /* temperature (flow kinds: the regulator scale Omega) */
     double t, tp, mu;   /* lattice parameters */
 } orc_integral;
 
@@ -157,7 +205,9 @@ typedef struct {
  *   ph:       f_l(k) f_m(k+q) F_ph(e(k), e(k+q))         (Eq. chi_ph, T form)
  *   pp:       f_l(k) f_m(q-k) F_pp(e(k), e(q-k))         (Eq. chi_pp, T form)
  *   overlap:  f_l(k) f_m(k+q)                             (F = 1)
- *   monomial: (kx/pi)^l (ky/pi)^m                         (rule test)      */
+ *   monomial: (kx/pi)^l (ky/pi)^m                         (rule test)
+ *   flow ph:  f_l(k) f_m(k) Fdot_ph(e(k + q/2), e(k - q/2))  (Eq. chi_ph, Omega form)
+ *   flow pp:  f_l(k) f_m(k) Fdot_pp(e(q/2 + k), e(q/2 - k))  (Eq. chi_pp, Omega form) */
 static double integrand(const orc_integral* p, double kx, double ky)
 {
     const double pref = 1.0 / (4.0 * ORC_PI * ORC_PI);
@@ -180,6 +230,13 @@ static double integrand(const orc_integral* p, double kx, double ky)
                     * oracle_form_factor(p->m, kx + p->qx, ky + p->qy);
     case ORC_MONOMIAL:
         return pref * pow(kx / ORC_PI, p->l) * pow(ky / ORC_PI, p->m);
+    case ORC_FLOW_PH:   /* symmetric routing: k +- l/2, both form factors at k */
+    case ORC_FLOW_PP:   /* e(l/2 - k) = e(k - l/2): the dispersion is even */
+        e1 = oracle_dispersion(kx + 0.5 * p->qx, ky + 0.5 * p->qy, p->t, p->tp, p->mu);
+        e2 = oracle_dispersion(kx - 0.5 * p->qx, ky - 0.5 * p->qy, p->t, p->tp, p->mu);
+        return pref * oracle_form_factor(p->l, kx, ky) * oracle_form_factor(p->m, kx, ky)
+                    * (p->kind == ORC_FLOW_PH ? oracle_kernel_flow_ph(e1, e2, p->T)
+                                              : oracle_kernel_flow_pp(e1, e2, p->T));
     default:
         return NAN;
     }
