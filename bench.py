@@ -59,7 +59,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
-    ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep"],
+    ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep",
+                                           "flow_omega"],
                     default="flow_step")
     ap.add_argument("--path", choices=["group", "learned", "plain", "fp32", "learned_fp32"],
                     default="group",
@@ -95,6 +96,8 @@ def workload(name):
         return W.config_flow_step(nq=4), 9
     if name == "sweep":
         return W.config_temperature_sweep(), 9
+    if name == "flow_omega":
+        return W.config_flow_omega(), 9
     return W.config_flow_step(), 9
 
 
@@ -103,7 +106,8 @@ def workload_config(w, ff, eval_mode, rule_n=4):
     return {
         "workload": w.name,
         "integrals": w.n,
-        "kinds": sorted({"ph" if b.kind == 0 else "pp" for b in w.batches}),
+        "kinds": sorted({{0: "ph", 1: "pp", 2: "monomial", 3: "overlap", 4: "flow ph",
+                          5: "flow pp"}[b.kind] for b in w.batches}),
         "T": b0.T if len({b.T for b in w.batches}) == 1 else sorted({b.T for b in w.batches}),
         "q_points": int(b0.q.shape[0]),
         "form_factors": ff,
@@ -298,6 +302,9 @@ def run_paid(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w, ff = workload(args.workload)
+    if args.workload == "flow_omega":
+        # the Omega-regulated flow kinds exist in the shared-partition kernel only
+        args.path, args.no_compare, args.no_learned = "group", True, True
     args.eval = "fp64" if args.path in ("plain", "group", "learned") else "fp32"
     group = 1 if args.path in ("group", "learned") else 0
     learned = args.path in ("learned", "learned_fp32")

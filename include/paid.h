@@ -19,6 +19,18 @@
  * PAID_OVERLAP (kernel = 1, integrand f_l(k) f_m(k+q)/(2pi)^2) and
  * PAID_MONOMIAL (integrand (kx/pi)^l (ky/pi)^m/(2pi)^2, 0 <= l, m <= 30).
  *
+ * The flow kinds (options.group_mode only) are the Omega-regulated bubbles of
+ * the flow equations, Eqs. chi_ph / chi_pp with G(k) = theta(k0)/(i k0 - e(k)),
+ * theta(k0) = k0^2/(k0^2 + Omega^2) (Sec. 2), at zero temperature, their
+ * frequency integral (measure dk0/2pi) done analytically and differentiated
+ * in Omega; a batch's T field carries Omega > 0.  With symmetric routing
+ * (q = the transfer momentum l of Sec. 2) and both form factors at k:
+ *   flow ph: I = (1/(2pi)^2) Int f_l(k) f_m(k) Hd(e(k + q/2), e(k - q/2)) d^2k
+ *   flow pp: I = -(1/(2pi)^2) Int f_l(k) f_m(k) Hd(e(q/2 + k), -e(q/2 - k)) d^2k
+ * where Hd(a, b) = [Hdot(a) - Hdot(b)] / (a - b) is the divided difference of
+ * Hdot(e) = e (3|e| + Omega) / (4 (|e| + Omega)^3), the Omega derivative of
+ * H(e) = Int dk0/2pi theta^2/(i k0 - e) = -e (2|e| + Omega)/(4 (|e| + Omega)^2).
+ *
  * How.  Adaptive cubature (Algorithm 1, with the 4-way split of
  * Algorithm 2): every region carries the nested Clenshaw-Curtis pair
  * Q_N, Q_2N and err = |Q_N - Q_2N| (Sec. 3); the returned value is the sum of
@@ -63,7 +75,8 @@ typedef struct paid_ctx paid_ctx;
 typedef enum { PAID_FF_SHELL1 = 5, PAID_FF_SHELL12 = 9 } paid_ffset;
 
 /* Integrand kinds. */
-typedef enum { PAID_PH = 0, PAID_PP = 1, PAID_MONOMIAL = 2, PAID_OVERLAP = 3 } paid_kind;
+typedef enum { PAID_PH = 0, PAID_PP = 1, PAID_MONOMIAL = 2, PAID_OVERLAP = 3,
+               PAID_FLOW_PH = 4, PAID_FLOW_PP = 5 } paid_kind;
 
 /* Call status. */
 typedef enum {

@@ -362,7 +362,11 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
     int64_t n_int = 0;
     for (int i = 0; i < nb; ++i) {
         const paid_batch& b = batches[i];
-        if (b.kind < PAID_PH || b.kind > PAID_OVERLAP) return fail(ctx, PAID_ERR_ARG, "bad kind");
+        if (b.kind < PAID_PH || b.kind > PAID_FLOW_PP) return fail(ctx, PAID_ERR_ARG, "bad kind");
+        if (!group && (b.kind == PAID_FLOW_PH || b.kind == PAID_FLOW_PP))
+            return fail(ctx, PAID_ERR_ARG, "the flow kinds take group_mode = 1");
+        if ((b.kind == PAID_FLOW_PH || b.kind == PAID_FLOW_PP) && !(b.T > 0.0))
+            return fail(ctx, PAID_ERR_ARG, "flow kinds: Omega (the T field) must be > 0");
         if (b.nq < 0 || b.npairs < 0) return fail(ctx, PAID_ERR_ARG, "nq, npairs must be >= 0");
         const int64_t nbi = int64_t(b.nq) * b.npairs;
         if (nbi > 0 && (!b.q || !b.lm || !b.values || !b.errors || !b.regions || !b.status))
@@ -768,8 +772,9 @@ int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int np
 {
     if (!ctx) return PAID_ERR_ARG;
     ctx->last_error.clear();
-    if (kind != PAID_PH && kind != PAID_PP && kind != PAID_OVERLAP)
-        return fail(ctx, PAID_ERR_ARG, "kind must be ph, pp or overlap");
+    if (kind != PAID_PH && kind != PAID_PP && kind != PAID_OVERLAP && kind != PAID_FLOW_PH &&
+        kind != PAID_FLOW_PP)
+        return fail(ctx, PAID_ERR_ARG, "kind must be ph, pp, overlap, flow ph or flow pp");
     if (npairs < 1 || npairs > kGroupPairs || nreg < 0)
         return fail(ctx, PAID_ERR_ARG, "npairs must be in 1..81 and nreg >= 0");
     if (!(T > 0.0) || !is_finite_d(T)) return fail(ctx, PAID_ERR_ARG, "T must be > 0");
@@ -1081,7 +1086,7 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     if (!ctx) return PAID_ERR_ARG;
     const paid_options& o = ctx->opt;
     const int64_t n0 = int64_t(1) << (2 * o.init_level);
-    if (kind < PAID_PH || kind > PAID_OVERLAP || nq < 0 || npairs < 0) return PAID_ERR_ARG;
+    if (kind < PAID_PH || kind > PAID_FLOW_PP || nq < 0 || npairs < 0) return PAID_ERR_ARG;
     const int64_t n = int64_t(nq) * npairs;
     if (n > kStaticMaxIntegrals) return PAID_ERR_ARG;
     if (n > 0 && (!q || !lm || !values || !errors || !regions || !status)) return PAID_ERR_ARG;
@@ -1089,6 +1094,7 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     if (max_regions < n0 || max_regions > kMaxRegionsPerIntegral) return PAID_ERR_ARG;
     const bool group = o.group_mode != 0;
     if (group && (kind == PAID_MONOMIAL || npairs > kGroupPairs)) return PAID_ERR_ARG;
+    if (!group && (kind == PAID_FLOW_PH || kind == PAID_FLOW_PP)) return PAID_ERR_ARG;
     ctx->stats = paid_stats{};
     ctx->stats.n_integrals = n;
     if (n == 0) return PAID_OK;

@@ -920,6 +920,31 @@ __device__ __forceinline__ double bubble_F2T(double x1, double x2, const double*
     return div_nr(num, den);
 }
 
+// Omega derivative of the frequency integrals of the flow kinds (Sec. 2,
+// regulator theta(k0) = k0^2 / (k0^2 + Omega^2), T = 0, measure dk0 / 2pi):
+// the divided difference of Hdot(e) = e (3|e| + W) / (4 (|e| + W)^3) at
+// (e1, e2) for ph and minus that at (e1, -e2) for pp.  With u = |e| + W:
+// energies of one sign (Hdot odd and smooth there):
+//   (-3 P^2 + 5 W S P - 2 W^2 (S^2 - P)) / (4 P^3),  P = u1 u2, S = u1 + u2
+// (the exact divided difference of (3/u - 5W/u^2 + 2W^2/u^3) / 4);
+// opposite signs (no cancellation):
+//   (e1 (3|e1| + W) u2^3 - e2 (3|e2| + W) u1^3) / (4 u1^3 u2^3 (e1 - e2)).
+__device__ __forceinline__ double flow_Fdot(double e1, double e2, double W, bool pp)
+{
+    if (pp) e2 = -e2;
+    const double a1 = fabs(e1), a2 = fabs(e2);
+    const double u1 = a1 + W, u2 = a2 + W;
+    const double P = u1 * u2, S = u1 + u2;
+    const bool same = (e1 >= 0.0) == (e2 >= 0.0);
+    const double u13 = u1 * u1 * u1, u23 = u2 * u2 * u2;
+    const double num_s = fma(-3.0 * P, P, W * fma(5.0 * S, P, -2.0 * W * fma(S, S, -P)));
+    const double num_o = fma(e1 * fma(3.0, a1, W), u23, -e2 * fma(3.0, a2, W) * u13);
+    const double num = same ? num_s : num_o;
+    const double den = same ? 4.0 * P * P * P : 4.0 * u13 * u23 * (e1 - e2);
+    const double D = div_nr(num, den);
+    return pp ? -D : D;
+}
+
 // Diagnostics for paid_check_math: which = 0: exp_neg(x), 1: div_nr(x, y).
 __global__ void k_check_math(int which, int64_t n, const double* x, const double* y, double* out)
 {
@@ -1012,8 +1037,8 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
             B = &w.batches[meta_batch(mt)];
             kind = meta_kind(mt);
             P = B->npairs;
-            const QTrig tq = w.trig[g];
-            const bool pp = kind == PP;
+            const QTrig tq = w.trig[g];     // flow kinds: rotation by q/2
+            const bool pp = kind == PP, flow = is_flow(kind);
             const double sxc = S.C[rho][0], cxc = S.C[rho][1];
             const double syc = S.C[rho][2], cyc = S.C[rho][3];
             const int ii = i <= N ? i : 2 * N - i;
@@ -1026,8 +1051,11 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
             const double sx2 = pp ? fma(tq.sqx, cx, -tq.cqx * sx) : fma(sx, tq.cqx, cx * tq.sqx);
             const double cy2 = pp ? fma(tq.cqy, cy, tq.sqy * sy) : fma(cy, tq.cqy, -sy * tq.sqy);
             const double sy2 = pp ? fma(tq.sqy, cy, -tq.cqy * sy) : fma(sy, tq.cqy, cy * tq.sqy);
-            const double gx[3] = {1.0, cx, sx}, gx2[3] = {1.0, cx2, sx2};
-            const double gy[3] = {1.0, cy, sy}, gy2[3] = {1.0, cy2, sy2};
+            // flow kinds: both form factors at k (symmetric routing)
+            const double gx[3] = {1.0, cx, sx};
+            const double gx2[3] = {1.0, flow ? cx : cx2, flow ? sx : sx2};
+            const double gy[3] = {1.0, cy, sy};
+            const double gy2[3] = {1.0, flow ? cy : cy2, flow ? sy : sy2};
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -1035,15 +1063,26 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                     S.X[rho][i][3 * a + c] = gx[a] * gx2[c];
                     S.Y[rho][i][3 * a + c] = gy[a] * gy2[c];
                 }
-            S.CY[rho][i][0] = cy;
-            S.CY[rho][i][1] = cy2;
-            // x = e / 2T = A + B cos ky along row i, for k and for k' (for pp the
-            // second energy enters with its sign flipped)
-            const double h1 = B->inv2T, h2 = pp ? -B->inv2T : B->inv2T;
-            A1 = fma(tA, cx, -lat.mu) * h1;
-            B1 = fma(tB, cx, tA) * h1;
-            A2 = fma(tA, cx2, -lat.mu) * h2;
-            B2 = fma(tB, cx2, tA) * h2;
+            if (flow) {
+                // e(k + q/2) and e(k - q/2): cos(k +- q/2) = cos k cos q/2 -+ sin k sin q/2
+                const double cxp = fma(cx, tq.cqx, -sx * tq.sqx), cxm = fma(cx, tq.cqx, sx * tq.sqx);
+                S.CY[rho][i][0] = fma(cy, tq.cqy, -sy * tq.sqy);
+                S.CY[rho][i][1] = fma(cy, tq.cqy, sy * tq.sqy);
+                A1 = fma(tA, cxp, -lat.mu);
+                B1 = fma(tB, cxp, tA);
+                A2 = fma(tA, cxm, -lat.mu);
+                B2 = fma(tB, cxm, tA);
+            } else {
+                S.CY[rho][i][0] = cy;
+                S.CY[rho][i][1] = cy2;
+                // x = e / 2T = A + B cos ky along row i, for k and for k' (for pp
+                // the second energy enters with its sign flipped)
+                const double h1 = B->inv2T, h2 = pp ? -B->inv2T : B->inv2T;
+                A1 = fma(tA, cx, -lat.mu) * h1;
+                B1 = fma(tB, cx, tA) * h1;
+                A2 = fma(tA, cx2, -lat.mu) * h2;
+                B2 = fma(tB, cx2, tA) * h2;
+            }
         }
         __syncthreads();
         if (live) {
@@ -1052,10 +1091,14 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
             for (int k = 0; k < 9; ++k) { rf[k] = 0.0; rc[k] = 0.0; }
 #pragma unroll
             for (int j = 0; j < NF; ++j) {
-                double F = 1.0;   // OVERLAP; the bubbles give 2T F (1/2T is in the Jacobian)
-                if (kind != OVERLAP)
-                    F = bubble_F2T(fma(B1, S.CY[rho][j][0], A1), fma(B2, S.CY[rho][j][1], A2),
-                                   S.tab);
+                // OVERLAP: 1; bubbles: 2T F (1/2T is in the Jacobian); flow: dF/dOmega
+                double F = 1.0;
+                const double x1 = fma(B1, S.CY[rho][j][0], A1);
+                const double x2 = fma(B2, S.CY[rho][j][1], A2);
+                if (is_flow(kind))
+                    F = flow_Fdot(x1, x2, B->T, kind == FLOW_PP);
+                else if (kind != OVERLAP)
+                    F = bubble_F2T(x1, x2, S.tab);
                 const double wf = c_wf[v][j] * F;
 #pragma unroll
                 for (int k = 0; k < 9; ++k) rf[k] = fma(wf, S.Y[rho][j][k], rf[k]);
@@ -1092,7 +1135,8 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
         }
         __syncthreads();
         if (live) {
-            const double scale = ldexp(0.25, -2 * int(L)) * (kind == OVERLAP ? 1.0 : B->inv2T);
+            const double scale =
+                ldexp(0.25, -2 * int(L)) * (kind == PH || kind == PP ? B->inv2T : 1.0);
             for (int p = i; p < P; p += NF) {
                 const int l = B->lm[2 * p], m = B->lm[2 * p + 1];
                 double q2 = 0.0, q1 = 0.0;

@@ -3,7 +3,7 @@
 //
 //   per integral g (global index over all batches of a call)
 //     trig[g]   QTrig (cos qx, sin qx, cos qy, sin qy)
-//     meta[g]   uint32  kind | l << 2 | m << 7 | valid << 12 | batch << 16
+//     meta[g]   uint32  kind | l << 3 | m << 8 | valid << 13 | batch << 16
 //     seg_base[g], seg_count[g]   uint32: the integral's contiguous pool segment
 //   per active slot s (the active list is compacted every round)
 //     active[s] uint32 integral index; cnt_new/cnt_eval/thr written by the
@@ -52,7 +52,8 @@ constexpr int kGroupPairs = 81;
 // chunks per group segment in the group reduce (blocks per group)
 constexpr int kGroupSplit = 8;
 
-enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3 };
+enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3, FLOW_PH = 4, FLOW_PP = 5 };
+__host__ __device__ inline bool is_flow(int kind) { return kind == FLOW_PH || kind == FLOW_PP; }
 enum Status : int { CONVERGED = 0, BUDGET = 1, NONFINITE = 2, ROUNDCAP = 3, POOL = 4, RUNNING = -1 };
 
 __host__ __device__ inline uint64_t make_key(uint32_t L, uint32_t ix, uint32_t iy)
@@ -65,19 +66,19 @@ __host__ __device__ inline uint32_t key_iy(uint64_t k) { return uint32_t(k & 0x1
 
 __host__ __device__ inline uint32_t make_meta(int kind, int l, int m, int valid, int batch)
 {
-    return uint32_t(kind & 3) | (uint32_t(l & 31) << 2) | (uint32_t(m & 31) << 7) |
-           (uint32_t(valid & 1) << 12) | (uint32_t(batch) << 16);
+    return uint32_t(kind & 7) | (uint32_t(l & 31) << 3) | (uint32_t(m & 31) << 8) |
+           (uint32_t(valid & 1) << 13) | (uint32_t(batch) << 16);
 }
-// bit 13: the integral is evaluated in FP64 (set at setup for the FP64 path,
+// bit 14: the integral is evaluated in FP64 (set at setup for the FP64 path,
 // or when its FP32 rounding noise bound exceeds half its tolerance)
-constexpr uint32_t kMetaFp64 = 1u << 13;
-// bit 14: the integral is evaluated in float-float (set when its FP32 rounding
+constexpr uint32_t kMetaFp64 = 1u << 14;
+// bit 15: the integral is evaluated in float-float (set when its FP32 rounding
 // noise exceeds a quarter of its tolerance)
-constexpr uint32_t kMetaDf32 = 1u << 14;
-__host__ __device__ inline int meta_kind(uint32_t mt) { return int(mt & 3u); }
-__host__ __device__ inline int meta_l(uint32_t mt) { return int((mt >> 2) & 31u); }
-__host__ __device__ inline int meta_m(uint32_t mt) { return int((mt >> 7) & 31u); }
-__host__ __device__ inline int meta_valid(uint32_t mt) { return int((mt >> 12) & 1u); }
+constexpr uint32_t kMetaDf32 = 1u << 15;
+__host__ __device__ inline int meta_kind(uint32_t mt) { return int(mt & 7u); }
+__host__ __device__ inline int meta_l(uint32_t mt) { return int((mt >> 3) & 31u); }
+__host__ __device__ inline int meta_m(uint32_t mt) { return int((mt >> 8) & 31u); }
+__host__ __device__ inline int meta_valid(uint32_t mt) { return int((mt >> 13) & 1u); }
 __host__ __device__ inline int meta_batch(uint32_t mt) { return int(mt >> 16); }
 
 // One batch as the kernels see it.

@@ -96,8 +96,11 @@ __device__ void setup_one(const Work& w, int64_t g, int64_t g0, int L0, int nff,
     else
         valid = l >= 0 && m >= 0 && l < nff && m < nff;
     double sx, cx, sy, cy;
-    sincos(qx, &sx, &cx);
-    sincos(qy, &sy, &cy);
+    // the flow kinds route the energies symmetrically, k +- q/2: their
+    // rotation is by half the transfer momentum
+    const double hq = is_flow(B.kind) ? 0.5 : 1.0;
+    sincos(hq * qx, &sx, &cx);
+    sincos(hq * qy, &sy, &cy);
     w.trig[g] = QTrig{cx, sx, cy, sy};
     w.meta[g] = make_meta(B.kind, valid ? l : 0, valid ? m : 0, valid, b) | (fp64 ? kMetaFp64 : 0u);
     w.born[g] = uint32_t(round);
@@ -268,8 +271,9 @@ __global__ void k_rule_setup(Work w, int kind, const double* q, const int32_t* r
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r == 0) {
         double sx, cx, sy, cy;
-        sincos(q[0], &sx, &cx);
-        sincos(q[1], &sy, &cy);
+        const double hq = is_flow(kind) ? 0.5 : 1.0;   // flow kinds: k +- q/2
+        sincos(hq * q[0], &sx, &cx);
+        sincos(hq * q[1], &sy, &cy);
         w.trig[0] = QTrig{cx, sx, cy, sy};
         w.meta[0] = make_meta(kind, 0, 0, 1, 0) | kMetaFp64;
     }

@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpaid.so")
 
-PH, PP, MONOMIAL, OVERLAP = 0, 1, 2, 3
+PH, PP, MONOMIAL, OVERLAP, FLOW_PH, FLOW_PP = 0, 1, 2, 3, 4, 5
 FF_SHELL1, FF_SHELL12 = 5, 9
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_POOL, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 CONVERGED, BUDGET, NONFINITE, ROUNDCAP, POOL = 0, 1, 2, 3, 4

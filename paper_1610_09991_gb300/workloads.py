@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-PH, PP, MONOMIAL, OVERLAP = 0, 1, 2, 3
+PH, PP, MONOMIAL, OVERLAP, FLOW_PH, FLOW_PP = 0, 1, 2, 3, 4, 5
 LATTICE = (1.0, -0.25, -1.0)  # (t, t', mu)
 
 
@@ -88,6 +88,19 @@ def config_flow_step(T: float = 0.05, rel_tol: float = 1e-6, nq: int = 24) -> Wo
     bs = [Batch(PH, T, q, lm, rel_tol, 1e-10, 100000),
           Batch(PP, T, q, lm, rel_tol, 1e-10, 100000)]
     return Workload("phpp_T%g_q%dx%d_ff9_%d" % (T, nq, nq, 2 * nq * nq * 81), LATTICE, 9, bs)
+
+
+def config_flow_omega(omega: float = 0.1, rel_tol: float = 1e-6, nq: int = 24) -> Workload:
+    """One flow step of the Omega-regulated scheme: the scale derivatives of the
+    ph and pp bubbles of the flow equations at regulator scale Omega (carried in
+    the batches' T field), l on an nq x nq grid of the full zone, all 81 pairs
+    (2 * 576 * 81 = 93,312 integrals at nq = 24)."""
+    q = q_grid_bz(nq)
+    lm = all_pairs(9)
+    bs = [Batch(FLOW_PH, omega, q, lm, rel_tol, 1e-10, 100000),
+          Batch(FLOW_PP, omega, q, lm, rel_tol, 1e-10, 100000)]
+    return Workload("flow_ph_pp_Omega%g_q%dx%d_ff9_%d" % (omega, nq, nq, 2 * nq * nq * 81),
+                    LATTICE, 9, bs)
 
 
 def config_temperature_sweep(nT: int = 12, nq: int = 16, rel_tol: float = 1e-6) -> Workload:
