@@ -51,6 +51,10 @@ DF_FP32_FLOPS_PER_REGION = 2 * 7774.8 + 29243.1 + 3018.3   # 47,811
 GROUP_FP64_FLOPS_PER_REGION = {4: 2 * 4839 + 663 + 1766, 6: 2 * 8955 + 1285 + 3118,
                                8: 2 * 14367 + 2131 + 4902, 10: 2 * 21075 + 3201 + 7118,
                                12: 2 * 29079 + 4495 + 9766}
+# the same for the Omega-regulated flow kinds (no exponential; same counters)
+GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
+                                    8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
+                                    12: 2 * 21054 + 3487 + 12891}
 
 
 def parse_args():
@@ -59,8 +63,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
+    ap.add_argument("--temperature", type=float, default=None,
+                    help="flow_step: the temperature (default 0.05)")
+    ap.add_argument("--rel-tol", type=float, default=None,
+                    help="flow_step / heldout: the relative tolerance (default 1e-6)")
     ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep",
-                                           "flow_omega"],
+                                           "flow_omega", "heldout"],
                     default="flow_step")
     ap.add_argument("--path", choices=["group", "learned", "plain", "fp32", "learned_fp32"],
                     default="group",
@@ -88,7 +96,7 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, temperature=None, rel_tol=None):
     from paper_1610_09991_gb300 import workloads as W
     if name == "first_shell":
         return W.config_first_shell(), 5
@@ -98,7 +106,18 @@ def workload(name):
         return W.config_temperature_sweep(), 9
     if name == "flow_omega":
         return W.config_flow_omega(), 9
-    return W.config_flow_step(), 9
+    if name == "heldout":
+        return W.config_heldout(rel_tol=rel_tol or 1e-6), 9
+    # the 93,312-integral flow step; --temperature / --rel-tol give the
+    # precision study's variants (T = 0.01 at rel tol 1e-5 and 1e-7)
+    w = W.config_flow_step(T=temperature or 0.05, rel_tol=rel_tol or 1e-6)
+    return w, 9
+
+
+def metric_name(w):
+    """The headline metric, with the workload's relative tolerance."""
+    rt = w.batches[0].rel_tol
+    return METRIC if rt == 1e-6 else METRIC.replace("1e-6", "%g" % rt)
 
 
 def workload_config(w, ff, eval_mode, rule_n=4):
@@ -251,7 +270,7 @@ def run_reference(args):
     import oracle
     from paper_1610_09991_gb300 import workloads as W
     oracle.build()
-    w, ff = workload(args.workload)
+    w, ff = workload(args.workload, args.temperature, args.rel_tol)
     flat = W.flatten(w)
     b0 = w.batches[0]
     per_step = 512
@@ -269,7 +288,7 @@ def run_reference(args):
     total = sum(times)
     value = conv / total
     cores = oracle.max_threads()
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+    line = {"impl": "reference", "metric": metric_name(w), "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -301,7 +320,7 @@ def run_paid(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w, ff = workload(args.workload)
+    w, ff = workload(args.workload, args.temperature, args.rel_tol)
     if args.workload == "flow_omega":
         # the Omega-regulated flow kinds exist in the shared-partition kernel only
         args.path, args.no_compare, args.no_learned = "group", True, True
@@ -431,7 +450,9 @@ def run_paid(args):
     eval_s = agg["eval_ms"] / 1e3
     roof = None
     if group and eval_s > 0:
-        fpr = GROUP_FP64_FLOPS_PER_REGION[ctx.options.rule_n]
+        flow = all(b.kind in (W.FLOW_PH, W.FLOW_PP) for b in w.batches)
+        fpr = (GROUP_FLOW_FP64_FLOPS_PER_REGION if flow
+               else GROUP_FP64_FLOPS_PER_REGION)[ctx.options.rule_n]
         achieved = agg["region_evals"] * fpr / eval_s / 1e12
         pk = peaks.get("fp64_fma_tflops")
         roof = {"bound": "alu", "kernel": "k_eval_group", "achieved": achieved, "peak": pk,
@@ -462,7 +483,8 @@ def run_paid(args):
                 "flops_per_region": DF_FP32_FLOPS_PER_REGION,
                 "share_of_eval": df_s / max(eval_s, 1e-12)}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric_name(w_job), "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
         "dtype": "f64" if args.eval == "fp64" else "f32+f64", "data": "synthetic",

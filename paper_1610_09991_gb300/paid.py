@@ -413,12 +413,15 @@ class Context:
                     rate, ctypes.c_void_p(ws.data_ptr()), nbytes,
                     ctypes.c_void_p(stream.cuda_stream))
             if rc == ERR_POOL and pool_capacity is None and cap < 2 ** 32 - 1:
+                # drop every reference to the old workspace before sizing the next
+                del ws
+                self.release_workspace()
                 free, _ = torch.cuda.mem_get_info(self.device)
-                bigger = min(4 * cap, self.pool_capacity(n, int(0.9 * (free + ws.numel()))),
-                             2 ** 32 - 1)
+                bigger = min(4 * cap, self.pool_capacity(n, int(0.9 * free)), 2 ** 32 - 1)
                 if bigger > cap:
                     cap = bigger
                     continue
+                ws = None
             if rc not in (OK, ERR_TIMEOUT, ERR_POOL):
                 raise PaidError(rc, self.last_error())
             self.last_rc = rc

@@ -141,6 +141,19 @@ def flatten(w: Workload):
                 T=np.concatenate(Ts), batch=np.concatenate(bid), local=np.concatenate(loc))
 
 
+def config_heldout(seed: int = 10000, nq: int = 24, rel_tol: float = 1e-6) -> Workload:
+    """A flow-step batch (ph + pp, all 81 pairs, nq x nq zone grid) at a seeded
+    held-out parameter draw (t', mu, T) of parameter_draws (seeds 10000+ are never
+    used for training)."""
+    tp, mu, T = parameter_draws(1, seed)[0]
+    q = q_grid_bz(nq)
+    lm = all_pairs(9)
+    bs = [Batch(PH, T, q, lm, rel_tol, 1e-10, 100000), Batch(PP, T, q, lm, rel_tol, 1e-10, 100000)]
+    return Workload("heldout%d_tp%.4f_mu%.4f_T%.4g_q%dx%d_ff9_%d" % (seed, tp, mu, T, nq, nq,
+                                                                    2 * nq * nq * 81),
+                    (1.0, tp, mu), 9, bs)
+
+
 def parameter_draws(k: int, seed0: int):
     """k seeded parameter draws (t', mu, T) with t' ~ U[-0.35, 0],
     mu ~ U[-1.4, 0], T log-uniform on [0.005, 1]; draw j uses seed seed0 + j."""
