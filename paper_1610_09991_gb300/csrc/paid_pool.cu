@@ -1,5 +1,7 @@
-// Region pool management: initial partition, per-integral reduction and
-// convergence test, batched selection, 2x2 split and stable compaction.
+// Region pool management: initial partition, per-unit reduction and
+// convergence test, batched selection, 2x2 split and stable compaction, and
+// the device-side loop control.  A unit is one integral, or in group mode one
+// (kind, q) group whose regions carry every pair's values.
 //
 // Paper correspondence (Sec. 4, Listings 1-5):
 //   k_setup        Listing 1: every integral starts from the uniform level-L0
@@ -19,9 +21,17 @@
 //                  regions emit 4 children (level + 1), others are copied;
 //                  positions come from a warp ballot / shuffle prefix so the
 //                  pool stays sorted by integral and stable within it.
+//   k_group_*      group mode: per-pair sums in chunks, the per-pair test, the
+//                  region scores (largest error over the unconverged pairs in
+//                  units of their tolerances) and the selection on them;
+//                  k_copy_vectors moves the kept regions' pair vectors.
+//   k_throttle     pool pressure: integrals split in slot order while the
+//                  growth fits in the pool, the rest wait a round.
+//   k_control      the master's loop control (Listing 5) on the device: next
+//                  round's counts, admission of waiting integrals, stop.
 // One warp owns one integral in reduce/split; sums use a fixed lane order and
-// a xor-butterfly, and the histogram sums are integers, so a run is bitwise
-// reproducible.
+// a xor-butterfly (group mode: fixed chunk and warp order), and the histogram
+// sums are integers, so a run is bitwise reproducible.
 #include <algorithm>
 #include <cmath>
 
