@@ -7,8 +7,9 @@ it, and it imports nothing from the product.
 Every function follows the paper section named in ``oracle.c``:
 the dispersion and form factors (Sec. 2), the Matsubara-summed bubble kernels
 of Eq. chi_ph / chi_pp in temperature form, the nested Clenshaw-Curtis pair
-(Sec. 3) and the greedy adaptive loop of Algorithm 1 with the 4-way split of
-Algorithm 2.
+(Sec. 3), the greedy adaptive loop of Algorithm 1 with the 4-way split of
+Algorithm 2, and Algorithm 2's group form (one heap and one global error sum
+over all (l, m) pairs of a (kind, q), Sec. 4).
 """
 from __future__ import annotations
 
@@ -71,6 +72,9 @@ def _load():
                                                _i, _i64, _i64, _p, _p]
             lib.oracle_integrate_batch.argtypes = [_i, _i, _p, _i, _p, _d, _d, _d, _d,
                                                    _d, _d, _i64, _i, _i, _i, _p, _p, _p, _p]
+            lib.oracle_integrate_group_global.argtypes = [_i, _i, _p, _i, _p, _d, _d, _d, _d,
+                                                          _d, _d, _i64, _i, _i, _i,
+                                                          _p, _p, _p, _p]
             lib.oracle_integrate_list.argtypes = [_i64, _p, _p, _p, _p, _d, _d, _d,
                                                   _d, _d, _i64, _i, _i, _i, _p, _p, _p, _p]
             lib.oracle_integrate_trace.argtypes = [_i, _d, _d, _i, _i, _d, _d, _d, _d,
@@ -182,6 +186,30 @@ def integrate_batch(kind, q, lm, T, lat, rel_tol, abs_tol, max_regions,
                                         _ptr(v), _ptr(e), _ptr(r), _ptr(s))
     if rc != 0:
         raise ValueError("oracle_integrate_batch: invalid argument")
+    return v, e, r, s
+
+
+def integrate_group_global(kind, q, lm, T, lat, rel_tol, abs_tol, max_regions,
+                           rule_n=4, init_level=2, nthreads=0):
+    """Algorithm 2 with the global error of Sec. 4: one group per q row (all
+    of lm's pairs), one heap and one error sum per group; a group is done when
+    sum_c E_c <= max(abs_tol, rel_tol * sum_c |V_c|).  Output index
+    iq * npairs + ip: every pair's own value, error and leaf count, the
+    group's status.  Returns (values, errors, regions, status)."""
+    t, tp, mu = lat
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 2)
+    lm = np.ascontiguousarray(lm, dtype=np.int32).reshape(-1, 2)
+    n = q.shape[0] * lm.shape[0]
+    v = np.zeros(n)
+    e = np.zeros(n)
+    r = np.zeros(n, dtype=np.int64)
+    s = np.zeros(n, dtype=np.int32)
+    rc = _load().oracle_integrate_group_global(kind, q.shape[0], _ptr(q), lm.shape[0], _ptr(lm),
+                                               T, t, tp, mu, rel_tol, abs_tol, int(max_regions),
+                                               rule_n, init_level, nthreads,
+                                               _ptr(v), _ptr(e), _ptr(r), _ptr(s))
+    if rc != 0:
+        raise ValueError("oracle_integrate_group_global: invalid argument")
     return v, e, r, s
 
 

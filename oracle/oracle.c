@@ -21,6 +21,8 @@
  *   - greedy adaptive integration with 2x2 subdivision of the
  *     largest-error sub-domain                       (Algorithm 1, Sec. 3;
  *                                       4-way split as in Algorithm 2)
+ *   - the group form: one heap and one error sum over all (l, m) pairs of
+ *     a (kind, q)                         (Algorithm 2, global error, Sec. 4)
  *   - per-integral independence: integrals run in parallel over OpenMP
  *     threads, one integral per task (Sec. 4 distributes independent work
  *     in the same way).
@@ -33,6 +35,8 @@
  *   full integrals   dense periodic trapezoid and Gauss-Legendre brute force,
  *                    C4v and q -> -q symmetries, nesting identity, dn/dmu
  *   adaptive driver  a hand-stepped greedy on tiny budgets
+ *   group driver     one pair = Algorithm 1 exactly; a hand-stepped group
+ *                    greedy on tiny budgets; brute-force values per pair
  */
 #include <math.h>
 #include <stdint.h>
@@ -460,6 +464,172 @@ int oracle_integrate_batch(int kind, int nq, const double* q, int npairs, const 
         int st = adaptive_one(&p, &r, init_level, rel_tol, abs_tol, max_regions,
                               &values[i], &errors[i], &regions[i], NULL, 0, NULL);
         status[i] = st < 0 ? ORC_NONFINITE : st;
+    }
+    (void)nthreads;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Algorithm 2 (Sec. 4) for one group: all (l, m) pairs of one (kind, q).
+ * Every pair keeps its own partition (a uniform level-L0 grid at the start,
+ * Listing 1), but the tasks of all pairs sit in one max-heap and one error
+ * sum decides when the group is done (the global error of Sec. 4: the sum of
+ * the pairs' absolute errors, without the coupling norms):
+ *   while E_g = sum_c E_c > max(abs_tol, rel_tol sum_c |V_c|):
+ *       take the task (pair, region) with the largest err over the group,
+ *       split it into 4, evaluate the children for that pair,
+ *       update that pair's E_c, V_c, push the children.
+ * With rel_tol = 0 the test is the paper's absolute E_g < eps.  A split is
+ * made only while the popped pair stays within max_regions leaves and the
+ * region is above the deepest level; otherwise the group stops with BUDGET.
+ * Ties in the heap: larger err, then smaller pair index, level, ix, iy.
+ * Sums are recomputed exactly from the leaves every 1024 splits and at the
+ * end.  Every pair of the group gets the group's status.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    orc_task t;
+    int c;              /* pair index within the group */
+} orc_gtask;
+
+static int gtask_before(const orc_gtask* a, const orc_gtask* b)
+{
+    if (a->t.err != b->t.err) return a->t.err > b->t.err;
+    if (a->c != b->c) return a->c < b->c;
+    return task_before(&a->t, &b->t);
+}
+
+static void gheap_push(orc_gtask* h, int64_t* n, orc_gtask t)
+{
+    int64_t i = (*n)++;
+    h[i] = t;
+    while (i > 0) {
+        int64_t par = (i - 1) / 2;
+        if (!gtask_before(&h[i], &h[par])) break;
+        orc_gtask tmp = h[i]; h[i] = h[par]; h[par] = tmp;
+        i = par;
+    }
+}
+
+static orc_gtask gheap_pop(orc_gtask* h, int64_t* n)
+{
+    orc_gtask top = h[0];
+    h[0] = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t a = 2 * i + 1, b = 2 * i + 2, best = i;
+        if (a < *n && gtask_before(&h[a], &h[best])) best = a;
+        if (b < *n && gtask_before(&h[b], &h[best])) best = b;
+        if (best == i) break;
+        orc_gtask tmp = h[i]; h[i] = h[best]; h[best] = tmp;
+        i = best;
+    }
+    return top;
+}
+
+static void group_exact_sums(const orc_gtask* h, int64_t n, int P, double* V, double* E)
+{
+    for (int c = 0; c < P; ++c) { V[c] = 0.0; E[c] = 0.0; }
+    for (int64_t i = 0; i < n; ++i) { V[h[i].c] += h[i].t.val2N; E[h[i].c] += h[i].t.err; }
+}
+
+static int adaptive_group(const orc_integral* pairs, int P, const orc_rule* r, int L0,
+                          double rel_tol, double abs_tol, int64_t max_regions,
+                          double* V, double* E, int64_t* leaves)
+{
+    int64_t n0 = (int64_t)1 << (2 * L0);
+    int64_t hcap = (int64_t)P * n0 * 4 + 4;   /* grows by doubling */
+    orc_gtask* heap = (orc_gtask*)malloc((size_t)hcap * sizeof(orc_gtask));
+    if (!heap) return -1;
+    int64_t n = 0;
+    int64_t side = (int64_t)1 << L0;
+    for (int c = 0; c < P; ++c) {
+        leaves[c] = n0;
+        for (int64_t ix = 0; ix < side; ++ix)
+            for (int64_t iy = 0; iy < side; ++iy) {
+                orc_gtask g = {make_task(&pairs[c], r, L0, ix, iy), c};
+                gheap_push(heap, &n, g);
+            }
+    }
+    group_exact_sums(heap, n, P, V, E);
+    int status = ORC_CONVERGED;
+    int64_t splits = 0;
+    for (;;) {
+        double Eg = 0.0, Vabs = 0.0;
+        int finite = 1;
+        for (int c = 0; c < P; ++c) {
+            if (!isfinite(V[c]) || !isfinite(E[c])) finite = 0;
+            Eg += E[c];
+            Vabs += fabs(V[c]);
+        }
+        if (!finite) { status = ORC_NONFINITE; break; }
+        if (Eg <= fmax(abs_tol, rel_tol * Vabs)) { status = ORC_CONVERGED; break; }
+        const orc_gtask* top = &heap[0];
+        if (leaves[top->c] + 3 > max_regions || top->t.L >= ORC_MAX_LEVEL) {
+            status = ORC_BUDGET;
+            break;
+        }
+        if (n + 4 > hcap) {
+            orc_gtask* h2 = (orc_gtask*)realloc(heap, (size_t)(2 * hcap) * sizeof(orc_gtask));
+            if (!h2) { free(heap); return -1; }
+            heap = h2;
+            hcap *= 2;
+        }
+        orc_gtask par = gheap_pop(heap, &n);
+        int c = par.c;
+        E[c] -= par.t.err;
+        V[c] -= par.t.val2N;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                orc_gtask ch = {make_task(&pairs[c], r, par.t.L + 1, 2 * par.t.ix + a,
+                                          2 * par.t.iy + b), c};
+                E[c] += ch.t.err;
+                V[c] += ch.t.val2N;
+                gheap_push(heap, &n, ch);
+            }
+        leaves[c] += 3;
+        if (++splits % 1024 == 0) group_exact_sums(heap, n, P, V, E);
+    }
+    group_exact_sums(heap, n, P, V, E);
+    for (int c = 0; c < P; ++c)
+        if (!isfinite(V[c]) || !isfinite(E[c])) status = ORC_NONFINITE;
+    free(heap);
+    return status;
+}
+
+/* Batch entry point of Algorithm 2: one group per q row, its pairs the
+ * batch's (l, m) list; outputs in the batch order idx = iq * npairs + ip
+ * (every pair's own V_c, E_c and leaf count; the group's status).  Groups run
+ * in parallel over `nthreads` OpenMP threads.  Returns 0, or -1 for an
+ * invalid argument. */
+int oracle_integrate_group_global(int kind, int nq, const double* q, int npairs, const int32_t* lm,
+                                  double T, double t, double tp, double mu,
+                                  double rel_tol, double abs_tol, int64_t max_regions,
+                                  int rule_n, int init_level, int nthreads,
+                                  double* values, double* errors, int64_t* regions,
+                                  int32_t* status)
+{
+    orc_rule r;
+    if (make_rule(rule_n, &r)) return -1;
+    if (nq < 0 || npairs < 1 || init_level < 0 || init_level > 12) return -1;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int iq = 0; iq < nq; ++iq) {
+        orc_integral* pairs = (orc_integral*)malloc((size_t)npairs * sizeof(orc_integral));
+        int st = -1;
+        int64_t o = (int64_t)iq * npairs;
+        if (pairs) {
+            for (int c = 0; c < npairs; ++c) {
+                orc_integral p = {kind, q[2 * iq], q[2 * iq + 1], lm[2 * c], lm[2 * c + 1],
+                                  T, t, tp, mu};
+                pairs[c] = p;
+            }
+            st = adaptive_group(pairs, npairs, &r, init_level, rel_tol, abs_tol, max_regions,
+                                &values[o], &errors[o], &regions[o]);
+            free(pairs);
+        }
+        for (int c = 0; c < npairs; ++c) status[o + c] = st < 0 ? ORC_NONFINITE : st;
     }
     (void)nthreads;
     return 0;
