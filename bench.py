@@ -230,6 +230,38 @@ def cpu_baseline(w, sample, seed=1234, rule_n=4):
             "seconds": dt, "converged": conv, "regions_mean": float(r.mean())}, (idx, v, s)
 
 
+def group_global_check(w, gv, gs, rule_n, rows_per_batch=4, seed=2024):
+    """The global-error group mode against Algorithm 2 of the oracle on a few
+    sampled (kind, q) groups of every batch: per group the summed deviation
+    over its pairs in units of the oracle's group tolerance (the parity bound
+    is 2)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    devs, fails, groups, off = [], 0, 0, 0
+    t0 = time.perf_counter()
+    for b in w.batches:
+        P = b.lm.shape[0]
+        v = gv[off:off + b.n].reshape(-1, P)
+        st = gs[off:off + b.n].reshape(-1, P)
+        off += b.n
+        rows = np.sort(rng.choice(b.q.shape[0], min(rows_per_batch, b.q.shape[0]), replace=False))
+        vo, eo, ro, so = oracle.integrate_group_global(b.kind, b.q[rows], b.lm, b.T, w.lattice,
+                                                       b.rel_tol, b.abs_tol, b.max_regions,
+                                                       rule_n=rule_n)
+        vo, so = vo.reshape(-1, P), so.reshape(-1, P)
+        tol = np.maximum(b.abs_tol, b.rel_tol * np.abs(vo).sum(1))
+        d = np.abs(v[rows] - vo).sum(1) / tol
+        ok = (st[rows] == 0).all(1) & (so == 0).all(1)
+        devs.extend(d[ok].tolist())
+        fails += int((d[ok] > 2.0 + 1e-12 / tol[ok]).sum()) + int((~ok).sum())
+        groups += len(rows)
+    return {"against": "FP64 oracle, Algorithm 2 with the global error, %d sampled groups "
+                       "(rule N = %d, %.1f s)" % (groups, rule_n, time.perf_counter() - t0),
+            "max_dev_over_group_tol": float(max(devs)) if devs else None,
+            "parity_failures": fails}
+
+
 def accuracy(v, s, vo, so, rel, ab, against, ident=None, lattice=None):
     """Error statement: |v - v_ref| in units of the requested tolerance
     max(rel |v_ref|, abs) on integrals both sides converged.  A pair above 2
@@ -563,6 +595,57 @@ def run_paid(args):
         del gouts
         cg.close()
         torch.cuda.empty_cache()
+    glob = None
+    if args.path == "group" and not args.no_compare:
+        # the paper's own stopping test (Algorithm 2, global error): one error
+        # sum and one tolerance per (kind, q) group, on the same shared
+        # partitions, rule and grid
+        cgl = P.Context(*w.lattice, ffset=ff, device=local, group_mode=2,
+                        cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks,
+                        rule_n=ctx.options.rule_n)
+
+        def glstep():
+            flush.fill_(1)
+            return cgl.integrate_multi(dbs, stream=stream)
+
+        for _ in range(max(1, args.warmup)):
+            glstep()
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hsteps = min(args.steps, 5)
+        h0.record(stream)
+        houts = [glstep() for _ in range(hsteps)]
+        h1.record(stream)
+        torch.cuda.synchronize()
+        th = h0.elapsed_time(h1) / 1e3
+        hst = cgl.last_stats()
+        hconv = sum(int((torch.cat([o.status for o in ho]) == 0).sum()) for ho in houts)
+        gv = torch.cat([o.values for o in houts[-1]]).cpu().numpy()
+        ge = torch.cat([o.errors for o in houts[-1]]).cpu().numpy()
+        gs = torch.cat([o.status for o in houts[-1]]).cpu().numpy()
+        met, ngr, off, agree = 0, 0, 0, 0.0
+        for b in w.batches:
+            Pn = b.lm.shape[0]
+            vv, ee = gv[off:off + b.n].reshape(-1, Pn), ge[off:off + b.n].reshape(-1, Pn)
+            vp = vals[off:off + b.n].reshape(-1, Pn)
+            off += b.n
+            tolg = np.maximum(b.abs_tol, b.rel_tol * np.abs(vv).sum(1))
+            met += int((ee.sum(1) <= tolg * (1 + 1e-6)).sum())
+            ngr += vv.shape[0]
+            agree = max(agree, float((np.abs(vv - vp).sum(1) / tolg).max()))
+        hval = hconv * world / th
+        glob = (gv, gs)
+        line["group_global"] = {
+            "path": "group mode 2: shared partition per (kind, q), one error sum and one "
+                    "tolerance per group (Algorithm 2's global error, rel_tol on sum |V_c|)",
+            "value": hval, "unit": UNIT, "ms_per_step": 1e3 * th / hsteps, "steps": hsteps,
+            "region_evals": hst["region_evals"], "rounds": hst["rounds"],
+            "speedup_vs_per_pair_group": hval / value,
+            "groups_meeting_group_tol": met, "groups": ngr,
+            "max_dev_from_per_pair_results_over_group_tol": agree}
+        del houts
+        cgl.close()
+        torch.cuda.empty_cache()
     if args.path not in ("plain",) and not args.no_compare:
         # the plain FP64 GPU path (one partition per integral) on the same batch:
         # with its own autotuned rule and cover, and with the library defaults
@@ -655,6 +738,9 @@ def run_paid(args):
         line["accuracy"] = accuracy(vals[idx], stats[idx], vo, so, w.batches[0].rel_tol,
                                     w.batches[0].abs_tol, "FP64 oracle, the CPU-baseline sample",
                                     ident_s, w.lattice)
+        if glob is not None:
+            line["group_global"]["accuracy"] = group_global_check(w, glob[0], glob[1],
+                                                                  ctx.options.rule_n)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -121,6 +121,12 @@ typedef struct {
                                E <= max(abs_tol, rel_tol |V|) with E its own error sum; the
                                region count reported is the group's.  max_regions bounds the
                                group's regions and pool_capacity counts them (about 2 KB each).
+                               2: the same shared partition with the global error of
+                               Algorithm 2 (Sec. 4): one error sum and one tolerance per group,
+                               done when sum_c E_c <= max(abs_tol, rel_tol sum_c |V_c|) over the
+                               group's valid pairs (rel_tol = 0 gives the paper's absolute
+                               eps = abs_tol); a region's score is its share of the sum, and
+                               every pair of a finished group takes the group's status.
                                Default 0 (one partition per integral) */
     int eval_blocks;        /* group_mode: grid of the region-evaluation kernel (it strides over
                                the eval list); 0 = 152 x 32 blocks.  Default 0 */

@@ -225,7 +225,7 @@ int check_options(const paid_options& o, std::string& why)
     if (o.pool_capacity < 0) { why = "pool_capacity must be >= 0"; return PAID_ERR_ARG; }
     if (o.timing != 0 && o.timing != 1) { why = "timing must be 0 or 1"; return PAID_ERR_ARG; }
     if (o.device_loop != 0 && o.device_loop != 1) { why = "device_loop must be 0 or 1"; return PAID_ERR_ARG; }
-    if (o.group_mode != 0 && o.group_mode != 1) { why = "group_mode must be 0 or 1"; return PAID_ERR_ARG; }
+    if (o.group_mode < 0 || o.group_mode > 2) { why = "group_mode must be 0, 1 or 2"; return PAID_ERR_ARG; }
     if (o.group_mode && o.eval_fp32) { why = "group_mode evaluates in FP64 (eval_fp32 = 0)"; return PAID_ERR_ARG; }
     if (o.eval_blocks < 0) { why = "eval_blocks must be >= 0"; return PAID_ERR_ARG; }
     return PAID_OK;
@@ -364,7 +364,7 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
         const paid_batch& b = batches[i];
         if (b.kind < PAID_PH || b.kind > PAID_FLOW_PP) return fail(ctx, PAID_ERR_ARG, "bad kind");
         if (!group && (b.kind == PAID_FLOW_PH || b.kind == PAID_FLOW_PP))
-            return fail(ctx, PAID_ERR_ARG, "the flow kinds take group_mode = 1");
+            return fail(ctx, PAID_ERR_ARG, "the flow kinds take group_mode = 1 or 2");
         if ((b.kind == PAID_FLOW_PH || b.kind == PAID_FLOW_PP) && !(b.T > 0.0))
             return fail(ctx, PAID_ERR_ARG, "flow kinds: Omega (the T field) must be > 0");
         if (b.nq < 0 || b.npairs < 0) return fail(ctx, PAID_ERR_ARG, "nq, npairs must be >= 0");
@@ -413,6 +413,7 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
     if (cap < n * n0) return fail(ctx, PAID_ERR_OOM, "workspace too small for the initial partition");
     const Layout L = layout(n, cap, group);
     w = make_work(static_cast<char*>(workspace), L, n, cap, int(hb.size()), group, ctx->nff);
+    w.gglobal = group && ctx->opt.group_mode == 2;
     cudaError_t e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
@@ -1111,6 +1112,7 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     const Layout L = layout(units, cap, group);
     char* base = static_cast<char*>(scratch);
     Work w = make_work(base, L, units, cap, 1, group, ctx->nff);
+    w.gglobal = group && o.group_mode == 2;
 
     // The scratch keeps whatever the previous call left in it.  Every array
     // is written before it is read within a call; the totals block is cleared

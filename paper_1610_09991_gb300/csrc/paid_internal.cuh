@@ -192,6 +192,7 @@ struct Work {
     int* gstate;
     int vstride;
     int nff;
+    int gglobal;               // group mode 2: one error sum and one tolerance per group
 };
 
 // ---- host-side launch wrappers (defined in the .cu files) -----------------

@@ -670,6 +670,13 @@ cudaError_t launch_reduce_test(const Work& w, int64_t hint_active, int max_round
 // error.  Finished groups write every pair's value, error, region count and
 // status (CONVERGED for the pairs that meet their tolerance).
 //
+// With w.gglobal (group mode 2, the global error of Algorithm 2) the group has
+// one error sum and one tolerance: E_g = sum_c E_c over the valid pairs,
+// tol_g = max(abs_tol, rel_tol sum_c |V_c|), done when E_g <= tol_g; the
+// score of a region is s_r = sum_c err_c,r / tol_g (its share of E_g), so the
+// same selection leaves at most cover * tol_g of E_g unsplit, and every pair
+// of a finished group takes the group's status.
+//
 // Four launches, so that a deep group does not keep one block streaming its
 // regions alone: each group's segment is cut into kGroupSplit chunks of
 // consecutive regions, and
@@ -734,13 +741,14 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sums(Work w)
 }
 
 // Outputs of a finished group: per pair value, error, region count, status.
+// gconv < 0: each pair's own test decides CONVERGED; else the group's verdict.
 __device__ void group_outputs(const Work& w, const DevBatch& B, uint32_t g, uint32_t cnt, int c,
-                              double V, double E, int st)
+                              double V, double E, int st, int gconv)
 {
     const int l = B.lm[2 * c], m = B.lm[2 * c + 1];
     const bool valid = l >= 0 && m >= 0 && l < w.nff && m < w.nff;
     const bool finite = isfinite(V) && isfinite(E);
-    const bool conv = E <= fmax(B.abs_tol, B.rel_tol * fabs(V));
+    const bool conv = gconv >= 0 ? gconv != 0 : E <= fmax(B.abs_tol, B.rel_tol * fabs(V));
     const int64_t o = (int64_t(g) - B.first) * B.npairs + c;
     B.values[o] = valid ? V : NAN;
     B.errors[o] = valid ? E : NAN;
@@ -771,8 +779,29 @@ k_group_test(Work w, int max_rounds, int force_status)
         const int l = B.lm[2 * tid], m = B.lm[2 * tid + 1];
         valid = l >= 0 && m >= 0 && l < w.nff && m < w.nff;
         finite = isfinite(V) && isfinite(E);
-        const double tol = fmax(B.abs_tol, B.rel_tol * fabs(V));
+    }
+    double tol = fmax(B.abs_tol, B.rel_tol * fabs(V));
+    if (w.gglobal) {
+        // one sum in pair order (deterministic), one tolerance for the group
+        __shared__ double sE[kGroupPairs], sV[kGroupPairs], sg[2];
+        if (tid < P) {
+            sE[tid] = valid && finite ? E : 0.0;
+            sV[tid] = valid && finite ? fabs(V) : 0.0;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int c = 0; c < P; ++c) { a += sE[c]; b += sV[c]; }
+            sg[0] = a;
+            sg[1] = fmax(B.abs_tol, B.rel_tol * b);
+        }
+        __syncthreads();
+        tol = sg[1];
+        conv = sg[0] <= tol;
+    } else {
         conv = E <= tol;
+    }
+    if (tid < P) {
         w.gtol[size_t(s) * kGroupPairs + tid] =
             (valid && finite && !conv) ? 1.0 / fmax(tol, 1e-300) : 0.0;
         w.gsum[size_t(s) * 2 * kGroupPairs + tid] = V;
@@ -789,7 +818,7 @@ k_group_test(Work w, int max_rounds, int force_status)
     else if (allowed <= 0) st = BUDGET;
     if (tid == 0) w.gstate[s] = st;
     if (st == RUNNING) return;
-    if (tid < P) group_outputs(w, B, g, cnt, tid, V, E, st);
+    if (tid < P) group_outputs(w, B, g, cnt, tid, V, E, st, w.gglobal ? int(conv) : -1);
     if (tid == 0) {
         if (st == ROUNDCAP && force_status < 0) atomicAdd(&w.totals->roundcap, 1ull);
         w.cnt_new[s] = 0;
@@ -823,13 +852,23 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_scores(Work w)
     for (uint32_t j = j0 + wid; j < j1; j += kGroupWarps) {
         const size_t r = size_t(base + j) * S;
         float sc = 0.0f;
+        if (w.gglobal) {
 #pragma unroll
-        for (int c3 = 0; c3 < 3; ++c3) {
-            const int c = lane + 32 * c3;
-            if (c < P) sc = fmaxf(sc, verr[r + c] * itol[c]);
+            for (int c3 = 0; c3 < 3; ++c3) {
+                const int c = lane + 32 * c3;
+                if (c < P) sc += verr[r + c] * itol[c];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(kFull, sc, o);
+        } else {
+#pragma unroll
+            for (int c3 = 0; c3 < 3; ++c3) {
+                const int c = lane + 32 * c3;
+                if (c < P) sc = fmaxf(sc, verr[r + c] * itol[c]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sc = fmaxf(sc, __shfl_xor_sync(kFull, sc, o));
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sc = fmaxf(sc, __shfl_xor_sync(kFull, sc, o));
         if (lane == 0) {
             const double scd = double(fminf(sc, 1.0e30f));   // finite even for a zero tolerance
             w.err[cur][base + j] = scd;
@@ -867,7 +906,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_select(Work w, doubl
     if (!(Smax > 0.0)) {   // nothing left to split
         if (tid < B.npairs)
             group_outputs(w, B, g, cnt, tid, w.gsum[size_t(s) * 2 * kGroupPairs + tid],
-                          w.gsum[size_t(s) * 2 * kGroupPairs + kGroupPairs + tid], BUDGET);
+                          w.gsum[size_t(s) * 2 * kGroupPairs + kGroupPairs + tid], BUDGET,
+                          w.gglobal ? 0 : -1);
         if (tid == 0) { w.cnt_new[s] = 0; w.cnt_eval[s] = 0; }
         return;
     }

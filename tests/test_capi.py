@@ -55,6 +55,10 @@ def test_host_side_calls_without_gpu(lib):
     assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
     bad.group_mode, bad.eval_fp32 = 1, 1   # group mode is FP64
     assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
+    bad.group_mode = 2                     # the global-error group mode is FP64 too
+    assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
+    bad.group_mode, bad.eval_fp32 = 3, 0   # modes are 0, 1, 2
+    assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
     assert lib.paid_integrate_multi(None, None, 0, None, 0, None) == paid.ERR_ARG
 
 
