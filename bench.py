@@ -87,6 +87,8 @@ def parse_args():
                     help="skip the extra timed steps of the learned_fp32 path")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the timed FP64 comparison step of an FP32 run")
+    ap.add_argument("--no-global", action="store_true",
+                    help="group path: skip the global-error group mode (group_mode = 2) block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-device-loop", action="store_true",
@@ -596,7 +598,7 @@ def run_paid(args):
         cg.close()
         torch.cuda.empty_cache()
     glob = None
-    if args.path == "group" and not args.no_compare:
+    if args.path == "group" and not args.no_global:
         # the paper's own stopping test (Algorithm 2, global error): one error
         # sum and one tolerance per (kind, q) group, on the same shared
         # partitions, rule and grid

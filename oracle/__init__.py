@@ -103,7 +103,12 @@ def trapezoid(kind, q, l, m, T, lat, M, nthreads=0):
 
 def brute_force(kind, q, l, m, T, lat, M0=1024, Mmax=8192, tol=1e-13):
     """Converged dense trapezoid: M doubled from M0 until two successive values
-    agree within tol (absolute).  Returns (value, M) or (nan, Mmax)."""
+    agree within tol (absolute).  Returns (value, M) or (nan, Mmax).
+
+    The flow kinds go to brute_force_h4: their kernel is not analytic on the
+    Fermi surface and the trapezoid converges like h^4 there, never to 1e-13."""
+    if kind in (FLOW_PH, FLOW_PP):
+        return brute_force_h4(kind, q, l, m, T, lat)
     prev = trapezoid(kind, q, l, m, T, lat, M0)
     M = M0
     while M < Mmax:
@@ -112,6 +117,25 @@ def brute_force(kind, q, l, m, T, lat, M0=1024, Mmax=8192, tol=1e-13):
         if abs(cur - prev) <= tol:
             return cur, M
         prev = cur
+    return float("nan"), M
+
+
+def brute_force_h4(kind, q, l, m, T, lat, M0=1024, Mmax=16384, tol=1e-11):
+    """Dense trapezoid for an integrand whose fourth derivative jumps on a curve
+    (the Omega-regulated flow kernels: |e| enters H(e), Sec. 2): the error
+    falls like h^4, so every doubling of M is followed by one Richardson step
+    R(M) = T(M) + (T(M) - T(M/2)) / 15, and two successive R must agree within
+    tol.  Returns (value, M) or (nan, Mmax)."""
+    prev = trapezoid(kind, q, l, m, T, lat, M0)
+    prevR = None
+    M = M0
+    while M < Mmax:
+        M *= 2
+        cur = trapezoid(kind, q, l, m, T, lat, M)
+        R = cur + (cur - prev) / 15.0
+        if prevR is not None and abs(R - prevR) <= tol:
+            return R, M
+        prev, prevR = cur, R
     return float("nan"), M
 
 

@@ -98,6 +98,18 @@ def test_flow_integrals_against_trapezoid(kind):
     assert np.all(np.abs(v.reshape(2, -1)[:, 4]) < 1e-11)
 
 
+def test_flow_brute_force_extrapolates():
+    # the decider the bench uses for the flow kinds: Richardson-extrapolated
+    # trapezoid against a tight adaptive value; the plain doubling test of
+    # brute_force would never reach 1e-13 on these integrands
+    q = np.array([(0.9, -0.4)])
+    v, e, r, s = oracle.integrate_batch(oracle.FLOW_PH, q, np.array([(2, 5)]), 0.2, LAT,
+                                        1e-10, 1e-13, 1000000)
+    assert s[0] == oracle.CONVERGED
+    bf, M = oracle.brute_force(oracle.FLOW_PH, q[0], 2, 5, 0.2, LAT)
+    assert M <= 16384 and abs(bf - v[0]) <= e[0] + 2e-11
+
+
 def test_flow_routing_symmetries():
     # f_m(k) f_n(k): I_mn = I_nm; l -> -l swaps the two energies: I(-l) = I(l)
     lm = W.all_pairs(9)
