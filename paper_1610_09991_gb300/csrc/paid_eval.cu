@@ -973,10 +973,11 @@ cudaError_t launch_check_math(int which, int64_t n, const double* x, const doubl
 //   X_ac = g_a(kx) g_c(kx'),   Y_bd = g_b(ky) g_d(ky'),
 // and the rule applied to every pair needs only the 81 moments
 //   M[ac][bd] = sum_i wx_i X_ac(x_i) R_i[bd],   R_i[bd] = sum_j wy_j F_ij Y_bd(y_j)
-// and their coarse-rule counterparts: the kernel F once per node, 2 x 729
-// FMA (fine) + 630 (coarse) for the moments, at most 4 terms per pair.
+// and their coarse-rule counterparts: the kernel F once per node, 81 NF FMA
+// (fine) + 81 (N+1) (coarse) for the moments, at most 4 terms per pair.
 // Block: NF = 2N+1 threads per region (thread i owns fine row i, and column
-// i for the shared column data), kGroupRegions<N> regions per block.
+// i for the shared column data, and moment cells i, i + NF, ...),
+// GroupShape<N>::R regions per block.
 template <int N> struct GroupShape;
 template <> struct GroupShape<4> { static constexpr int R = 14; };   // 126 threads
 template <> struct GroupShape<6> { static constexpr int R = 9; };    // 117 threads
@@ -1108,30 +1109,31 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                     for (int k = 0; k < 9; ++k) rc[k] = fma(wc, S.Y[rho][j][k], rc[k]);
                 }
             }
+            // the row's own rule weight (fine, and coarse on the even rows)
+            // goes into its sums, so the moments below are plain dot products
+            const double wr = c_wf[v][i];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = rf[k];
-            if ((i & 1) == 0)
+            for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = wr * rf[k];
+            if ((i & 1) == 0) {
+                const double wrc = c_wc[v][i >> 1];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) S.Rc[rho][i >> 1][k] = rc[k];
+                for (int k = 0; k < 9; ++k) S.Rc[rho][i >> 1][k] = wrc * rc[k];
+            }
         }
         __syncthreads();
-        if (live && i < 9) {   // thread i: moments of ac = i
-            double mf[9], mc[9];
+        if (live) {
+            // moments M[ac][bd]: the 81 (ac, bd) cells dealt over the region's
+            // NF threads (all of them busy, rather than one thread per ac)
+            for (int u = i; u < 81; u += NF) {
+                const int ac = u / 9, bd = u - 9 * (u / 9);
+                double mf = 0.0, mc = 0.0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) { mf[k] = 0.0; mc[k] = 0.0; }
+                for (int r = 0; r < NF; ++r) mf = fma(S.X[rho][r][ac], S.Rf[rho][r][bd], mf);
 #pragma unroll
-            for (int r = 0; r < NF; ++r) {
-                const double xf = c_wf[v][r] * S.X[rho][r][i];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) mf[k] = fma(xf, S.Rf[rho][r][k], mf[k]);
-                if ((r & 1) == 0) {
-                    const double xc = c_wc[v][r >> 1] * S.X[rho][r][i];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) mc[k] = fma(xc, S.Rc[rho][r >> 1][k], mc[k]);
-                }
+                for (int r = 0; r <= N; ++r) mc = fma(S.X[rho][2 * r][ac], S.Rc[rho][r][bd], mc);
+                S.Mf[rho][ac][bd] = mf;
+                S.Mc[rho][ac][bd] = mc;
             }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) { S.Mf[rho][i][k] = mf[k]; S.Mc[rho][i][k] = mc[k]; }
         }
         __syncthreads();
         if (live) {
