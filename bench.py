@@ -47,10 +47,18 @@ DF_FP32_FLOPS_PER_REGION = 2 * 7774.8 + 29243.1 + 3018.3   # 47,811
 # FP64 flops per region of the shared-partition kernel (k_eval_group, 81 pairs)
 # by rule order N: DFMA counted as 2, DADD / DMUL as 1, from the ncu
 # instruction counters of one launch over 10^5 regions per N divided by the
-# regions (profiles/k_eval_group_flow_step_q4.md).
-GROUP_FP64_FLOPS_PER_REGION = {4: 2 * 4839 + 663 + 1766, 6: 2 * 8955 + 1285 + 3118,
-                               8: 2 * 14367 + 2131 + 4902, 10: 2 * 21075 + 3201 + 7118,
-                               12: 2 * 29079 + 4495 + 9766}
+# regions (profiles/k_eval_group_flow_step_q4.md), taken when every node still
+# evaluated the near-degenerate series of the kernel F.  That series (d^2,
+# four FMA, two products: 11 flops per node) now runs only in warps that hold a
+# node with |x1 - x2| <= 1/16, so the figure used is the count minus
+# 11 (2N+1)^2: a lower bound on the work done, which keeps the roofline
+# fraction conservative.
+GROUP_NEAR_FLOPS_PER_NODE = 2 * 4 + 3
+GROUP_FP64_FLOPS_PER_REGION = {
+    n: f - GROUP_NEAR_FLOPS_PER_NODE * (2 * n + 1) ** 2
+    for n, f in {4: 2 * 4839 + 663 + 1766, 6: 2 * 8955 + 1285 + 3118,
+                 8: 2 * 14367 + 2131 + 4902, 10: 2 * 21075 + 3201 + 7118,
+                 12: 2 * 29079 + 4495 + 9766}.items()}
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,

@@ -912,11 +912,19 @@ __device__ __forceinline__ double bubble_F2T(double x1, double x2, const double*
     const bool same = neg1 == (x2 < 0.0);
     double far = same ? (u2 - u1) : fma(-u1, u2, 1.0);
     far = neg1 ? -far : far;
-    const double d2 = d * d;
-    const double sinhc2 = fma(d2, fma(d2, fma(d2, fma(d2, 2.0 / 362880.0, 2.0 / 5040.0),
-                                               2.0 / 120.0), 2.0 / 6.0), 2.0);
-    const double num = near ? (v1 * v2) * sinhc2 : far;
-    const double den = near ? p : p * d;
+    double num = far, den = p * d;
+    // the near branch is needed only in the thin band |e(k) - e(k')| <= 2T/16
+    // (all of the zone only near q = 0): a warp none of whose lanes is near
+    // skips the series
+    if (__any_sync(__activemask(), near)) {
+        const double d2 = d * d;
+        const double sinhc2 = fma(d2, fma(d2, fma(d2, fma(d2, 2.0 / 362880.0, 2.0 / 5040.0),
+                                                   2.0 / 120.0), 2.0 / 6.0), 2.0);
+        if (near) {
+            num = (v1 * v2) * sinhc2;
+            den = p;
+        }
+    }
     return div_nr(num, den);
 }
 
