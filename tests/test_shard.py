@@ -66,7 +66,7 @@ def _free_port():
     return port
 
 
-def _rank(rank, world, port, out):
+def _rank(rank, world, port, out, group_global=False):
     import torch.distributed as dist
     import oracle
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -76,10 +76,10 @@ def _rank(rank, world, port, out):
         bs = _batches()
         shares = S.plan(bs, world)
         local = []
+        run = oracle.integrate_group_global if group_global else oracle.integrate_batch
         for b, sub in S.local_batches(bs, shares[rank]):
-            local.append(oracle.integrate_batch(sub.kind, sub.q, sub.lm, sub.T, W.LATTICE,
-                                                sub.rel_tol, sub.abs_tol, sub.max_regions,
-                                                nthreads=1))
+            local.append(run(sub.kind, sub.q, sub.lm, sub.T, W.LATTICE, sub.rel_tol,
+                             sub.abs_tol, sub.max_regions, nthreads=1))
         full = S.gather(bs, shares, local, rank, world)
         if rank == 0:
             np.savez(out, *[a for r in full for a in r])
@@ -87,17 +87,21 @@ def _rank(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_match_one_process(tmp_path):
+@pytest.mark.parametrize("group_global", [False, True])
+def test_two_gloo_ranks_match_one_process(tmp_path, group_global):
+    # per-integral Algorithm 1, and Algorithm 2's group error: a shard is a set
+    # of q rows, each row is a whole (kind, q) group, so no group sum crosses
+    # ranks and the gathered results equal one process's bit for bit
     import torch.multiprocessing as mp
     import oracle
     out = str(tmp_path / "gathered.npz")
-    mp.start_processes(_rank, args=(2, _free_port(), out), nprocs=2, join=True,
+    mp.start_processes(_rank, args=(2, _free_port(), out, group_global), nprocs=2, join=True,
                        start_method="spawn")
     got = np.load(out)
     arrays = [got["arr_%d" % i] for i in range(len(got.files))]
     bs = _batches()
+    run = oracle.integrate_group_global if group_global else oracle.integrate_batch
     for b, bt in enumerate(bs):
-        ref = oracle.integrate_batch(bt.kind, bt.q, bt.lm, bt.T, W.LATTICE, bt.rel_tol,
-                                     bt.abs_tol, bt.max_regions)
+        ref = run(bt.kind, bt.q, bt.lm, bt.T, W.LATTICE, bt.rel_tol, bt.abs_tol, bt.max_regions)
         for j in range(4):
             assert np.array_equal(arrays[4 * b + j], ref[j]), (b, j)
