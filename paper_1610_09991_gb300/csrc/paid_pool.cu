@@ -741,7 +741,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sums(Work w)
 }
 
 // Outputs of a finished group: per pair value, error, region count, status.
-// gconv < 0: each pair's own test decides CONVERGED; else the group's verdict.
+// gconv < 0: each pair's own test decides CONVERGED; otherwise gconv is the
+// group's outcome (1 converged, 0 not).
 __device__ void group_outputs(const Work& w, const DevBatch& B, uint32_t g, uint32_t cnt, int c,
                               double V, double E, int st, int gconv)
 {
