@@ -97,6 +97,14 @@ typedef enum {
     PAID_POOL = 4           /* region pool capacity reached */
 } paid_status;
 
+/* Values of options.group_mode. */
+typedef enum {
+    PAID_GROUP_NONE = 0,      /* one partition per integral, per-integral test */
+    PAID_GROUP_PER_PAIR = 1,  /* one partition per (kind, q), every pair meets its own test */
+    PAID_GROUP_GLOBAL = 2     /* one partition per (kind, q), one error sum per group
+                                 (the global error of Algorithm 2, Sec. 4) */
+} paid_group_mode;
+
 /* Options; paid_options_default() fills the defaults named here. */
 typedef struct {
     int rule_n;             /* N of the nested CC pair (coarse N, fine 2N intervals): 4 or 6, and

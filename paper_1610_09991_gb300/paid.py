@@ -23,6 +23,7 @@ PH, PP, MONOMIAL, OVERLAP, FLOW_PH, FLOW_PP = 0, 1, 2, 3, 4, 5
 FF_SHELL1, FF_SHELL12 = 5, 9
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_POOL, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 CONVERGED, BUDGET, NONFINITE, ROUNDCAP, POOL = 0, 1, 2, 3, 4
+GROUP_NONE, GROUP_PER_PAIR, GROUP_GLOBAL = 0, 1, 2       # options.group_mode
 
 #: every entry point declared in include/paid.h
 EXPORTS = ("paid_options_default", "paid_create", "paid_destroy", "paid_workspace_size",

@@ -37,6 +37,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(paid.EXPORTS) <= names
 
 
+def test_binding_constants_match_the_header():
+    txt = open(os.path.join(ROOT, "include", "paid.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\bPAID_(\w+)\s*=\s*(-?\d+)", txt)}
+    for name in ("PH", "PP", "MONOMIAL", "OVERLAP", "FLOW_PH", "FLOW_PP", "OK", "ERR_ARG",
+                 "ERR_OOM", "ERR_CUDA", "ERR_POOL", "ERR_TIMEOUT", "CONVERGED", "BUDGET",
+                 "NONFINITE", "ROUNDCAP", "POOL", "GROUP_NONE", "GROUP_PER_PAIR",
+                 "GROUP_GLOBAL", "FF_SHELL1", "FF_SHELL12"):
+        assert getattr(paid, name) == consts[name], name
+
+
 def test_host_side_calls_without_gpu(lib):
     assert paid.error_string(paid.ERR_POOL) == "region pool full"
     o = paid.options_default()
