@@ -78,13 +78,15 @@ def parse_args():
     ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep",
                                            "flow_omega", "heldout"],
                     default="flow_step")
-    ap.add_argument("--path", choices=["group", "learned", "plain", "fp32", "learned_fp32"],
+    ap.add_argument("--path", choices=["group", "group_fp32", "learned", "plain", "fp32",
+                                       "learned_fp32"],
                     default="group",
                     help="group: one shared partition per (kind, q) for all its pairs, FP64, "
-                         "uniform start; learned: group with the learned proposal's seeded "
-                         "start; plain: one partition per integral, FP64, uniform start; "
-                         "fp32: per integral, FP32 / float-float evaluation; learned_fp32: "
-                         "fp32 with the seeded start")
+                         "uniform start; group_fp32: the same with the kernel F and the row "
+                         "sums in float-float on the FP32 pipe; learned: group with the "
+                         "learned proposal's seeded start; plain: one partition per integral, "
+                         "FP64, uniform start; fp32: per integral, FP32 / float-float "
+                         "evaluation; learned_fp32: fp32 with the seeded start")
     ap.add_argument("--rule-n", type=int, choices=[4, 6, 8, 10, 12], default=12,
                     help="N of the nested rule for the reference arm and for group-mode GPU runs "
                          "without the autotuner (the GPU arm's tuner chooses it otherwise; on "
@@ -277,9 +279,12 @@ def accuracy(v, s, vo, so, rel, ab, against, ident=None, lattice=None):
     max(rel |v_ref|, abs) on integrals both sides converged.  A pair above 2
     (the parity criterion, plus 1e-12 absolute) is decided by the converged
     dense-trapezoid value of the integral (the oracle's brute force): it counts
-    as a parity failure only if v is not within 2 tol of that value."""
+    as a parity failure only if v is not within 2 tol of that value.  An
+    integral the reference converged and v did not (budget, round cap, pool,
+    non-finite) is a parity failure as well."""
     import numpy as np
     both = (s == 0) & (so == 0)
+    unconv = np.where((so == 0) & (s != 0))[0]
     tol = np.maximum(rel * np.abs(vo), ab)
     r = np.abs(v - vo)[both] / tol[both]
     over = np.where(both & (np.abs(v - vo) > 2 * tol + 1e-12))[0]
@@ -300,7 +305,8 @@ def accuracy(v, s, vo, so, rel, ab, against, ident=None, lattice=None):
             "max_err_over_tol": float(r.max()) if r.size else None,
             "median_err_over_tol": float(np.median(r)) if r.size else None,
             "disagreements_decided_by_brute_force": decided,
-            "parity_failures": fails}
+            "unconverged_where_reference_converged": int(unconv.size),
+            "parity_failures": fails + int(unconv.size)}
 
 
 def run_reference(args):
@@ -367,10 +373,11 @@ def run_paid(args):
         # the Omega-regulated flow kinds exist in the shared-partition kernel only
         args.path, args.no_compare, args.no_learned = "group", True, True
     args.eval = "fp64" if args.path in ("plain", "group", "learned") else "fp32"
-    group = 1 if args.path in ("group", "learned") else 0
+    group = 1 if args.path in ("group", "learned", "group_fp32") else 0
     learned = args.path in ("learned", "learned_fp32")
+    fp32_mode = 1 if args.eval == "fp32" else 0
     ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1,
-                    eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group,
+                    eval_fp32=fp32_mode, group_mode=group,
                     rule_n=args.rule_n if group else 4)
     dev = torch.device("cuda", local)
     # N > 1: the temperature sweep is one fixed job split across the ranks by
@@ -491,7 +498,7 @@ def run_paid(args):
 
     eval_s = agg["eval_ms"] / 1e3
     roof = None
-    if group and eval_s > 0:
+    if group and eval_s > 0 and args.eval == "fp64":
         flow = all(b.kind in (W.FLOW_PH, W.FLOW_PP) for b in w.batches)
         fpr = (GROUP_FLOW_FP64_FLOPS_PER_REGION if flow
                else GROUP_FP64_FLOPS_PER_REGION)[ctx.options.rule_n]
@@ -540,6 +547,10 @@ def run_paid(args):
         "path": {"plain": "plain FP64 GPU cubature from the uniform level-2 start",
                  "group": "FP64 GPU cubature, one shared partition per (kind, q) serving all "
                           "81 (l, m) pairs, each pair to its own tolerance",
+                 "group_fp32": "GPU cubature, one shared partition per (kind, q) serving all "
+                               "81 (l, m) pairs, each pair to its own tolerance; kernel F and "
+                               "row sums in float-float on the FP32 pipe, moments and totals "
+                               "FP64",
                  "learned": "learned proposal seeding + batched FP64 GPU cubature, one shared "
                             "partition per (kind, q) serving all 81 (l, m) pairs, each pair "
                             "to its own tolerance",
@@ -571,7 +582,7 @@ def run_paid(args):
         # launch per call (conditional WHILE node), no per-round host sync and
         # no per-kernel events
         cg = P.Context(*w.lattice, ffset=ff, device=local, device_loop=1,
-                       eval_fp32=1 if args.eval == "fp32" else 0, group_mode=group,
+                       eval_fp32=fp32_mode, group_mode=group,
                        cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks,
                        rule_n=ctx.options.rule_n)
 
@@ -606,13 +617,13 @@ def run_paid(args):
         cg.close()
         torch.cuda.empty_cache()
     glob = None
-    if args.path == "group" and not args.no_global:
+    if args.path in ("group", "group_fp32") and not args.no_global:
         # the paper's own stopping test (Algorithm 2, global error): one error
         # sum and one tolerance per (kind, q) group, on the same shared
         # partitions, rule and grid
         cgl = P.Context(*w.lattice, ffset=ff, device=local, group_mode=2,
                         cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks,
-                        rule_n=ctx.options.rule_n)
+                        rule_n=ctx.options.rule_n, eval_fp32=ctx.options.eval_fp32)
 
         def glstep():
             flush.fill_(1)

@@ -110,7 +110,13 @@ typedef struct {
     int rule_n;             /* N of the nested CC pair (coarse N, fine 2N intervals): 4 or 6, and
                                with group_mode also 8, 10 or 12. Default 4 */
     int init_level;         /* L0: initial uniform partition of D into 4^L0 regions, 0..8. Default 2 */
-    int eval_fp32;          /* 1: integrand in FP32, sums in FP64. Default 0 (all FP64) */
+    int eval_fp32;          /* 1: integrand on the FP32 pipe.  One partition per integral: FP32
+                               integrand, FP64 sums, integrals whose FP32 rounding noise crowds
+                               their tolerance re-evaluated in float-float.  group_mode: the
+                               kernel F, the rule's row sums and the moments in float-float
+                               (unevaluated pairs of FP32 numbers, about 44 significant bits
+                               after rounding), each region's pair values Q_2N, Q_N, their
+                               difference and all totals in FP64.  Default 0 (all FP64) */
     int max_rounds;         /* cap on refinement rounds of an integral, counted from the round
                                it entered the pool. Default 4096 */
     double cover;           /* the regions split in a round cover (E - cover * tol) of the error. Default 0.5 */
@@ -122,7 +128,7 @@ typedef struct {
                                waits once, at the end).  0: the host launches every round and
                                reads its counts back.  Default 1 */
     int group_mode;         /* 1: one shared partition per (kind, q) of a batch serves all of the
-                               batch's (l, m) pairs (at most 81; kinds ph, pp, overlap; FP64).
+                               batch's (l, m) pairs (at most 81; kinds ph, pp, overlap, flow).
                                A region evaluates the kernel F once per node and every pair from
                                81 separable moments; it is split while any pair of the group has
                                not met its own tolerance.  Every integral still meets
@@ -138,6 +144,15 @@ typedef struct {
                                Default 0 (one partition per integral) */
     int eval_blocks;        /* group_mode: grid of the region-evaluation kernel (it strides over
                                the eval list); 0 = 152 x 32 blocks.  Default 0 */
+    int trace;              /* 1: every integrate call records each unit's final partition as a
+                               16 x 16 map (entry c = 16 ix + iy: the level of the coarsest final
+                               region meeting level-4 cell (ix, iy); a region of level L < 4
+                               counts for all 4^(4-L) cells it covers) into the buffer given to
+                               paid_set_trace_buffer (none given: nothing is recorded); a unit is
+                               a (kind, q) group in group_mode, else an integral, in the call's
+                               global order; cells of units the call never started are NaN.
+                               These maps are the training targets of the learned proposal.
+                               Default 0 */
 } paid_options;
 
 /* Statistics of the last integrate call on a context. */
@@ -242,12 +257,23 @@ int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int np
                       const int32_t* lm, int nreg, const int32_t* regions, double* q2N,
                       double* dq, void* workspace, size_t ws_bytes, void* stream);
 
-/* Diagnostics: the FP64 exp and division the shared-partition kernel uses
- * (its own exp after Tang's table-driven method, its own division from the
- * approximate reciprocal and Newton-Raphson steps), applied element-wise on
- * device arrays so that tests can hold them to their error bounds.
- *   which = 0: out[i] = exp(-x[i]), x[i] >= 0 (y unused, may be NULL);
- *   which = 1: out[i] = x[i] / y[i], y[i] normal and non-zero.
+/* Diagnostics: the arithmetic of the shared-partition kernel (its own exp
+ * after Tang's table-driven method, its own division from the approximate
+ * reciprocal and Newton-Raphson steps, and their float-float counterparts
+ * of the FP32-pipe path), applied element-wise on device arrays so that tests
+ * can hold them to their error bounds.
+ *   which = 0: out[i] = exp(-x[i]), x[i] >= 0, FP64 (y unused, may be NULL);
+ *   which = 1: out[i] = x[i] / y[i], y[i] normal and non-zero, FP64;
+ *   which = 2: out[i] = exp(-x[i]), x[i] >= 0, float-float (x rounded to
+ *              float-float first; y unused);
+ *   which = 3: out[i] = 2T F(x1, x2) of the temperature bubbles (Sec. 2,
+ *              F = [tanh x1 - tanh x2] / (2 (e1 - e2)), x = e/2T) at
+ *              x1 = x[i], x2 = y[i], float-float;
+ *   which = 4: the same 2T F in FP64;
+ *   which = 5: the Omega derivative of the flow kinds' frequency integral,
+ *              the divided difference of Hdot at (e1, e2) = (x[i], y[i]) with
+ *              Omega = 0.1 (flow ph), float-float;
+ *   which = 6: the same in FP64.
  * Returns PAID_OK (stream synchronised), PAID_ERR_ARG or PAID_ERR_CUDA. */
 int paid_check_math(paid_ctx* ctx, int which, int64_t n, const double* x, const double* y,
                     double* out, void* stream);
@@ -289,10 +315,11 @@ int paid_tu_flow_rhs(paid_ctx* ctx, int nq, int nff, const double* VP, const dou
                      double* dC, double* dD, void* stream);
 
 /* paid_integrate_batch without a workspace argument, for callers that cannot
- * allocate device memory when they need the integrals: code that runs while
- * a CUDA graph is being captured, runtimes that fix their device-memory budget
- * at start-up, or latency-bound loops that must not allocate.  (The paper has
- * no counterpart; it is a deployment convenience.)
+ * allocate device memory when they need the integrals: runtimes that fix their
+ * device-memory budget at start-up, plug-ins living inside another framework's
+ * memory manager, or latency-bound loops that must not allocate (cudaMalloc and
+ * cudaFree can synchronise the device).  (The paper has no counterpart; it is
+ * a deployment convenience.)
  *   - The region pool is a 64 MiB array built into the library
  *     (PAID_STATIC_SCRATCH_BYTES); every GPU that loads the library keeps it
  *     until the process exits.  The call allocates nothing: no cudaMalloc,
@@ -324,40 +351,48 @@ int paid_integrate_batch_static(paid_ctx* ctx, int kind,
 
 /* ---------------------------------------------------------------------------
  * Learned refinement proposal (not in the paper; the workload specification's
- * learned component).  A 16 x 16 map per integral of predicted log10 cell
- * errors, relative to the integral's scale, decides how far each level-4 cell
- * of the domain is pre-split before refinement starts; it never decides
- * convergence (the |Q_N - Q_2N| sums still do).
+ * learned component).  A 16 x 16 map per unit -- (kind, q) group in group_mode,
+ * else integral -- of the predicted level of the coarsest final region in each
+ * level-4 cell (what options.trace records) decides how deep each cell of the
+ * domain starts; it never decides convergence (the |Q_N - Q_2N| sums still
+ * do), and a map entry that is too deep only costs evaluations.
  *
  * Map convention: entry c = 16 ix + iy is the level-4 cell (ix, iy) of the
- * region grid; its value is log10(err_c / S) with err_c = |Q_N - Q_2N| of the
- * cell evaluated as one region and S = sum_c |Q_2N of cell c| (clamped to
- * [-16, 0]).
+ * region grid.
  * ------------------------------------------------------------------------- */
 
-/* Targets for training: evaluate each integral's uniform level-4 grid once
- * (FP64, with the context's rule, or N = 6 when the context's N is higher)
- * and write its map to out (device, float [nq*npairs][256], the batch order
- * of paid_integrate_batch).  Workspace as for paid_integrate_batch with 4^4
+/* The buffer the integrate calls write their trace maps to when
+ * options.trace = 1: device, float [n_units][256], owned by the caller and
+ * kept alive until the work on the call's stream has finished.  A call whose
+ * unit count exceeds n_units returns PAID_ERR_ARG.  maps = NULL, n_units = 0
+ * clears it.  Returns PAID_OK or PAID_ERR_ARG. */
+int paid_set_trace_buffer(paid_ctx* ctx, float* maps, int64_t n_units);
+
+/* Rule-error maps of the uniform level-4 grid: evaluate each integral's 256
+ * level-4 cells once (FP64, with the context's rule, or N = 6 when the
+ * context's N is higher) and write log10(err_c / S), err_c = |Q_N - Q_2N| of
+ * cell c as one region, S = sum_c |Q_2N of cell c| (clamped to [-16, 0]), to
+ * out (device, float [nq*npairs][256], the batch order of
+ * paid_integrate_batch).  Workspace as for paid_integrate_batch with 4^4
  * initial regions per integral.  Returns PAID_OK / ERR_ARG / ERR_OOM / ERR_CUDA. */
 int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
                      const int32_t* lm, double T, float* out, void* workspace, size_t ws_bytes,
                      void* stream);
 
 /* paid_integrate_multi with the initial partition taken from maps:
- *   proposal  device, float [n][256] in the global order of the batches
- *             (batch 0's integrals first), or NULL for a uniform level-4 start;
- *   rate      calibrated decay of a cell's error per level, as a power of 4
- *             (a cell predicted at log10 error t is split k = floor((t - b) /
- *             (rate log10 4)) more levels, b = log10(rel_tol / 256), k in
- *             [-2, 3]; cells predicted below b are merged back to level 3 or 2
- *             where all their siblings agree).
- * With options.group_mode, a (kind, q) group is seeded from the cell-wise
- * largest value over its pairs' maps (every cell as deep as its most
- * demanding pair asks).
- * Everything else as paid_integrate_multi. */
+ *   proposal  device, float [n_units][256] in the global unit order of the
+ *             batches (batch 0's units first; units as for options.trace),
+ *             or NULL for a uniform level-4 start;
+ *   margin    finite: cell c starts at level floor(proposal[c] - margin),
+ *             clamped to 2..7 (4^(level-4) regions in the cell from level 4
+ *             on; a level-3 block whose four cells all ask for <= 3, and a
+ *             level-2 block whose 16 cells all ask for 2, stay one region).
+ *             With margin >= the map's error every seed region is an ancestor
+ *             of (or equal to) a region of the unseeded run's final partition.
+ * A seed above max_regions / 2 regions for a unit falls back to the uniform
+ * level-2 start.  Everything else as paid_integrate_multi. */
 int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb,
-                                const float* proposal, double rate, void* workspace,
+                                const float* proposal, double margin, void* workspace,
                                 size_t ws_bytes, void* stream);
 
 /* The network: 32 -> 256 -> 256 -> 256 -> 256 -> 256, GELU after the four
@@ -380,6 +415,10 @@ int paid_mlp_init(float* params, uint64_t seed, void* stream);
  *  one-hot kind [ph, pp], 0 padding), mu and t' from the context. */
 int paid_mlp_features(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
                       const int32_t* lm, double T, uint16_t* x, void* stream);
+/* The same with one row per (kind, q) group (x: [nq][32], the form-factor
+ * one-hots zero): the inputs of a group-mode proposal. */
+int paid_mlp_group_features(paid_ctx* ctx, int kind, int nq, const double* q, double T,
+                            uint16_t* x, void* stream);
 /* Forward pass: x (BF16 [M][32]) -> out (FP32 [M][256]). */
 int paid_mlp_forward(const float* params, const uint16_t* x, int64_t M, float* out,
                      void* workspace, size_t ws_bytes, void* stream);
@@ -391,6 +430,32 @@ int paid_mlp_grad(const float* params, const uint16_t* x, const float* target, i
  * weights only) with moments m, v (FP32, param_count); step counts from 1. */
 int paid_mlp_adamw(float* params, const float* grad, float* m, float* v, int step, float lr,
                    float weight_decay, void* stream);
+
+/* Training of the network on the device: `epochs` passes over the M rows
+ * (x: BF16 [M][32], target: FP32 [M][256], both device, finite) in minibatches
+ * of `batch` rows, each pass in a fresh order drawn from `seed` (splitmix64,
+ * Fisher-Yates); per minibatch the mean-squared-error gradient and one AdamW
+ * step (paid_mlp_grad, paid_mlp_adamw) with the learning rate decayed from lr
+ * to 0 on a cosine over the call's steps.  params, m, v (device, FP32,
+ * param_count): master weights and AdamW moments, updated in place.  *step
+ * (host): AdamW steps taken so far (0 for a fresh start), advanced.
+ * epoch_loss: host float [epochs] (mean minibatch loss per pass), or NULL.
+ * workspace: device, >= paid_proposal_train_workspace_size(M, batch) bytes.
+ * Synchronises `stream` once per epoch when epoch_loss is given.
+ * Returns PAID_OK, PAID_ERR_ARG, PAID_ERR_OOM or PAID_ERR_CUDA. */
+int paid_proposal_train_workspace_size(int64_t M, int64_t batch, size_t* bytes);
+int paid_proposal_train(float* params, float* m, float* v, const uint16_t* x, const float* target,
+                        int64_t M, int epochs, int64_t batch, float lr, float weight_decay,
+                        uint64_t seed, int* step, float* epoch_loss, void* workspace,
+                        size_t ws_bytes, void* stream);
+/* Save the network's FP32 parameters (device, param_count) to a file: the 8
+ * bytes "PAIDMLP1", the count as int64, then the values (little-endian IEEE
+ * binary32).  Load checks the tag and the count and uploads; a file of another
+ * layout returns PAID_ERR_ARG and leaves params unchanged.  Both synchronise
+ * `stream`.  Returns PAID_OK, PAID_ERR_ARG (bad path or file) or
+ * PAID_ERR_CUDA. */
+int paid_proposal_save(const float* params, const char* path, void* stream);
+int paid_proposal_load(float* params, const char* path, void* stream);
 
 /* Statistics of the last integrate call.  Returns PAID_OK or PAID_ERR_ARG. */
 int paid_last_stats(paid_ctx* ctx, paid_stats* out);

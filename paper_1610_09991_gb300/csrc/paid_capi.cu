@@ -39,6 +39,7 @@ struct LoopGraph {
     int64_t n = 0, cap = 0;
     int nb = 0, vstride = 0;
     int rule_n = 0, eval_fp32 = 0, max_rounds = 0, eval_blocks = 0;
+    const float* tmap = nullptr;       // trace buffer it writes (null: none)
     double cover = 0.0;
 };
 
@@ -54,6 +55,8 @@ struct paid_ctx {
     LoopGraph loop;
     std::string last_error;
     paid_stats stats{};
+    float* trace_buf = nullptr;        // paid_set_trace_buffer
+    int64_t trace_units = 0;
 };
 
 namespace {
@@ -67,7 +70,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t batches, totals, ls, trig, meta, born, seg_base, seg_count, active0, active1, cnt_new, cnt_eval,
         thr, pre_pool, pre_eval, pre_act, blk_pool, blk_eval, blk_act, key0, key1, val0, val1,
-        err0, err1, nse0, nse1, evl, vval0, vval1, verr0, verr1, vsrc, gmap, gpart, gsum, gtol,
+        err0, err1, nse0, nse1, evl, vval0, vval1, verr0, verr1, vsrc, gpart, gsum, gtol,
         gsc, gstate, end;
 };
 
@@ -112,7 +115,6 @@ Layout layout(int64_t n, int64_t cap, bool group)
         L.verr0 = take(4 * kGroupPairs * cap);
         L.verr1 = take(4 * kGroupPairs * cap);
         L.vsrc = take(4 * cap);
-        L.gmap = take(4 * 256 * n);
         L.gpart = take(8 * size_t(kGroupSplit) * 2 * kGroupPairs * n);
         L.gsum = take(8 * 2 * kGroupPairs * n);
         L.gtol = take(8 * kGroupPairs * n);
@@ -164,7 +166,6 @@ Work make_work(char* base, const Layout& L, int64_t n, int64_t cap, int nb, bool
         w.verr[0] = reinterpret_cast<float*>(base + L.verr0);
         w.verr[1] = reinterpret_cast<float*>(base + L.verr1);
         w.vsrc = reinterpret_cast<uint32_t*>(base + L.vsrc);
-        w.gmap = reinterpret_cast<float*>(base + L.gmap);
         w.gpart = reinterpret_cast<double*>(base + L.gpart);
         w.gsum = reinterpret_cast<double*>(base + L.gsum);
         w.gtol = reinterpret_cast<double*>(base + L.gtol);
@@ -226,8 +227,8 @@ int check_options(const paid_options& o, std::string& why)
     if (o.timing != 0 && o.timing != 1) { why = "timing must be 0 or 1"; return PAID_ERR_ARG; }
     if (o.device_loop != 0 && o.device_loop != 1) { why = "device_loop must be 0 or 1"; return PAID_ERR_ARG; }
     if (o.group_mode < 0 || o.group_mode > 2) { why = "group_mode must be 0, 1 or 2"; return PAID_ERR_ARG; }
-    if (o.group_mode && o.eval_fp32) { why = "group_mode evaluates in FP64 (eval_fp32 = 0)"; return PAID_ERR_ARG; }
     if (o.eval_blocks < 0) { why = "eval_blocks must be >= 0"; return PAID_ERR_ARG; }
+    if (o.trace != 0 && o.trace != 1) { why = "trace must be 0 or 1"; return PAID_ERR_ARG; }
     return PAID_OK;
 }
 
@@ -248,6 +249,7 @@ int paid_options_default(paid_options* opt)
     opt->device_loop = 1;
     opt->group_mode = 0;
     opt->eval_blocks = 0;
+    opt->trace = 0;
     return PAID_OK;
 }
 
@@ -345,6 +347,27 @@ int paid_last_stats(paid_ctx* ctx, paid_stats* out)
 
 namespace {
 
+// The per-batch argument rules shared by every integrate entry point: null
+// when `b` is valid, else a static message (no allocation, so that the
+// allocation-free entry point can use it too).  nl0 = 4^init_level.
+const char* batch_error(const paid_batch& b, int64_t nl0, bool group)
+{
+    if (b.kind < PAID_PH || b.kind > PAID_FLOW_PP) return "bad kind";
+    const bool flow = b.kind == PAID_FLOW_PH || b.kind == PAID_FLOW_PP;
+    if (!group && flow) return "the flow kinds take group_mode = 1 or 2";
+    if (flow && !(b.T > 0.0)) return "flow kinds: Omega (the T field) must be > 0";
+    if (b.nq < 0 || b.npairs < 0) return "nq, npairs must be >= 0";
+    const int64_t nbi = int64_t(b.nq) * b.npairs;
+    if (nbi > 0 && (!b.q || !b.lm || !b.values || !b.errors || !b.regions || !b.status))
+        return "null buffer";
+    if (!(b.rel_tol >= 0.0) || !(b.abs_tol >= 0.0)) return "tolerances must be >= 0";
+    if (b.max_regions < nl0 || b.max_regions > kMaxRegionsPerIntegral)
+        return "max_regions must be in [4^init_level, 2^23]";
+    if (group && b.kind == PAID_MONOMIAL) return "group_mode takes the ph, pp, overlap and flow kinds";
+    if (group && b.npairs > kGroupPairs) return "group_mode takes at most 81 pairs per batch";
+    return nullptr;
+}
+
 // Validates the batches, sizes the pool, lays out the workspace and uploads
 // the batch table.  n0 = regions per integral that the start needs at least.
 int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, size_t ws_bytes,
@@ -362,23 +385,8 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
     int64_t n_int = 0;
     for (int i = 0; i < nb; ++i) {
         const paid_batch& b = batches[i];
-        if (b.kind < PAID_PH || b.kind > PAID_FLOW_PP) return fail(ctx, PAID_ERR_ARG, "bad kind");
-        if (!group && (b.kind == PAID_FLOW_PH || b.kind == PAID_FLOW_PP))
-            return fail(ctx, PAID_ERR_ARG, "the flow kinds take group_mode = 1 or 2");
-        if ((b.kind == PAID_FLOW_PH || b.kind == PAID_FLOW_PP) && !(b.T > 0.0))
-            return fail(ctx, PAID_ERR_ARG, "flow kinds: Omega (the T field) must be > 0");
-        if (b.nq < 0 || b.npairs < 0) return fail(ctx, PAID_ERR_ARG, "nq, npairs must be >= 0");
+        if (const char* why = batch_error(b, nl0, group)) return fail(ctx, PAID_ERR_ARG, why);
         const int64_t nbi = int64_t(b.nq) * b.npairs;
-        if (nbi > 0 && (!b.q || !b.lm || !b.values || !b.errors || !b.regions || !b.status))
-            return fail(ctx, PAID_ERR_ARG, "null buffer");
-        if (!(b.rel_tol >= 0.0) || !(b.abs_tol >= 0.0))
-            return fail(ctx, PAID_ERR_ARG, "tolerances must be >= 0");
-        if (b.max_regions < nl0 || b.max_regions > kMaxRegionsPerIntegral)
-            return fail(ctx, PAID_ERR_ARG, "max_regions must be in [4^init_level, 2^23]");
-        if (group && b.kind == PAID_MONOMIAL)
-            return fail(ctx, PAID_ERR_ARG, "group_mode takes the ph, pp and overlap kinds");
-        if (group && b.npairs > kGroupPairs)
-            return fail(ctx, PAID_ERR_ARG, "group_mode takes at most 81 pairs per batch");
         if (nbi == 0) continue;
         DevBatch d{};
         d.kind = b.kind;
@@ -411,12 +419,22 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
     cap = capacity_for(n, ws_bytes, group);
     if (o.pool_capacity > 0) cap = std::min(cap, o.pool_capacity);
     if (cap < n * n0) return fail(ctx, PAID_ERR_OOM, "workspace too small for the initial partition");
+    const bool trace = o.trace && ctx->trace_buf;
+    if (trace && ctx->trace_units < n)
+        return fail(ctx, PAID_ERR_ARG, "options.trace: the trace buffer (paid_set_trace_buffer) "
+                                       "must hold one map per unit of the call");
     const Layout L = layout(n, cap, group);
     w = make_work(static_cast<char*>(workspace), L, n, cap, int(hb.size()), group, ctx->nff);
     w.gglobal = group && ctx->opt.group_mode == 2;
     cudaError_t e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+    if (trace) {
+        // NaN in every cell of a unit that never runs (0xffffffff is a NaN)
+        w.tmap = ctx->trace_buf;
+        if ((e = cudaMemsetAsync(w.tmap, 0xff, sizeof(float) * 256 * size_t(n), s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "trace init");
+    }
     return PAID_OK;
 }
 
@@ -434,13 +452,14 @@ cudaError_t launch_round(paid_ctx* ctx, const Work& w, int64_t hint_eval, int64_
     cudaError_t e;
     const bool group = w.vstride > 0;
     if ((e = mark(0)) != cudaSuccess ||
-        (e = group ? launch_eval_group(w, hint_eval, o.rule_n, ctx->lat, s, nullptr, nullptr,
-                                       o.eval_blocks)
+        (e = group ? launch_eval_group(w, hint_eval, o.rule_n, o.eval_fp32, ctx->lat, s, nullptr,
+                                       nullptr, o.eval_blocks)
                    : launch_eval(w, hint_eval, o.rule_n, o.eval_fp32, ctx->lat, s,
                                  ev && o.eval_fp32 ? ev[6] : nullptr)) != cudaSuccess ||
         (e = mark(1)) != cudaSuccess ||
         (e = group ? launch_reduce_group(w, hint_active, o.max_rounds, o.cover, s)
                    : launch_reduce_test(w, hint_active, o.max_rounds, o.cover, s)) != cudaSuccess ||
+        (e = launch_trace(w, hint_active, s)) != cudaSuccess ||
         (e = mark(2)) != cudaSuccess ||
         (e = launch_scan(w, hint_active, 0, s)) != cudaSuccess ||
         (e = launch_throttle(w, hint_active, s)) != cudaSuccess ||
@@ -458,12 +477,12 @@ cudaError_t launch_round(paid_ctx* ctx, const Work& w, int64_t hint_eval, int64_
 // kernels one round launches (graph: every node; host loop: those with work)
 int64_t round_kernels(const paid_options& o, int64_t n_eval, int64_t n_active, bool in_graph)
 {
-    const int64_t ev = n_eval > 0 ? (o.eval_fp32 ? 2 : 1) : 0;
+    const int64_t ev = n_eval > 0 ? (o.eval_fp32 && !o.group_mode ? 2 : 1) : 0;
     const int64_t slots = n_active > 0 ? 1 : 0;
     // eval, reduce (group: 4), scan (2), throttle, rescan (2), split, [vector copy], control,
     // [wave]
-    return ev + (o.group_mode ? 4 : 1) * slots + (slots + 1) + slots + (slots + 1) + slots +
-           (o.group_mode ? slots : 0) + 1 + (in_graph ? 1 : 0);
+    return ev + (o.group_mode ? 4 : 1) * slots + (o.trace ? slots : 0) + (slots + 1) + slots +
+           (slots + 1) + slots + (o.group_mode ? slots : 0) + 1 + (in_graph ? 1 : 0);
 }
 
 // The device-loop graph for this workspace layout and these options:
@@ -475,7 +494,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     if (G.exec && G.base == w.batches && G.n == w.n && G.cap == w.cap && G.nb == w.nb &&
         G.vstride == w.vstride &&
         G.rule_n == o.rule_n && G.eval_fp32 == o.eval_fp32 && G.max_rounds == o.max_rounds &&
-        G.eval_blocks == o.eval_blocks &&
+        G.eval_blocks == o.eval_blocks && G.tmap == w.tmap &&
         G.cover == o.cover) {
         *out = G.exec;
         return PAID_OK;
@@ -533,6 +552,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     G.eval_fp32 = o.eval_fp32;
     G.max_rounds = o.max_rounds;
     G.eval_blocks = o.eval_blocks;
+    G.tmap = w.tmap;
     G.cover = o.cover;
     *out = exec;
     return PAID_OK;
@@ -606,7 +626,7 @@ int run_loop(paid_ctx* ctx, const Work& w, int64_t admitted, int64_t n_eval, int
             if ((e = read_state(L, t)) != cudaSuccess) return cfail(e, "round sync");
             if (timed) {
                 st.eval_ms += span(0, 1);
-                if (o.eval_fp32 && ne > 0) st.df_ms += span(6, 1);
+                if (o.eval_fp32 && !o.group_mode && ne > 0) st.df_ms += span(6, 1);
                 st.reduce_ms += span(1, 2);
                 st.scan_ms += span(2, 3);
                 st.split_ms += span(3, 4);
@@ -691,11 +711,11 @@ int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb, void*
 }
 
 int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb,
-                                const float* proposal, double rate, void* workspace,
+                                const float* proposal, double margin, void* workspace,
                                 size_t ws_bytes, void* stream)
 {
     if (!ctx) return PAID_ERR_ARG;
-    if (!(rate > 0.0)) return fail(ctx, PAID_ERR_ARG, "rate must be > 0");
+    if (!std::isfinite(margin)) return fail(ctx, PAID_ERR_ARG, "margin must be finite");
     const paid_options& o = ctx->opt;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceGuard guard(ctx->device);
@@ -705,13 +725,10 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     int rc = prepare(ctx, batches, nb, workspace, ws_bytes, 16, s, w, n, cap, group);
     if (rc != PAID_OK || n == 0) return rc;
     cudaError_t e;
-    // group mode seeds each group from the cell-wise maximum of its pairs' maps
-    const float* seed_map = group && proposal ? w.gmap : proposal;
     // the slot scan reads its slot count from the loop state
     if ((e = launch_setup(w, -1, ctx->nff, o.eval_fp32 ? 0 : 1, s)) != cudaSuccess ||
         (e = launch_state_init(w, n, 0, 0, n, -1, o.max_rounds, s)) != cudaSuccess ||
-        (group && (e = launch_group_map(w, proposal, s)) != cudaSuccess) ||
-        (e = launch_seed(w, seed_map, rate, 0, s)) != cudaSuccess ||
+        (e = launch_seed(w, proposal, margin, 0, s)) != cudaSuccess ||
         (e = launch_scan(w, n, 0, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "seed");
     if ((e = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals), cudaMemcpyDeviceToHost,
@@ -721,9 +738,27 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     const RoundTotals t = *ctx->h_totals;
     if (int64_t(t.pool) > cap)
         return fail(ctx, PAID_ERR_OOM, "workspace too small for the seeded partition");
-    if ((e = launch_seed(w, seed_map, rate, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
-    ctx->stats.launches = 6;
+    if ((e = launch_seed(w, proposal, margin, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
+    ctx->stats.launches = 5;
     return run_loop(ctx, w, n, int64_t(t.eval), int64_t(t.pool), -1, s);
+}
+
+int paid_set_trace_buffer(paid_ctx* ctx, float* maps, int64_t n_units)
+{
+    if (!ctx || n_units < 0 || (n_units > 0 && !maps)) return PAID_ERR_ARG;
+    ctx->trace_buf = n_units > 0 ? maps : nullptr;
+    ctx->trace_units = n_units;
+    return PAID_OK;
+}
+
+int paid_mlp_group_features(paid_ctx* ctx, int kind, int nq, const double* q, double T,
+                            uint16_t* x, void* stream)
+{
+    if (!ctx || nq < 0) return PAID_ERR_ARG;
+    if (nq > 0 && (!q || !x)) return PAID_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    return launch_features(kind, nq, q, 1, nullptr, T, ctx->lat.mu, ctx->lat.tp, x,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
 }
 
 int paid_cell_errors(paid_ctx* ctx, int kind, int nq, const double* q, int npairs,
@@ -804,7 +839,8 @@ int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int np
     if ((e = cudaMemcpyAsync(w.batches, &d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = launch_rule_setup(w, kind, q, regions, nreg, bad, s)) != cudaSuccess ||
         (e = launch_state_init(w, 1, nreg, nreg, 1, 0, 1, s)) != cudaSuccess ||
-        (e = launch_eval_group(w, nreg, ctx->opt.rule_n, ctx->lat, s, q2N, dq)) != cudaSuccess ||
+        (e = launch_eval_group(w, nreg, ctx->opt.rule_n, ctx->opt.eval_fp32, ctx->lat, s, q2N,
+                               dq)) != cudaSuccess ||
         (e = launch_rule_flag(bad, nreg, npairs, q2N, dq, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "rule regions");
     // like the integrate calls, return with the outputs complete
@@ -815,8 +851,8 @@ int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int np
 int paid_check_math(paid_ctx* ctx, int which, int64_t n, const double* x, const double* y,
                     double* out, void* stream)
 {
-    if (!ctx || (which != 0 && which != 1) || n < 0) return PAID_ERR_ARG;
-    if (n > 0 && (!x || !out || (which == 1 && !y))) return PAID_ERR_ARG;
+    if (!ctx || which < 0 || which > 6 || n < 0) return PAID_ERR_ARG;
+    if (n > 0 && (!x || !out || (which != 0 && which != 2 && !y))) return PAID_ERR_ARG;
     DeviceGuard guard(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_check_math(which, n, x, y, out, s);
@@ -1032,14 +1068,14 @@ int paid_integrate_batch(paid_ctx* ctx, int kind, int nq, const double* q, int n
 // Allocation-free variant of paid_integrate_batch.
 //
 // Some callers cannot allocate device memory at the point where they need the
-// integrals: code running while a CUDA graph is being captured, host runtimes
-// that hand out a fixed device-memory budget at start-up and forbid later
-// allocations, or real-time loops where an allocation (and the device-wide
-// synchronisation it can imply) is not acceptable.  Such callers cannot pass
-// a workspace either, because that workspace would itself have to be
-// allocated.  For them the region pool lives in the file-scope array below,
-// which is part of the library's device image: every GPU that loads the
-// library holds it until the process exits.
+// integrals: host runtimes that hand out a fixed device-memory budget at
+// start-up and forbid later allocations, plug-ins that run inside another
+// framework's memory manager, or real-time loops where an allocation (and the
+// device-wide synchronisation cudaMalloc and cudaFree can imply) is not
+// acceptable.  Such callers cannot pass a workspace either, because that
+// workspace would itself have to be allocated.  For them the region pool lives
+// in the file-scope array below, which is part of the library's device image:
+// every GPU that loads the library holds it until the process exits.
 //
 // Host code must not use the array's name as an address (on the host it is a
 // stand-in symbol, not device memory); its device address is looked up once
@@ -1087,15 +1123,25 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     if (!ctx) return PAID_ERR_ARG;
     const paid_options& o = ctx->opt;
     const int64_t n0 = int64_t(1) << (2 * o.init_level);
-    if (kind < PAID_PH || kind > PAID_FLOW_PP || nq < 0 || npairs < 0) return PAID_ERR_ARG;
+    const bool group = o.group_mode != 0;
+    paid_batch b{};
+    b.kind = kind;
+    b.T = T;
+    b.nq = nq;
+    b.q = q;
+    b.npairs = npairs;
+    b.lm = lm;
+    b.rel_tol = rel_tol;
+    b.abs_tol = abs_tol;
+    b.max_regions = max_regions;
+    b.values = values;
+    b.errors = errors;
+    b.regions = regions;
+    b.status = status;
+    // the same argument rules as paid_integrate_batch
+    if (batch_error(b, n0, group)) return PAID_ERR_ARG;
     const int64_t n = int64_t(nq) * npairs;
     if (n > kStaticMaxIntegrals) return PAID_ERR_ARG;
-    if (n > 0 && (!q || !lm || !values || !errors || !regions || !status)) return PAID_ERR_ARG;
-    if (!(rel_tol >= 0.0) || !(abs_tol >= 0.0)) return PAID_ERR_ARG;
-    if (max_regions < n0 || max_regions > kMaxRegionsPerIntegral) return PAID_ERR_ARG;
-    const bool group = o.group_mode != 0;
-    if (group && (kind == PAID_MONOMIAL || npairs > kGroupPairs)) return PAID_ERR_ARG;
-    if (!group && (kind == PAID_FLOW_PH || kind == PAID_FLOW_PP)) return PAID_ERR_ARG;
     ctx->stats = paid_stats{};
     ctx->stats.n_integrals = n;
     if (n == 0) return PAID_OK;

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "paid_internal.cuh"
 
@@ -953,15 +954,237 @@ __device__ __forceinline__ double flow_Fdot(double e1, double e2, double W, bool
     return pp ? -D : D;
 }
 
-// Diagnostics for paid_check_math: which = 0: exp_neg(x), 1: div_nr(x, y).
+// ---------------------------------------------------------------------------
+// FP32-pipe evaluation of the shared-partition kernel (options.eval_fp32 with
+// group_mode).  The kernel F and the row sums run in float-float on the FP32
+// pipe (64x the FP64 pipe on this GPU); the moments, the pair values, their
+// errors and every total stay FP64.  A float-float number is an unevaluated
+// sum hi + lo of two FP32 numbers (about 48 significant bits).  The building
+// blocks are the published error-free transformations: Knuth's TwoSum,
+// Dekker's FastTwoSum (|a| >= |b|) and the FMA form of TwoProduct, combined as
+// in double-word arithmetic.  Every product whose rounded value enters a
+// TwoSum is written with __fmul_rn, which the compiler never contracts into
+// an FMA, so that each transformation stays exact.
+__device__ __forceinline__ f2 ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ f2 ff_fast(float a, float b)   // |a| >= |b| (or a = 0)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2 ff_from(double x)
+{
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - double(h))};
+}
+__device__ __forceinline__ double ff_to(f2 a) { return double(a.hi) + double(a.lo); }
+__device__ __forceinline__ f2 ff_neg(f2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ f2 ff_add(f2 a, f2 b)
+{
+    const f2 s = ff_two_sum(a.hi, b.hi);
+    return ff_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ f2 ff_sub(f2 a, f2 b) { return ff_add(a, ff_neg(b)); }
+// 1 + u for 0 <= u <= 1
+__device__ __forceinline__ f2 ff_one_plus(f2 u)
+{
+    const f2 s = ff_fast(1.0f, u.hi);
+    return ff_fast(s.hi, __fadd_rn(s.lo, u.lo));
+}
+__device__ __forceinline__ f2 ff_mul(f2 a, f2 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff_fast(p, e);
+}
+__device__ __forceinline__ f2 ff_sqr(f2 a)
+{
+    const float p = __fmul_rn(a.hi, a.hi);
+    float e = fmaf(a.hi, a.hi, -p);
+    e = fmaf(a.hi + a.hi, a.lo, e);
+    return ff_fast(p, e);
+}
+// a b + c, normalised
+__device__ __forceinline__ f2 ff_fma(f2 a, f2 b, f2 c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const f2 s = ff_two_sum(c.hi, p);
+    return ff_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+// c += a b with c an accumulator left unnormalised: hi takes the rounded
+// running sum, lo every rounding error (exact TwoSum and TwoProduct errors and
+// the cross terms), so lo stays within a few ulp of hi over a row of nodes;
+// ff_fast(hi, lo) normalises at the end.
+__device__ __forceinline__ void ff_acc(f2 a, f2 b, f2& c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = __fadd_rn(c.hi, p);
+    const float bb = __fsub_rn(s, c.hi);
+    const float t = __fadd_rn(__fsub_rn(c.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    c.hi = s;
+    c.lo = __fadd_rn(c.lo, __fadd_rn(t, e));
+}
+// a / b, b normal and non-zero: q1 = a_hi rcp(b_hi), one correction from the
+// residual a - b q1 (its leading part a_hi - b_hi q1 is exact, Sterbenz).
+__device__ __forceinline__ f2 ff_div(f2 a, f2 b)
+{
+    const float r = rcp_approx(b.hi);
+    const float q1 = __fmul_rn(a.hi, r);
+    const float p = __fmul_rn(b.hi, q1);
+    const float e = fmaf(b.hi, q1, -p);
+    float res = __fsub_rn(__fsub_rn(a.hi, p), e);
+    res = fmaf(-b.lo, q1, res);
+    res = __fadd_rn(res, a.lo);
+    return ff_fast(q1, __fmul_rn(res, r));
+}
+
+// exp(-a) for a float-float a >= 0 (Tang's table-driven method, as exp_neg):
+// a = k ln2/64 + r, k = rint(64 a / ln2), e^-a = 2^(-k/64) e^-r.  ln2/64 is
+// split as C1 + C2 + C3 with C1 of 9 significant bits, so k C1 is exact for
+// k < 2^15 and a_hi - k C1 is exact (Sterbenz); r is then formed in
+// float-float.  e^t (t = -r, |t| <= 0.0055) = 1 + t + t^2/2 + t^3 (1/6 + t/24
+// + t^2/120): the first three terms in float-float, the rest (< 3e-8) in FP32
+// (error < 4e-15); truncation t^6/720 < 4e-17.  2^(j/64) comes from a
+// float-float table and 2^m (m >= -73) scales both parts exactly.  a >= 50
+// gives 0 (e^-50 < 2e-22: the kernel F only uses v^2 and products of v there,
+// which flush to zero in FP32).
+__device__ __forceinline__ f2 ff_exp_neg(f2 a, const float2* tab)
+{
+    if (!(a.hi < 50.0f)) return {a.hi != a.hi ? a.hi : 0.0f, 0.0f};
+    const float C1 = 0.010833740234375f;          // 0x1.63p-7
+    const float C2 = -3.3155381515825866e-06f;
+    const float C3 = 2.572804640231345e-14f;
+    const float k = rintf(a.hi * 92.33248138427734f);
+    const float t1 = fmaf(-k, C1, a.hi);          // exact
+    const f2 s1 = ff_two_sum(t1, a.lo);
+    const float p2 = __fmul_rn(k, C2);
+    const float e2 = fmaf(k, C2, -p2);
+    const f2 s2 = ff_two_sum(s1.hi, -p2);
+    float lo = __fadd_rn(s2.lo, s1.lo);
+    lo = __fsub_rn(lo, e2);
+    lo = fmaf(-k, C3, lo);
+    const f2 r = ff_fast(s2.hi, lo);
+    const float th = -r.hi, tl = -r.lo;           // t = -r
+    const float h = __fmul_rn(th, th);
+    const float hl = fmaf(th, th, -h);            // th^2 = h + hl
+    float q = fmaf(th, 1.0f / 120.0f, 1.0f / 24.0f);
+    q = fmaf(th, q, 1.0f / 6.0f);
+    const float c = __fmul_rn(__fmul_rn(h, th), q);
+    const f2 S = ff_fast(th, 0.5f * h);           // t + t^2/2, leading parts
+    float sl = __fadd_rn(S.lo, tl);
+    sl = fmaf(0.5f, hl, sl);
+    sl = fmaf(th, tl, sl);
+    sl = __fadd_rn(sl, c);
+    const f2 P0 = ff_fast(1.0f, S.hi);
+    const f2 P = ff_fast(P0.hi, __fadd_rn(P0.lo, sl));
+    const int n = -int(k);
+    const int m = n >> 6;                         // floor(n / 64)
+    const int j = n & 63;
+    const float2 tj = tab[j];
+    const f2 y = ff_mul(P, f2{tj.x, tj.y});
+    const float sc = __int_as_float((m + 127) << 23);
+    return {__fmul_rn(y.hi, sc), __fmul_rn(y.lo, sc)};
+}
+
+// 2T F(x1, x2) in float-float from the reduced energies (x = e/2T, the same
+// branches and identities as bubble_F2T): d = x1 - x2,
+//   near (|d| <= 1/16):  v1 v2 (2 sinhc d) / ((1+u1)(1+u2))
+//   far:                 s [u2 - u1 | 1 - u1 u2] / ((1+u1)(1+u2) d)
+// 2 sinhc d = 2 + d^2/3 + d^4/60 + d^6/2520 + d^8/181440 (next term < 5e-20
+// at |d| = 1/16), the d^2/3 term in float-float.
+__device__ __forceinline__ f2 bubble_F2T_ff(f2 x1, f2 x2, const float2* tab)
+{
+    const f2 d = ff_sub(x1, x2);
+    const bool neg1 = x1.hi < 0.0f, neg2 = x2.hi < 0.0f;
+    const f2 v1 = ff_exp_neg(neg1 ? ff_neg(x1) : x1, tab);
+    const f2 v2 = ff_exp_neg(neg2 ? ff_neg(x2) : x2, tab);
+    const f2 u1 = ff_sqr(v1), u2 = ff_sqr(v2);
+    const f2 p = ff_mul(ff_one_plus(u1), ff_one_plus(u2));
+    const bool same = neg1 == neg2;
+    const f2 u12 = ff_mul(u1, u2);
+    f2 num = ff_sub(same ? u2 : f2{1.0f, 0.0f}, same ? u1 : u12);
+    if (neg1) num = ff_neg(num);
+    f2 den = ff_mul(p, d);
+    const bool near = fabsf(d.hi) <= 0.0625f;
+    if (__any_sync(__activemask(), near)) {
+        const f2 d2 = ff_sqr(d);
+        const float g = d2.hi;
+        const float tail = __fmul_rn(__fmul_rn(g, g),
+                                     fmaf(g, fmaf(g, 1.0f / 181440.0f, 1.0f / 2520.0f), 1.0f / 60.0f));
+        const f2 third = ff_mul(d2, f2{0.3333333432674408f, -9.934107758624577e-09f});
+        const f2 S = ff_add(f2{2.0f, 0.0f}, ff_fast(third.hi, __fadd_rn(third.lo, tail)));
+        if (near) {
+            num = ff_mul(ff_mul(v1, v2), S);
+            den = p;
+        }
+    }
+    return ff_div(num, den);
+}
+
+// Omega derivative of the flow kinds' frequency integrals in float-float (the
+// same formulas as flow_Fdot; e1, e2 energies, W = Omega as float-float).
+__device__ __forceinline__ f2 flow_Fdot_ff(f2 e1, f2 e2, f2 W, bool pp)
+{
+    if (pp) e2 = ff_neg(e2);
+    const bool n1 = e1.hi < 0.0f, n2 = e2.hi < 0.0f;
+    const f2 a1 = n1 ? ff_neg(e1) : e1, a2 = n2 ? ff_neg(e2) : e2;
+    const f2 u1 = ff_add(a1, W), u2 = ff_add(a2, W);
+    const f2 P = ff_mul(u1, u2), S = ff_add(u1, u2);
+    f2 num, den;
+    if (n1 == n2) {
+        // -3 P^2 + W (5 S P - 2 W (S^2 - P))
+        const f2 inner = ff_sub(ff_mul(ff_mul(f2{5.0f, 0.0f}, S), P),
+                                ff_mul(ff_mul(f2{2.0f, 0.0f}, W), ff_sub(ff_sqr(S), P)));
+        num = ff_sub(ff_mul(W, inner), ff_mul(f2{3.0f, 0.0f}, ff_sqr(P)));
+        den = ff_mul(f2{4.0f, 0.0f}, ff_mul(P, ff_sqr(P)));
+    } else {
+        const f2 u13 = ff_mul(u1, ff_sqr(u1)), u23 = ff_mul(u2, ff_sqr(u2));
+        const f2 g1 = ff_mul(e1, ff_add(ff_mul(f2{3.0f, 0.0f}, a1), W));
+        const f2 g2 = ff_mul(e2, ff_add(ff_mul(f2{3.0f, 0.0f}, a2), W));
+        num = ff_sub(ff_mul(g1, u23), ff_mul(g2, u13));
+        den = ff_mul(ff_mul(f2{4.0f, 0.0f}, ff_mul(u13, u23)), ff_sub(e1, e2));
+    }
+    const f2 D = ff_div(num, den);
+    return pp ? ff_neg(D) : D;
+}
+
+// Diagnostics for paid_check_math: which = 0: exp_neg(x), 1: div_nr(x, y),
+// 2: ff_exp_neg(x) (x rounded to float-float), 3: bubble_F2T_ff(x, y),
+// 4: bubble_F2T(x, y) (FP64), 5: flow_Fdot_ff(x, y) with Omega = 0.1 (ph),
+// 6: flow_Fdot(x, y) with Omega = 0.1 (ph).
 __global__ void k_check_math(int which, int64_t n, const double* x, const double* y, double* out)
 {
     __shared__ double tab[64];
-    if (threadIdx.x < 64) tab[threadIdx.x] = c_exp2d[threadIdx.x];
+    __shared__ float2 tabf[64];
+    if (threadIdx.x < 64) {
+        tab[threadIdx.x] = c_exp2d[threadIdx.x];
+        const f2 a = ff_from(c_exp2d[threadIdx.x]);
+        tabf[threadIdx.x] = make_float2(a.hi, a.lo);
+    }
     __syncthreads();
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = which == 0 ? exp_neg(x[i], tab) : div_nr(x[i], y[i]);
+    switch (which) {
+    case 0: out[i] = exp_neg(x[i], tab); break;
+    case 1: out[i] = div_nr(x[i], y[i]); break;
+    case 2: out[i] = ff_to(ff_exp_neg(ff_from(x[i]), tabf)); break;
+    case 3: out[i] = ff_to(bubble_F2T_ff(ff_from(x[i]), ff_from(y[i]), tabf)); break;
+    case 4: out[i] = bubble_F2T(x[i], y[i], tab); break;
+    case 5: out[i] = ff_to(flow_Fdot_ff(ff_from(x[i]), ff_from(y[i]), ff_from(0.1), false)); break;
+    default: out[i] = flow_Fdot(x[i], y[i], 0.1, false); break;
+    }
 }
 
 cudaError_t launch_check_math(int which, int64_t n, const double* x, const double* y, double* out,
@@ -1007,19 +1230,81 @@ struct GroupSmem {
     double tab[64];          // 2^(j/64)
 };
 
+// The FP32-pipe variant: every per-node and per-row quantity in float-float,
+// the column data with the column's rule weight folded in (fine, and coarse on
+// the even columns); the moments reuse the column data's memory once the row
+// sums are done.
 template <int N>
+struct GroupSmemF {
+    static constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
+    float2 X[R][NF][9];          // X_ac at the fine rows
+    union {
+        struct {
+            float2 Yf[R][NF][9];     // wf_j Y_bd(y_j)
+            float2 Yc[R][N + 1][9];  // wc_j Y_bd(y_2j)
+            float2 CY[R][NF][2];     // cos ky, cos ky' (flow kinds: cos(ky +- qy/2))
+        } c;
+        struct {
+            double Mf[R][9][9];
+            double Mc[R][9][9];
+        } m;
+    } u;
+    float2 Rf[R][NF][9];         // row sums with the row's fine weight
+    float2 Rc[R][N + 1][9];      // coarse (even rows)
+    double C[R][4];
+    float2 tab[64];              // 2^(j/64) as float-float
+    float2 wr[NF];               // fine row weights, float-float
+    float2 wrc[N + 1];           // coarse row weights
+};
+
+template <int N>
+__device__ __forceinline__ auto& group_Mf(GroupSmem<N>& S) { return S.Mf; }
+template <int N>
+__device__ __forceinline__ auto& group_Mc(GroupSmem<N>& S) { return S.Mc; }
+template <int N>
+__device__ __forceinline__ auto& group_Mf(GroupSmemF<N>& S) { return S.u.m.Mf; }
+template <int N>
+__device__ __forceinline__ auto& group_Mc(GroupSmemF<N>& S) { return S.u.m.Mc; }
+
+template <int N, int PREC>
+using GroupSmemOf = typename std::conditional<PREC == 0, GroupSmem<N>, GroupSmemF<N>>::type;
+
+__device__ __forceinline__ f2 ff_ld(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 ff_st(f2 a) { return make_float2(a.hi, a.lo); }
+
+// PREC 0: everything FP64.  PREC 1 (options.eval_fp32): the kernel F, the row
+// sums and the moments in float-float on the FP32 pipe; each region's pair
+// values Q_2N, Q_N, their difference and every total in FP64.
+template <int N, int PREC>
 __global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1))
 k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
 {
     constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GroupSmem<N>& S = *reinterpret_cast<GroupSmem<N>*>(smem_raw);
+    using Smem = GroupSmemOf<N, PREC>;
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     const int v = rule_variant(N);
     const int cur = w.ls->cur;
     const int64_t n_eval = w.ls->n_eval;
     const int rho = threadIdx.x / NF, i = threadIdx.x % NF;
     const double tA = -2.0 * lat.t, tB = -4.0 * lat.tp;
-    if (threadIdx.x < 64) S.tab[threadIdx.x] = c_exp2d[threadIdx.x];
+    if constexpr (PREC == 0) {
+        if (threadIdx.x < 64) S.tab[threadIdx.x] = c_exp2d[threadIdx.x];
+    } else {
+        if (threadIdx.x < 64) {
+            const double x = c_exp2d[threadIdx.x];
+            const float h = __double2float_rn(x);
+            S.tab[threadIdx.x] = make_float2(h, __double2float_rn(x - double(h)));
+        }
+        if (threadIdx.x < NF) {
+            const f2 a = ff_from(c_wf[v][threadIdx.x]);
+            S.wr[threadIdx.x] = make_float2(a.hi, a.lo);
+        }
+        if (threadIdx.x <= N) {
+            const f2 a = ff_from(c_wc[v][threadIdx.x]);
+            S.wrc[threadIdx.x] = make_float2(a.hi, a.lo);
+        }
+    }
     for (int64_t chunk = blockIdx.x; chunk * R < n_eval; chunk += gridDim.x) {
         const int64_t t = chunk * R + rho;
         const bool live = t < n_eval;
@@ -1063,27 +1348,66 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
             // flow kinds: both form factors at k (symmetric routing)
             const double gx[3] = {1.0, cx, sx};
             const double gx2[3] = {1.0, flow ? cx : cx2, flow ? sx : sx2};
-            const double gy[3] = {1.0, cy, sy};
-            const double gy2[3] = {1.0, flow ? cy : cy2, flow ? sy : sy2};
+            if constexpr (PREC == 1) {
+                const f2 one = {1.0f, 0.0f};
+                const f2 fcx = ff_from(cx), fsx = ff_from(sx);
+                const f2 fx[3] = {one, fcx, fsx};
+                const f2 fx2[3] = {one, flow ? fcx : ff_from(cx2), flow ? fsx : ff_from(sx2)};
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+                for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    S.X[rho][i][3 * a + c] = gx[a] * gx2[c];
-                    S.Y[rho][i][3 * a + c] = gy[a] * gy2[c];
-                }
+                    for (int c = 0; c < 3; ++c)
+                        S.X[rho][i][3 * a + c] =
+                            ff_st(a == 0 ? fx2[c] : (c == 0 ? fx[a] : ff_mul(fx[a], fx2[c])));
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) S.X[rho][i][3 * a + c] = gx[a] * gx2[c];
+            }
+            if constexpr (PREC == 0) {
+                const double gy[3] = {1.0, cy, sy};
+                const double gy2[3] = {1.0, flow ? cy : cy2, flow ? sy : sy2};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) S.Y[rho][i][3 * a + c] = gy[a] * gy2[c];
+            } else {
+                // Y_bd(y_i) in float-float, times the column's fine and coarse weights
+                const f2 one = {1.0f, 0.0f};
+                const f2 fcy = ff_from(cy), fsy = ff_from(sy);
+                const f2 gy[3] = {one, fcy, fsy};
+                const f2 gy2[3] = {one, flow ? fcy : ff_from(cy2), flow ? fsy : ff_from(sy2)};
+                const float2 wj = S.wr[i];
+                const f2 wf = {wj.x, wj.y};
+                f2 wc = {0.0f, 0.0f};
+                if ((i & 1) == 0) { const float2 c = S.wrc[i >> 1]; wc = {c.x, c.y}; }
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const f2 y = (a == 0) ? gy2[c] : (c == 0 ? gy[a] : ff_mul(gy[a], gy2[c]));
+                        const f2 yf = ff_mul(wf, y);
+                        S.u.c.Yf[rho][i][3 * a + c] = make_float2(yf.hi, yf.lo);
+                        if ((i & 1) == 0) {
+                            const f2 yc = ff_mul(wc, y);
+                            S.u.c.Yc[rho][i >> 1][3 * a + c] = make_float2(yc.hi, yc.lo);
+                        }
+                    }
+            }
+            double cy_a, cy_b;
             if (flow) {
                 // e(k + q/2) and e(k - q/2): cos(k +- q/2) = cos k cos q/2 -+ sin k sin q/2
                 const double cxp = fma(cx, tq.cqx, -sx * tq.sqx), cxm = fma(cx, tq.cqx, sx * tq.sqx);
-                S.CY[rho][i][0] = fma(cy, tq.cqy, -sy * tq.sqy);
-                S.CY[rho][i][1] = fma(cy, tq.cqy, sy * tq.sqy);
+                cy_a = fma(cy, tq.cqy, -sy * tq.sqy);
+                cy_b = fma(cy, tq.cqy, sy * tq.sqy);
                 A1 = fma(tA, cxp, -lat.mu);
                 B1 = fma(tB, cxp, tA);
                 A2 = fma(tA, cxm, -lat.mu);
                 B2 = fma(tB, cxm, tA);
             } else {
-                S.CY[rho][i][0] = cy;
-                S.CY[rho][i][1] = cy2;
+                cy_a = cy;
+                cy_b = cy2;
                 // x = e / 2T = A + B cos ky along row i, for k and for k' (for pp
                 // the second energy enters with its sign flipped)
                 const double h1 = B->inv2T, h2 = pp ? -B->inv2T : B->inv2T;
@@ -1092,55 +1416,128 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 A2 = fma(tA, cx2, -lat.mu) * h2;
                 B2 = fma(tB, cx2, tA) * h2;
             }
+            if constexpr (PREC == 0) {
+                S.CY[rho][i][0] = cy_a;
+                S.CY[rho][i][1] = cy_b;
+            } else {
+                const f2 a = ff_from(cy_a), b = ff_from(cy_b);
+                S.u.c.CY[rho][i][0] = make_float2(a.hi, a.lo);
+                S.u.c.CY[rho][i][1] = make_float2(b.hi, b.lo);
+            }
         }
         __syncthreads();
         if (live) {
-            double rf[9], rc[9];
+            if constexpr (PREC == 0) {
+                double rf[9], rc[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) { rf[k] = 0.0; rc[k] = 0.0; }
+                for (int k = 0; k < 9; ++k) { rf[k] = 0.0; rc[k] = 0.0; }
 #pragma unroll
-            for (int j = 0; j < NF; ++j) {
-                // OVERLAP: 1; bubbles: 2T F (1/2T is in the Jacobian); flow: dF/dOmega
-                double F = 1.0;
-                const double x1 = fma(B1, S.CY[rho][j][0], A1);
-                const double x2 = fma(B2, S.CY[rho][j][1], A2);
-                if (is_flow(kind))
-                    F = flow_Fdot(x1, x2, B->T, kind == FLOW_PP);
-                else if (kind != OVERLAP)
-                    F = bubble_F2T(x1, x2, S.tab);
-                const double wf = c_wf[v][j] * F;
+                for (int j = 0; j < NF; ++j) {
+                    // OVERLAP: 1; bubbles: 2T F (1/2T is in the Jacobian); flow: dF/dOmega
+                    double F = 1.0;
+                    const double x1 = fma(B1, S.CY[rho][j][0], A1);
+                    const double x2 = fma(B2, S.CY[rho][j][1], A2);
+                    if (is_flow(kind))
+                        F = flow_Fdot(x1, x2, B->T, kind == FLOW_PP);
+                    else if (kind != OVERLAP)
+                        F = bubble_F2T(x1, x2, S.tab);
+                    const double wf = c_wf[v][j] * F;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) rf[k] = fma(wf, S.Y[rho][j][k], rf[k]);
-                if ((j & 1) == 0) {
-                    const double wc = c_wc[v][j >> 1] * F;
+                    for (int k = 0; k < 9; ++k) rf[k] = fma(wf, S.Y[rho][j][k], rf[k]);
+                    if ((j & 1) == 0) {
+                        const double wc = c_wc[v][j >> 1] * F;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) rc[k] = fma(wc, S.Y[rho][j][k], rc[k]);
+                        for (int k = 0; k < 9; ++k) rc[k] = fma(wc, S.Y[rho][j][k], rc[k]);
+                    }
                 }
-            }
-            // the row's own rule weight (fine, and coarse on the even rows)
-            // goes into its sums, so the moments below are plain dot products
-            const double wr = c_wf[v][i];
+                // the row's own rule weight (fine, and coarse on the even rows)
+                // goes into its sums, so the moments below are plain dot products
+                const double wr = c_wf[v][i];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = wr * rf[k];
-            if ((i & 1) == 0) {
-                const double wrc = c_wc[v][i >> 1];
+                for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = wr * rf[k];
+                if ((i & 1) == 0) {
+                    const double wrc = c_wc[v][i >> 1];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) S.Rc[rho][i >> 1][k] = wrc * rc[k];
+                    for (int k = 0; k < 9; ++k) S.Rc[rho][i >> 1][k] = wrc * rc[k];
+                }
+            } else {
+                const f2 fA1 = ff_from(A1), fB1 = ff_from(B1), fA2 = ff_from(A2), fB2 = ff_from(B2);
+                const f2 W = ff_from(B->T);
+                f2 rf[9], rc[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) { rf[k] = {0.0f, 0.0f}; rc[k] = {0.0f, 0.0f}; }
+                // one node (i, j): the kernel F once, then every row sum
+                auto node = [&](int j, bool even) {
+                    const f2 x1 = ff_fma(fB1, ff_ld(S.u.c.CY[rho][j][0]), fA1);
+                    const f2 x2 = ff_fma(fB2, ff_ld(S.u.c.CY[rho][j][1]), fA2);
+                    f2 F = {1.0f, 0.0f};
+                    if (is_flow(kind))
+                        F = flow_Fdot_ff(x1, x2, W, kind == FLOW_PP);
+                    else if (kind != OVERLAP)
+                        F = bubble_F2T_ff(x1, x2, S.tab);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yf[rho][j][k]), rf[k]);
+                    if (even) {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yc[rho][j >> 1][k]), rc[k]);
+                    }
+                };
+                // two columns per trip (even, then odd) keeps the coarse-rule
+                // columns static without unrolling all 2N+1 nodes of the row:
+                // the float-float node is ~400 instructions, and a fully
+                // unrolled row overflows the instruction cache
+#pragma unroll 1
+                for (int j = 0; j < 2 * N; j += 2) {
+                    node(j, true);
+                    node(j + 1, false);
+                }
+                node(2 * N, true);
+                // the row weight in float-float; one value per sum
+                const f2 wr = ff_ld(S.wr[i]);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const f2 r = ff_mul(wr, ff_fast(rf[k].hi, rf[k].lo));
+                    S.Rf[rho][i][k] = ff_st(r);
+                }
+                if ((i & 1) == 0) {
+                    const f2 wrc = ff_ld(S.wrc[i >> 1]);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const f2 r = ff_mul(wrc, ff_fast(rc[k].hi, rc[k].lo));
+                        S.Rc[rho][i >> 1][k] = ff_st(r);
+                    }
+                }
             }
         }
         __syncthreads();
+        auto& Mf = group_Mf(S);
+        auto& Mc = group_Mc(S);
         if (live) {
             // moments M[ac][bd]: the 81 (ac, bd) cells dealt over the region's
             // NF threads (all of them busy, rather than one thread per ac)
             for (int u = i; u < 81; u += NF) {
                 const int ac = u / 9, bd = u - 9 * (u / 9);
-                double mf = 0.0, mc = 0.0;
+                if constexpr (PREC == 1) {
+                    // float-float dot products on the FP32 pipe, one FP64 value each
+                    f2 mf = {0.0f, 0.0f}, mc = {0.0f, 0.0f};
 #pragma unroll
-                for (int r = 0; r < NF; ++r) mf = fma(S.X[rho][r][ac], S.Rf[rho][r][bd], mf);
+                    for (int r = 0; r < NF; ++r)
+                        ff_acc(ff_ld(S.X[rho][r][ac]), ff_ld(S.Rf[rho][r][bd]), mf);
 #pragma unroll
-                for (int r = 0; r <= N; ++r) mc = fma(S.X[rho][2 * r][ac], S.Rc[rho][r][bd], mc);
-                S.Mf[rho][ac][bd] = mf;
-                S.Mc[rho][ac][bd] = mc;
+                    for (int r = 0; r <= N; ++r)
+                        ff_acc(ff_ld(S.X[rho][2 * r][ac]), ff_ld(S.Rc[rho][r][bd]), mc);
+                    Mf[rho][ac][bd] = ff_to(ff_fast(mf.hi, mf.lo));
+                    Mc[rho][ac][bd] = ff_to(ff_fast(mc.hi, mc.lo));
+                } else {
+                    double mf = 0.0, mc = 0.0;
+#pragma unroll
+                    for (int r = 0; r < NF; ++r) mf = fma(S.X[rho][r][ac], S.Rf[rho][r][bd], mf);
+#pragma unroll
+                    for (int r = 0; r <= N; ++r)
+                        mc = fma(S.X[rho][2 * r][ac], S.Rc[rho][r][bd], mc);
+                    Mf[rho][ac][bd] = mf;
+                    Mc[rho][ac][bd] = mc;
+                }
             }
         }
         __syncthreads();
@@ -1156,8 +1553,8 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                             const double c = c_ffc[l][k1] * c_ffc[m][k2];
                             const int ac = 3 * c_ffa[l][k1] + c_ffa[m][k2];
                             const int bd = 3 * c_ffb[l][k1] + c_ffb[m][k2];
-                            q2 = fma(c, S.Mf[rho][ac][bd], q2);
-                            q1 = fma(c, S.Mc[rho][ac][bd], q1);
+                            q2 = fma(c, Mf[rho][ac][bd], q2);
+                            q1 = fma(c, Mc[rho][ac][bd], q1);
                         }
                 }
                 q2 *= scale;
@@ -1176,45 +1573,61 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
     }
 }
 
-template <int N>
+template <int N, int PREC>
 static cudaError_t group_attr()
 {
-    return cudaFuncSetAttribute(k_eval_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(sizeof(GroupSmem<N>)));
+    return cudaFuncSetAttribute(k_eval_group<N, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(sizeof(GroupSmemOf<N, PREC>)));
+}
+
+template <int PREC>
+static cudaError_t group_prec_attrs()
+{
+    cudaError_t e = group_attr<4, PREC>();
+    if (e == cudaSuccess) e = group_attr<6, PREC>();
+    if (e == cudaSuccess) e = group_attr<8, PREC>();
+    if (e == cudaSuccess) e = group_attr<10, PREC>();
+    if (e == cudaSuccess) e = group_attr<12, PREC>();
+    return e;
 }
 
 static cudaError_t group_kernel_attributes()
 {
-    cudaError_t e = group_attr<4>();
-    if (e == cudaSuccess) e = group_attr<6>();
-    if (e == cudaSuccess) e = group_attr<8>();
-    if (e == cudaSuccess) e = group_attr<10>();
-    if (e == cudaSuccess) e = group_attr<12>();
+    cudaError_t e = group_prec_attrs<0>();
+    if (e == cudaSuccess) e = group_prec_attrs<1>();
     return e;
 }
 
-template <int N>
+template <int N, int PREC>
 static void group_launch(const Work& w, int64_t hint_eval, int64_t cap, Lattice lat, cudaStream_t s,
                          double* rule_q2, double* rule_d)
 {
     constexpr int R = GroupShape<N>::R;
     const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, cap);
-    k_eval_group<N><<<int(blocks), R * (2 * N + 1), sizeof(GroupSmem<N>), s>>>(w, lat, rule_q2,
-                                                                               rule_d);
+    k_eval_group<N, PREC><<<int(blocks), R * (2 * N + 1), sizeof(GroupSmemOf<N, PREC>), s>>>(
+        w, lat, rule_q2, rule_d);
 }
 
-cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Lattice lat,
+template <int PREC>
+static void group_dispatch(const Work& w, int64_t hint_eval, int rule_n, int64_t cap, Lattice lat,
+                           cudaStream_t s, double* rule_q2, double* rule_d)
+{
+    switch (rule_n) {
+    case 4: group_launch<4, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    case 6: group_launch<6, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    case 8: group_launch<8, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    case 10: group_launch<10, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    default: group_launch<12, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
+    }
+}
+
+cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,
                               cudaStream_t s, double* rule_q2, double* rule_d, int max_blocks)
 {
     if (hint_eval <= 0) return cudaSuccess;
     const int64_t cap = max_blocks > 0 ? max_blocks : 152 * 32;
-    switch (rule_n) {
-    case 4: group_launch<4>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    case 6: group_launch<6>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    case 8: group_launch<8>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    case 10: group_launch<10>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    default: group_launch<12>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    }
+    if (fp32) group_dispatch<1>(w, hint_eval, rule_n, cap, lat, s, rule_q2, rule_d);
+    else      group_dispatch<0>(w, hint_eval, rule_n, cap, lat, s, rule_q2, rule_d);
     return cudaGetLastError();
 }
 

@@ -180,7 +180,9 @@ struct Work {
     double* vval[2];
     float* verr[2];
     uint32_t* vsrc;            // per next-pool slot: the region it copies (~0u: a new child)
-    float* gmap;               // per group: the seed map (256 cells), see launch_group_map
+    float* tmap;               // with options.trace: per unit the level of the coarsest
+                               // region meeting each level-4 cell (256 entries), the
+                               // caller's buffer; null otherwise
     // per active slot, temporaries of the group reduce: chunk sums of V and E
     // ([slot][chunk][2][81]), V and E ([slot][2][81]), 1/tol of the pairs not
     // yet converged ([slot][81]), chunk score sum and max ([slot][chunk][2]),
@@ -205,11 +207,13 @@ cudaError_t init_rule_tables(int device);
 // given, is recorded between the two
 cudaError_t launch_eval(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,
                         cudaStream_t s, cudaEvent_t mid = nullptr);
-// group mode: every pair of every region on the eval list (FP64).  With
-// rule_q2 / rule_d non-null, entry t's Q_2N and Q_N - Q_2N (times the region's
-// Jacobian) go to rule_q2 / rule_d[t * npairs + pair] instead of the pool.
-// max_blocks > 0 caps the grid (the kernel is grid-stride), else 152 x 32
-cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, Lattice lat,
+// group mode: every pair of every region on the eval list; fp32 = 0: FP64,
+// 1: the kernel F and the row sums in float-float on the FP32 pipe, moments
+// and pair values FP64.  With rule_q2 / rule_d non-null, entry t's Q_2N and
+// Q_N - Q_2N (times the region's Jacobian) go to rule_q2 / rule_d[t * npairs +
+// pair] instead of the pool.  max_blocks > 0 caps the grid (the kernel is
+// grid-stride), else 152 x 32
+cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,
                               cudaStream_t s, double* rule_q2 = nullptr, double* rule_d = nullptr,
                               int max_blocks = 0);
 // which = 0: the group kernel's exp(-x); 1: its division x / y (diagnostics)
@@ -239,12 +243,15 @@ cudaError_t launch_rule_flag(const uint32_t* bad, int nreg, int npairs, double* 
                              cudaStream_t s);
 // the admission wave chosen by the last control step (w.ls->wave_*)
 cudaError_t launch_setup_wave(const Work& w, int64_t hint_wave, int nff, int fp64, cudaStream_t s);
-// pass 0: region counts into cnt_new / cnt_eval (slot = integral); pass 1 (after
-// launch_scan): keys, eval list, segments.  proposal null = uniform level 4.
-cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s);
-// group mode: each group's seed map = the cell-wise largest predicted error
-// over its pairs' maps (proposal [n_integrals][256], global integral order)
-cudaError_t launch_group_map(const Work& w, const float* proposal, cudaStream_t s);
+// pass 0: region counts into cnt_new / cnt_eval (slot = unit); pass 1 (after
+// launch_scan): keys, eval list, segments.  proposal: per unit a 16 x 16 map
+// of predicted levels of the coarsest final region per level-4 cell, seeded
+// at floor(level - margin); null = uniform level 4.
+cudaError_t launch_seed(const Work& w, const float* proposal, double margin, int pass,
+                        cudaStream_t s);
+// with w.tmap: every active unit's current partition as a level map (after
+// the round's test, before the split)
+cudaError_t launch_trace(const Work& w, int64_t hint_active, cudaStream_t s);
 cudaError_t launch_features(int kind, int nq, const double* q, int npairs, const int32_t* lm,
                             double T, double mu, double tp, void* x, cudaStream_t s);
 cudaError_t launch_cell_map(const Work& w, float* out, cudaStream_t s);

@@ -15,8 +15,12 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "../../include/paid.h"
 
@@ -321,6 +325,113 @@ cudaError_t forward(const float* params, const __nv_bfloat16* x, int64_t M, floa
     return cudaSuccess;
 }
 
+// MSE gradient of M rows into grad (zeroed first) and loss (zeroed first).
+cudaError_t grad_rows(const float* params, const __nv_bfloat16* xb, const float* target, int64_t M,
+                      float* grad, float* loss, MlpWork& w, cudaStream_t s)
+{
+    if (forward(params, xb, M, nullptr, w, s) != cudaSuccess) return cudaErrorLaunchFailure;
+    const int64_t nout = M * kHid;
+    const int tb = 256;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(grad, 0, sizeof(float) * param_count(), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(loss, 0, sizeof(float), s)) != cudaSuccess)
+        return e;
+    k_mse<<<int((nout + tb - 1) / tb), tb, 0, s>>>(w.pre[kLayers - 1], target, nout,
+                                                   1.0f / float(nout), w.dy, loss);
+    const __nv_bfloat16* d = w.dy;   // gradient w.r.t. the current layer's pre-activation
+    const int splits = int(std::min<int64_t>(64, (M + 1023) / 1024));
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int K = layer_k(l);
+        const __nv_bfloat16* in = l == 0 ? xb : w.h[l - 1];
+        float* gW = grad + layer_w_off(l);
+        float* gb = gW + int64_t(K) * kHid;
+        // dW[k][n] = sum_m in[m][k] d[m][n]:  A(k, m) = in[m K + k], B(m, n) = d[m 256 + n]
+        if ((e = gemm<EPI_ATOMIC>(K, kHid, int(M), in, 1, K, d, kHid, 1, nullptr, gW, kHid,
+                                  nullptr, splits, s)) != cudaSuccess)
+            return e;
+        dim3 gbg((kHid + 127) / 128, int((M + 255) / 256));
+        k_bias_grad<<<gbg, 128, 0, s>>>(d, int(M), kHid, gb);
+        if (l == 0) break;
+        // dh[m][k] = sum_n d[m][n] W_l[k][n]:  B(n, k) = W_l[k][n] = w[k 256 + n]
+        if ((e = gemm<EPI_STORE>(int(M), K, kHid, d, kHid, 1, w.w + wofs(l), 1, kHid, nullptr,
+                                 w.dh, K, nullptr, 1, s)) != cudaSuccess)
+            return e;
+        k_gelu_back<<<int((M * K + tb - 1) / tb), tb, 0, s>>>(w.dh, w.pre[l - 1], M * K, w.da);
+        // the next step reads da while this one's d may alias it: swap buffers
+        d = w.da;
+        if (l - 1 > 0) {
+            // keep d in da, use dy as the next gradient buffer
+            __nv_bfloat16* t = w.dy;
+            w.dy = w.da;
+            w.da = t;
+        }
+    }
+    return cudaGetLastError();
+}
+
+// rows perm[r0 .. r0 + n) of x and target into xb, tb
+__global__ void k_gather_rows(const __nv_bfloat16* __restrict__ x, const float* __restrict__ t,
+                              const int32_t* __restrict__ perm, int64_t r0, int64_t n,
+                              __nv_bfloat16* __restrict__ xb, float* __restrict__ tb)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n * kHid) return;
+    const int64_t r = i / kHid, c = i % kHid;
+    const int64_t src = perm[r0 + r];
+    tb[i] = t[src * kHid + c];
+    if (c < kIn) xb[r * kIn + c] = x[src * kIn + c];
+}
+
+// AdamW with bias corrections for step k (counting from 1)
+cudaError_t adamw_step(float* params, const float* grad, float* m, float* v, int step, float lr,
+                       float weight_decay, cudaStream_t s)
+{
+    const int64_t n = param_count();
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, float(step)), c2 = 1.0f - powf(b2, float(step));
+    k_adamw<<<int((n + 255) / 256), 256, 0, s>>>(params, grad, m, v, n, lr, b1, b2, 1e-8f,
+                                                 weight_decay, c1, c2);
+    return cudaGetLastError();
+}
+
+// Workspace of paid_proposal_train: the permutation, one minibatch of inputs
+// and targets, the per-step losses of an epoch, the gradient and the forward /
+// backward buffers of one minibatch.
+struct TrainWork {
+    int32_t* perm;
+    __nv_bfloat16* xb;
+    float* tb;
+    float* losses;
+    float* grad;
+    char* mlp;
+};
+
+size_t train_work_bytes(int64_t M, int64_t batch, TrainWork* t, char* base)
+{
+    size_t o = 0;
+    auto take = [&](size_t b) { size_t at = o; o = align256(o + b); return base ? base + at : nullptr; };
+    const int64_t steps = (M + batch - 1) / batch;
+    char* p;
+    p = take(sizeof(int32_t) * M); if (t) t->perm = (int32_t*)p;
+    p = take(sizeof(__nv_bfloat16) * batch * kIn); if (t) t->xb = (__nv_bfloat16*)p;
+    p = take(sizeof(float) * batch * kHid); if (t) t->tb = (float*)p;
+    p = take(sizeof(float) * steps); if (t) t->losses = (float*)p;
+    p = take(sizeof(float) * param_count()); if (t) t->grad = (float*)p;
+    p = take(mlp_work_bytes(batch, nullptr, nullptr)); if (t) t->mlp = p;
+    return o;
+}
+
+// splitmix64 (Steele, Lea and Flood), the seeded source of the minibatch order
+uint64_t splitmix64(uint64_t& z)
+{
+    uint64_t r = (z += 0x9e3779b97f4a7c15ull);
+    r = (r ^ (r >> 30)) * 0xbf58476d1ce4e5b9ull;
+    r = (r ^ (r >> 27)) * 0x94d049bb133111ebull;
+    return r ^ (r >> 31);
+}
+
+constexpr char kMagic[8] = {'P', 'A', 'I', 'D', 'M', 'L', 'P', '1'};
+
 }  // namespace
 
 extern "C" {
@@ -369,56 +480,123 @@ int paid_mlp_grad(const float* params, const uint16_t* x, const float* target, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MlpWork w;
     mlp_work_bytes(M, &w, static_cast<char*>(workspace));
-    const __nv_bfloat16* xb = reinterpret_cast<const __nv_bfloat16*>(x);
-    if (forward(params, xb, M, nullptr, w, s) != cudaSuccess) return PAID_ERR_CUDA;
-    const int64_t nout = M * kHid;
-    const int tb = 256;
-    if (cudaMemsetAsync(grad, 0, sizeof(float) * param_count(), s) != cudaSuccess ||
-        cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess)
-        return PAID_ERR_CUDA;
-    k_mse<<<int((nout + tb - 1) / tb), tb, 0, s>>>(w.pre[kLayers - 1], target, nout,
-                                                   1.0f / float(nout), w.dy, loss);
-    const __nv_bfloat16* d = w.dy;   // gradient w.r.t. the current layer's pre-activation
-    const int splits = int(std::min<int64_t>(64, (M + 1023) / 1024));
-    for (int l = kLayers - 1; l >= 0; --l) {
-        const int K = layer_k(l);
-        const __nv_bfloat16* in = l == 0 ? xb : w.h[l - 1];
-        float* gW = grad + layer_w_off(l);
-        float* gb = gW + int64_t(K) * kHid;
-        // dW[k][n] = sum_m in[m][k] d[m][n]:  A(k, m) = in[m K + k], B(m, n) = d[m 256 + n]
-        if (gemm<EPI_ATOMIC>(K, kHid, int(M), in, 1, K, d, kHid, 1, nullptr, gW, kHid, nullptr,
-                             splits, s) != cudaSuccess)
-            return PAID_ERR_CUDA;
-        dim3 gbg((kHid + 127) / 128, int((M + 255) / 256));
-        k_bias_grad<<<gbg, 128, 0, s>>>(d, int(M), kHid, gb);
-        if (l == 0) break;
-        // dh[m][k] = sum_n d[m][n] W_l[k][n]:  B(n, k) = W_l[k][n] = w[k 256 + n]
-        if (gemm<EPI_STORE>(int(M), K, kHid, d, kHid, 1, w.w + wofs(l), 1, kHid, nullptr,
-                            w.dh, K, nullptr, 1, s) != cudaSuccess)
-            return PAID_ERR_CUDA;
-        k_gelu_back<<<int((M * K + tb - 1) / tb), tb, 0, s>>>(w.dh, w.pre[l - 1], M * K, w.da);
-        // the next step reads da while this one's d may alias it: swap buffers
-        d = w.da;
-        if (l - 1 > 0) {
-            // keep d in da, use dy as the next gradient buffer
-            __nv_bfloat16* t = w.dy;
-            w.dy = w.da;
-            w.da = t;
-        }
-    }
-    return cudaGetLastError() == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
+    return grad_rows(params, reinterpret_cast<const __nv_bfloat16*>(x), target, M, grad, loss, w,
+                     s) == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
 }
 
 int paid_mlp_adamw(float* params, const float* grad, float* m, float* v, int step, float lr,
                    float weight_decay, void* stream)
 {
     if (!params || !grad || !m || !v || step < 1) return PAID_ERR_ARG;
-    const int64_t n = param_count();
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.0f - powf(b1, float(step)), c2 = 1.0f - powf(b2, float(step));
-    k_adamw<<<int((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        params, grad, m, v, n, lr, b1, b2, 1e-8f, weight_decay, c1, c2);
+    return adamw_step(params, grad, m, v, step, lr, weight_decay,
+                      static_cast<cudaStream_t>(stream)) == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
+}
+
+int paid_proposal_train_workspace_size(int64_t M, int64_t batch, size_t* bytes)
+{
+    if (!bytes || M <= 0 || batch <= 0 || M > int64_t(0x7fffffff)) return PAID_ERR_ARG;
+    *bytes = train_work_bytes(M, std::min(M, batch), nullptr, nullptr);
+    return PAID_OK;
+}
+
+int paid_proposal_train(float* params, float* m, float* v, const uint16_t* x, const float* target,
+                        int64_t M, int epochs, int64_t batch, float lr, float weight_decay,
+                        uint64_t seed, int* step, float* epoch_loss, void* workspace,
+                        size_t ws_bytes, void* stream)
+{
+    if (!params || !m || !v || !x || !target || !step || *step < 0 || M <= 0 || epochs < 0 ||
+        batch <= 0 || M > int64_t(0x7fffffff) || !(lr >= 0.0f) || !(weight_decay >= 0.0f))
+        return PAID_ERR_ARG;
+    batch = std::min(M, batch);
+    if (!workspace || ws_bytes < train_work_bytes(M, batch, nullptr, nullptr)) return PAID_ERR_OOM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TrainWork t;
+    train_work_bytes(M, batch, &t, static_cast<char*>(workspace));
+    MlpWork w;
+    mlp_work_bytes(batch, &w, t.mlp);
+    const __nv_bfloat16* xb = reinterpret_cast<const __nv_bfloat16*>(x);
+    const int64_t steps = (M + batch - 1) / batch;
+    const int64_t total = steps * int64_t(epochs);
+    std::vector<int32_t> perm(static_cast<size_t>(M));
+    std::vector<float> losses(static_cast<size_t>(steps));
+    uint64_t z = seed;
+    int64_t k = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        // a fresh Fisher-Yates order of the rows for every epoch
+        for (int64_t i = 0; i < M; ++i) perm[size_t(i)] = int32_t(i);
+        for (int64_t i = M - 1; i > 0; --i) {
+            const int64_t j = int64_t(splitmix64(z) % uint64_t(i + 1));
+            std::swap(perm[size_t(i)], perm[size_t(j)]);
+        }
+        // the host order is copied before this call returns control (pageable
+        // source), so the vector may be refilled for the next epoch
+        if (cudaMemcpyAsync(t.perm, perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return PAID_ERR_CUDA;
+        for (int64_t b = 0; b < steps; ++b, ++k) {
+            const int64_t r0 = b * batch, n = std::min(batch, M - r0);
+            k_gather_rows<<<int((n * kHid + 255) / 256), 256, 0, s>>>(xb, target, t.perm, r0, n,
+                                                                     t.xb, t.tb);
+            // cosine decay of the learning rate over all steps of the call
+            const float a = lr * 0.5f * (1.0f + cosf(3.14159265358979f * float(k) /
+                                                     float(std::max<int64_t>(1, total))));
+            if (grad_rows(params, t.xb, t.tb, n, t.grad, t.losses + b, w, s) != cudaSuccess ||
+                adamw_step(params, t.grad, m, v, *step + 1, a, weight_decay, s) != cudaSuccess)
+                return PAID_ERR_CUDA;
+            ++*step;
+        }
+        if (epoch_loss) {
+            if (cudaMemcpyAsync(losses.data(), t.losses, sizeof(float) * steps,
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return PAID_ERR_CUDA;
+            double sum = 0.0;
+            for (float l : losses) sum += l;
+            epoch_loss[ep] = float(sum / double(steps));
+        }
+    }
     return cudaGetLastError() == cudaSuccess ? PAID_OK : PAID_ERR_CUDA;
+}
+
+int paid_proposal_save(const float* params, const char* path, void* stream)
+{
+    if (!params || !path) return PAID_ERR_ARG;
+    const int64_t n = param_count();
+    std::vector<float> h(static_cast<size_t>(n));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(h.data(), params, sizeof(float) * n, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PAID_ERR_CUDA;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return PAID_ERR_ARG;
+    const bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&n, sizeof(n), 1, f) == 1 &&
+                    std::fwrite(h.data(), sizeof(float), size_t(n), f) == size_t(n);
+    return (std::fclose(f) == 0 && ok) ? PAID_OK : PAID_ERR_ARG;
+}
+
+int paid_proposal_load(float* params, const char* path, void* stream)
+{
+    if (!params || !path) return PAID_ERR_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return PAID_ERR_ARG;
+    char magic[8] = {};
+    int64_t n = 0;
+    const int64_t want = param_count();
+    std::vector<float> h(static_cast<size_t>(want));
+    const bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+                    std::fread(&n, sizeof(n), 1, f) == 1 && n == want &&
+                    std::fread(h.data(), sizeof(float), size_t(n), f) == size_t(n) &&
+                    std::fgetc(f) == EOF;
+    std::fclose(f);
+    if (!ok) return PAID_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the host copy lives on this call's stack: wait for the upload
+    if (cudaMemcpyAsync(params, h.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PAID_ERR_CUDA;
+    return PAID_OK;
 }
 
 }  // extern "C"

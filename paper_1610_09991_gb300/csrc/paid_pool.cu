@@ -320,30 +320,35 @@ cudaError_t launch_rule_flag(const uint32_t* bad, int nreg, int npairs, double* 
 }
 
 // ---------------------------------------------------------------------------
-// Proposal-seeded initial partition.  For integral g the map gives t_c, the
-// predicted log10 error of level-4 cell c (c = 16 ix + iy) relative to the
-// integral's scale.  Cell c is split k_c = floor((t_c - b) / step) further
-// levels, b = log10(rel_tol / 256), step = rate log10 4, k_c in [-2, 3]; a
+// Proposal-seeded initial partition.  For unit g (an integral, or in group
+// mode a (kind, q) group) the map gives d_c, the predicted level of the
+// coarsest final region meeting level-4 cell c (c = 16 ix + iy) -- the map a
+// traced run records.  Cell c is seeded at level floor(d_c - margin), that is
+// k_c = floor(d_c - margin) - 4 levels below level 4, k_c in [-2, 3]; a
 // level-3 block whose four cells all have k <= -1 stays one region, and a
-// level-2 block whose 16 cells all have k <= -2 stays one region.  A seed of
-// more than max_regions / 2 regions falls back to the uniform level-2 grid.
-__device__ __forceinline__ int seed_k(const float* map, int c, float b, float inv_step)
+// level-2 block whose 16 cells all have k <= -2 stays one region.  With a
+// margin >= the map's error the seed regions are ancestors of (or equal to)
+// final regions, so seeding skips the evaluations of coarser regions without
+// ever evaluating a region the unseeded run would not.  A non-finite entry
+// counts as level 2.  A seed of more than max_regions / 2 regions falls back
+// to the uniform level-2 grid.
+__device__ __forceinline__ int seed_k(const float* map, int c, float margin)
 {
     if (!map) return 0;                          // uniform level-4 start
-    const float t = map[c];
-    if (!isfinite(t)) return 0;
-    return int(fminf(fmaxf(floorf((t - b) * inv_step), -2.0f), 3.0f));
+    const float d = map[c];
+    if (!isfinite(d)) return -2;
+    return int(fminf(fmaxf(floorf(d - margin) - 4.0f, -2.0f), 3.0f));
 }
 
 // regions emitted by level-2 block (bx, by) of integral g; with emit != null
 // writes them (keys and eval entries) starting at pool position p
-__device__ uint32_t seed_block(const float* map, int bx, int by, float b, float inv_step,
+__device__ uint32_t seed_block(const float* map, int bx, int by, float margin,
                               uint64_t* key, uint2* evl, unsigned long long p,
                               unsigned long long e, uint32_t g, bool emit)
 {
     int kmax2 = -2;
     for (int u = 0; u < 4; ++u)
-        for (int v = 0; v < 4; ++v) kmax2 = max(kmax2, seed_k(map, (4 * bx + u) * 16 + 4 * by + v, b, inv_step));
+        for (int v = 0; v < 4; ++v) kmax2 = max(kmax2, seed_k(map, (4 * bx + u) * 16 + 4 * by + v, margin));
     if (kmax2 <= -2) {
         if (emit) { key[p] = make_key(2, bx, by); evl[e] = make_uint2(uint32_t(p), g); }
         return 1;
@@ -355,7 +360,7 @@ __device__ uint32_t seed_block(const float* map, int bx, int by, float b, float 
             int k[4], kmax3 = -2;
             for (int u = 0; u < 2; ++u)
                 for (int v = 0; v < 2; ++v) {
-                    k[2 * u + v] = seed_k(map, (2 * sx + u) * 16 + 2 * sy + v, b, inv_step);
+                    k[2 * u + v] = seed_k(map, (2 * sx + u) * 16 + 2 * sy + v, margin);
                     kmax3 = max(kmax3, k[2 * u + v]);
                 }
             if (kmax3 <= -1) {
@@ -381,16 +386,15 @@ __device__ uint32_t seed_block(const float* map, int bx, int by, float b, float 
 }
 
 // one warp per integral; lanes 0..15 own the 16 level-2 blocks
-__global__ void __launch_bounds__(256) k_seed(Work w, const float* proposal, float inv_step, int pass)
+__global__ void __launch_bounds__(256) k_seed(Work w, const float* proposal, float margin, int pass)
 {
     const int lane = threadIdx.x & 31;
     const int64_t g = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
     if (g >= w.n) return;
     const DevBatch& B = w.batches[meta_batch(w.meta[g])];
-    const float b = float(log10(B.rel_tol > 0.0 ? B.rel_tol / 256.0 : 1e-300));
     const float* map = proposal ? proposal + g * 256 : nullptr;
     uint32_t mine = 0;
-    if (lane < 16) mine = seed_block(map, lane >> 2, lane & 3, b, inv_step, nullptr, nullptr, 0, 0,
+    if (lane < 16) mine = seed_block(map, lane >> 2, lane & 3, margin, nullptr, nullptr, 0, 0,
                                      uint32_t(g), false);
     uint32_t total = mine;
 #pragma unroll
@@ -421,7 +425,7 @@ __global__ void __launch_bounds__(256) k_seed(Work w, const float* proposal, flo
         }
         const uint32_t off = incl - mine;
         if (lane < 16)
-            seed_block(map, lane >> 2, lane & 3, b, inv_step, w.key[0], w.evl, pbase + off,
+            seed_block(map, lane >> 2, lane & 3, margin, w.key[0], w.evl, pbase + off,
                        ebase + off, uint32_t(g), true);
     }
     if (lane == 0) {
@@ -430,34 +434,51 @@ __global__ void __launch_bounds__(256) k_seed(Work w, const float* proposal, flo
     }
 }
 
-// Group mode: the seed map of group g is the cell-wise maximum of its pairs'
-// predicted relative log errors, so every cell is seeded as deep as its most
-// demanding pair asks.
-__global__ void k_group_map(Work w, const float* proposal)
+// Trace of the current partition: for every active unit the level of the
+// coarsest region meeting each level-4 cell (a region of level L < 4 covers
+// 4^(4-L) cells), written over the unit's 256 map entries.  Run every round
+// after the test, it leaves each unit's final partition in the map: the last
+// round a unit is active is the round its outcome is decided.
+__global__ void __launch_bounds__(256) k_trace(Work w)
 {
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= w.n * 256) return;
-    const int64_t g = t >> 8;
-    const int c = int(t & 255);
-    const DevBatch& B = w.batches[meta_batch(w.meta[g])];
-    const int64_t row0 = B.ifirst + (g - B.first) * B.npairs;
-    float m = -INFINITY;
-    for (int p = 0; p < B.npairs; ++p) m = fmaxf(m, proposal[(row0 + p) * 256 + c]);
-    w.gmap[t] = m;
+    __shared__ int lv[256];
+    const LoopState& Ls = *w.ls;
+    const int64_t s = blockIdx.x;
+    if (s >= Ls.n_active) return;
+    const int cur = Ls.cur;
+    const uint32_t g = w.active[cur][s];
+    const uint32_t base = w.seg_base[g], cnt = w.seg_count[g];
+    lv[threadIdx.x] = kMaxLevel + 1;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const uint64_t key = w.key[cur][base + j];
+        const int L = int(key_level(key));
+        const uint32_t ix = key_ix(key), iy = key_iy(key);
+        if (L >= 4) {
+            atomicMin(&lv[(ix >> (L - 4)) * 16 + (iy >> (L - 4))], L);
+        } else {
+            const int side = 1 << (4 - L);
+            for (int a = 0; a < side; ++a)
+                for (int b = 0; b < side; ++b)
+                    atomicMin(&lv[(ix * side + a) * 16 + iy * side + b], L);
+        }
+    }
+    __syncthreads();
+    w.tmap[size_t(g) * 256 + threadIdx.x] = float(lv[threadIdx.x]);
 }
 
-cudaError_t launch_group_map(const Work& w, const float* proposal, cudaStream_t s)
+cudaError_t launch_trace(const Work& w, int64_t hint_active, cudaStream_t s)
 {
-    if (w.n <= 0 || !proposal) return cudaSuccess;
-    k_group_map<<<int((w.n * 256 + 255) / 256), 256, 0, s>>>(w, proposal);
+    if (!w.tmap || hint_active <= 0) return cudaSuccess;
+    k_trace<<<int(hint_active), 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed(const Work& w, const float* proposal, double rate, int pass, cudaStream_t s)
+cudaError_t launch_seed(const Work& w, const float* proposal, double margin, int pass,
+                        cudaStream_t s)
 {
     if (w.n <= 0) return cudaSuccess;
-    const float inv_step = float(1.0 / (rate * log10(4.0)));
-    k_seed<<<int((w.n + 7) / 8), 256, 0, s>>>(w, proposal, inv_step, pass);
+    k_seed<<<int((w.n + 7) / 8), 256, 0, s>>>(w, proposal, float(margin), pass);
     return cudaGetLastError();
 }
 
@@ -472,7 +493,8 @@ __global__ void k_features(int kind, int nq, const double* q, int npairs, const 
     double sx, cx, sy, cy;
     sincos(q[2 * iq], &sx, &cx);
     sincos(q[2 * iq + 1], &sy, &cy);
-    const int l = lm[2 * ip], m = lm[2 * ip + 1];
+    // lm null: one row per (kind, q) group, the form-factor one-hots left zero
+    const int l = lm ? lm[2 * ip] : -1, m = lm ? lm[2 * ip + 1] : -1;
     float f[32];
     for (int i = 0; i < 32; ++i) f[i] = 0.0f;
     f[0] = float(sx); f[1] = float(cx); f[2] = float(sy); f[3] = float(cy);

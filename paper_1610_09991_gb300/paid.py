@@ -32,7 +32,9 @@ EXPORTS = ("paid_options_default", "paid_create", "paid_destroy", "paid_workspac
            "paid_error_string", "paid_last_error", "paid_mlp_param_count",
            "paid_mlp_workspace_size", "paid_mlp_init", "paid_mlp_features", "paid_mlp_forward",
            "paid_mlp_grad", "paid_mlp_adamw", "paid_rule_regions", "paid_check_math",
-           "paid_get_options", "paid_autotune", "paid_tu_flow_rhs")
+           "paid_get_options", "paid_autotune", "paid_tu_flow_rhs", "paid_integrate_batch_static",
+           "paid_set_trace_buffer", "paid_mlp_group_features", "paid_proposal_train",
+           "paid_proposal_train_workspace_size", "paid_proposal_save", "paid_proposal_load")
 
 
 class paid_options(ctypes.Structure):
@@ -40,7 +42,8 @@ class paid_options(ctypes.Structure):
                 ("eval_fp32", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("cover", ctypes.c_double), ("pool_capacity", ctypes.c_int64),
                 ("timing", ctypes.c_int), ("device_loop", ctypes.c_int),
-                ("group_mode", ctypes.c_int), ("eval_blocks", ctypes.c_int)]
+                ("group_mode", ctypes.c_int), ("eval_blocks", ctypes.c_int),
+                ("trace", ctypes.c_int)]
 
 
 class paid_stats(ctypes.Structure):
@@ -116,6 +119,15 @@ def load(path: str = LIB_PATH):
         lib.paid_mlp_forward.argtypes = [P, P, I64, P, P, ctypes.c_size_t, P]
         lib.paid_mlp_grad.argtypes = [P, P, P, I64, P, P, P, ctypes.c_size_t, P]
         lib.paid_mlp_adamw.argtypes = [P, P, P, P, I, ctypes.c_float, ctypes.c_float, P]
+        lib.paid_set_trace_buffer.argtypes = [P, P, I64]
+        lib.paid_mlp_group_features.argtypes = [P, I, I, P, D, P, P]
+        lib.paid_proposal_train_workspace_size.argtypes = [I64, I64, ctypes.POINTER(ctypes.c_size_t)]
+        lib.paid_proposal_train.argtypes = [P, P, P, P, P, I64, I, I64, ctypes.c_float,
+                                            ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(I),
+                                            P, P, ctypes.c_size_t, P]
+        lib.paid_proposal_save.argtypes = [P, ctypes.c_char_p, P]
+        lib.paid_proposal_load.argtypes = [P, ctypes.c_char_p, P]
+        lib.paid_integrate_batch_static.argtypes = [P, I, I, P, I, P, D, D, D, I64, P, P, P, P, P]
         _lib = lib
         return lib
 
@@ -237,11 +249,42 @@ class Context:
         max_regions.  Returns one Result of cuda tensors per batch."""
         return self._integrate(batches, pool_capacity, stream, None)
 
-    def integrate_multi_seeded(self, batches, proposal=None, rate=2.0, pool_capacity=None,
+    def integrate_multi_seeded(self, batches, proposal=None, margin=1.0, pool_capacity=None,
                                stream=None):
-        """As integrate_multi, with the initial partition from proposal maps
-        (cuda float32 [n, 256], global batch order; None = uniform level 4)."""
-        return self._integrate(batches, pool_capacity, stream, (proposal, float(rate)))
+        """As integrate_multi, with the initial partition from level maps
+        (cuda float32 [units, 256], global unit order: (kind, q) groups in
+        group mode, else integrals; None = uniform level 4): cell c starts at
+        level floor(map[c] - margin)."""
+        return self._integrate(batches, pool_capacity, stream, (proposal, float(margin)))
+
+    def set_trace_buffer(self, maps):
+        """Give the integrate calls a buffer for the trace maps (options.trace):
+        cuda float32 [units, 256] (None clears it); it is kept referenced here."""
+        torch = _torch()
+        if maps is None:
+            rc = self._lib.paid_set_trace_buffer(self._h, None, 0)
+        else:
+            if (maps.dtype != torch.float32 or maps.dim() != 2 or maps.shape[1] != 256
+                    or not maps.is_contiguous() or maps.device != self.torch_device):
+                raise ValueError("trace maps must be contiguous float32 [units, 256] on %s"
+                                 % self.torch_device)
+            rc = self._lib.paid_set_trace_buffer(self._h, maps.data_ptr(), maps.shape[0])
+        if rc != OK:
+            raise PaidError(rc, "paid_set_trace_buffer")
+        self._trace = maps
+
+    def group_features(self, kind, q, T, stream=None):
+        """Proposal inputs with one row per (kind, q) group: cuda bfloat16 [nq, 32]."""
+        torch = _torch()
+        x = torch.empty((q.shape[0], 32), dtype=torch.bfloat16, device=self.torch_device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.torch_device)
+        rc = self._lib.paid_mlp_group_features(self._h, int(kind), q.shape[0], q.data_ptr(),
+                                               float(T), x.data_ptr(),
+                                               ctypes.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_mlp_group_features")
+        return x
 
     def rule_regions(self, kind, q, lm, T, regions, stream=None):
         """The nested rule on given regions for every pair of one (kind, q).
@@ -268,7 +311,9 @@ class Context:
         return q2, dq
 
     def check_math(self, which, x, y=None):
-        """paid_check_math on cuda float64 tensors: 0 = exp(-x), 1 = x / y."""
+        """paid_check_math on cuda float64 tensors: 0 = exp(-x), 1 = x / y (FP64),
+        2 = exp(-x) in float-float, 3 / 4 = 2T F(x, y) of the bubbles in
+        float-float / FP64, 5 / 6 = the flow kernel at Omega = 0.1."""
         torch = _torch()
         out = torch.empty_like(x)
         stream = torch.cuda.current_stream(self.torch_device)
@@ -405,13 +450,16 @@ class Context:
                                                     ctypes.c_void_p(ws.data_ptr()), nbytes,
                                                     ctypes.c_void_p(stream.cuda_stream))
             else:
-                prop, rate = seeded
-                if prop is not None and (prop.dtype != torch.float32 or prop.shape != (n, 256)
-                                         or not prop.is_contiguous()):
-                    raise ValueError("proposal must be contiguous float32 [n, 256]")
+                prop, margin = seeded
+                units = self.units(batches)
+                if prop is not None and (prop.dtype != torch.float32
+                                         or tuple(prop.shape) != (units, 256)
+                                         or not prop.is_contiguous()
+                                         or prop.device != self.torch_device):
+                    raise ValueError("proposal must be contiguous float32 [%d, 256]" % units)
                 rc = self._lib.paid_integrate_multi_seeded(
                     self._h, arr, len(batches), prop.data_ptr() if prop is not None else None,
-                    rate, ctypes.c_void_p(ws.data_ptr()), nbytes,
+                    margin, ctypes.c_void_p(ws.data_ptr()), nbytes,
                     ctypes.c_void_p(stream.cuda_stream))
             if rc == ERR_POOL and pool_capacity is None and cap < 2 ** 32 - 1:
                 # drop every reference to the old workspace before sizing the next
@@ -428,6 +476,12 @@ class Context:
             self.last_rc = rc
             return outs
 
+    def units(self, batches) -> int:
+        """Units of a call: (kind, q) groups in group mode, else integrals."""
+        if self.options.group_mode:
+            return sum(int(b["q"].shape[0]) for b in batches)
+        return sum(int(b["q"].shape[0]) * int(b["lm"].shape[0]) for b in batches)
+
     def integrate_batch(self, kind, q, lm, T, rel_tol=1e-6, abs_tol=1e-10, max_regions=100000,
                         pool_capacity=None, stream=None) -> Result:
         """One batch (device tensors in, device tensors out), idx = iq * npairs + ip."""
@@ -435,10 +489,10 @@ class Context:
                                           abs_tol=abs_tol, max_regions=max_regions)],
                                     pool_capacity=pool_capacity, stream=stream)[0]
 
-    def integrate_host(self, batches, pool_capacity=None, proposal=None, rate=2.0):
+    def integrate_host(self, batches, pool_capacity=None, proposal=None, margin=1.0):
         """End-to-end call on host (numpy) inputs: copies q and lm from pinned
         host memory to the device, integrates (seeded from `proposal`, a
-        Proposal network, when given), and copies the results back.
+        Proposal network, with `margin`, when given), and copies the results back.
         Returns (list of numpy Result, bytes host->device, bytes device->host)."""
         torch = _torch()
         dev = self.torch_device
@@ -455,9 +509,8 @@ class Context:
         if proposal is None:
             outs = self.integrate_multi(dbs, pool_capacity=pool_capacity, stream=stream)
         else:
-            x = torch.cat([self.features(b["kind"], b["q"], b["lm"], b["T"], stream) for b in dbs])
-            maps = proposal.forward(x, stream)
-            outs = self.integrate_multi_seeded(dbs, maps, rate, pool_capacity=pool_capacity,
+            maps = proposal.predict(self, dbs, stream)
+            outs = self.integrate_multi_seeded(dbs, maps, margin, pool_capacity=pool_capacity,
                                                stream=stream)
         res, d2h = [], 0
         for r in outs:
@@ -478,10 +531,12 @@ class Context:
         allocate passes buffers it already holds to the C function."""
         torch = _torch()
         lib = self._lib
-        P_, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
-        lib.paid_integrate_batch_static.argtypes = [P_, I, I, P_, I, P_, D, D, D, I64, P_, P_,
-                                                    P_, P_, P_]
         dev = self.torch_device
+        for t_, dt, what in ((q, torch.float64, "q"), (lm, torch.int32, "lm")):
+            if (t_.device != dev or t_.dtype != dt or not t_.is_contiguous() or t_.dim() != 2
+                    or t_.shape[1] != 2):
+                raise ValueError("%s must be a contiguous %s [n, 2] tensor on %s"
+                                 % (what, dt, dev))
         nq, npairs = q.shape[0], lm.shape[0]
         r = Result(torch.empty(nq * npairs, dtype=torch.float64, device=dev),
                    torch.empty(nq * npairs, dtype=torch.float64, device=dev),
@@ -576,29 +631,63 @@ class Proposal:
             raise PaidError(rc, "paid_mlp_adamw")
         return self.loss_buf
 
-    def train(self, x, target, epochs=10, batch=4096, lr=2e-3, weight_decay=1e-4, seed=0):
-        """Minibatch AdamW over shuffled rows (cosine-decayed learning rate);
-        returns the mean loss per epoch."""
+    def train(self, x, target, epochs=10, batch=4096, lr=2e-3, weight_decay=1e-4, seed=0,
+              stream=None):
+        """paid_proposal_train: minibatch AdamW on the device over the rows of
+        x (BF16 [M, 32]) and target (FP32 [M, 256]) with a cosine-decayed
+        learning rate; returns the mean loss per epoch."""
         torch = _torch()
-        gen = torch.Generator(device="cpu").manual_seed(seed)
         M = x.shape[0]
-        steps = epochs * ((M + batch - 1) // batch)
-        k = 0
-        hist = []
-        for _ in range(epochs):
-            perm = torch.randperm(M, generator=gen).to(self.device)
-            tot = torch.zeros(1, device=self.device)
-            nb = 0
-            for i in range(0, M, batch):
-                idx = perm[i:i + batch]
-                xb = x.index_select(0, idx).contiguous()
-                tb = target.index_select(0, idx).contiguous()
-                a = lr * 0.5 * (1.0 + math.cos(math.pi * k / max(1, steps)))
-                tot += self.step(xb, tb, a, weight_decay)
-                k += 1
-                nb += 1
-            hist.append(float(tot.item()) / nb)
-        return hist
+        b = ctypes.c_size_t()
+        rc = self._lib.paid_proposal_train_workspace_size(M, int(batch), ctypes.byref(b))
+        if rc != OK:
+            raise PaidError(rc, "paid_proposal_train_workspace_size")
+        ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
+        step = ctypes.c_int(self.step_count)
+        hist = (ctypes.c_float * max(1, epochs))()
+        s = stream or torch.cuda.current_stream(self.device)
+        rc = self._lib.paid_proposal_train(self.params.data_ptr(), self.m.data_ptr(),
+                                           self.v.data_ptr(), x.contiguous().data_ptr(),
+                                           target.contiguous().data_ptr(), M, int(epochs),
+                                           int(batch), float(lr), float(weight_decay), int(seed),
+                                           ctypes.byref(step), hist, ctypes.c_void_p(ws.data_ptr()),
+                                           ws.numel(), ctypes.c_void_p(s.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_proposal_train")
+        self.step_count = step.value
+        return [float(hist[i]) for i in range(epochs)]
+
+    def save(self, path, stream=None):
+        """paid_proposal_save: the FP32 parameters to a file."""
+        torch = _torch()
+        s = stream or torch.cuda.current_stream(self.device)
+        rc = self._lib.paid_proposal_save(self.params.data_ptr(), str(path).encode(),
+                                          ctypes.c_void_p(s.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_proposal_save")
+
+    @classmethod
+    def load(cls, path, device=0, stream=None):
+        """paid_proposal_load: a network from a file written by save()."""
+        torch = _torch()
+        p = cls(device=device)
+        s = stream or torch.cuda.current_stream(p.device)
+        rc = p._lib.paid_proposal_load(p.params.data_ptr(), str(path).encode(),
+                                       ctypes.c_void_p(s.cuda_stream))
+        if rc != OK:
+            raise PaidError(rc, "paid_proposal_load")
+        return p
+
+    def predict(self, ctx, batches, stream=None):
+        """Level maps for ctx's units of these batches (group mode: one row per
+        (kind, q) group; else one per integral), FP32 [units, 256]."""
+        torch = _torch()
+        if ctx.options.group_mode:
+            x = torch.cat([ctx.group_features(b["kind"], b["q"], b["T"], stream) for b in batches])
+        else:
+            x = torch.cat([ctx.features(b["kind"], b["q"], b["lm"], b["T"], stream)
+                           for b in batches])
+        return self.forward(x, stream)
 
     def state(self):
         return self.params.detach().cpu().numpy().copy()

@@ -1,11 +1,15 @@
-"""Training data, training, rate calibration and inference for the learned
-refinement proposal (the network itself and all its arithmetic live in the
-CUDA library; this module only orchestrates calls).
+"""Training data, training, margin calibration and inference for the learned
+refinement proposal (the network and all its arithmetic live in the CUDA
+library; this module only orchestrates calls).
 
-Targets are the rule's own relative log10 error maps of the uniform level-4
-grid (paid_cell_errors); inputs are the per-integral features
-(paid_mlp_features).  Training draws lattice parameters t' ~ U[-0.35, 0],
-mu ~ U[-1.4, 0] and T log-uniform on [0.005, 1] (workloads.parameter_draws).
+Targets are what the plain method emits: the trace of a converged unseeded
+run (options.trace), per unit the level of the coarsest final region in each
+of the 256 level-4 cells.  A unit is a (kind, q) group in group mode (the
+headline path, one shared partition per group), else an integral.  Inputs
+are the unit's features (paid_mlp_group_features / paid_mlp_features).
+Training draws lattice parameters t' ~ U[-0.35, 0], mu ~ U[-1.4, 0] and T
+log-uniform on [0.005, 1] (workloads.parameter_draws, seeds 0..n-1); held-out
+draws use seeds 10000+.
 """
 from __future__ import annotations
 
@@ -13,6 +17,9 @@ import numpy as np
 
 from . import paid as P
 from . import workloads as W
+
+#: rule order and cover of the shared-partition path the proposal serves
+GROUP_OPTIONS = dict(group_mode=1, rule_n=12, cover=1.0)
 
 
 def draw_batches(T, nq, rel_tol=1e-6, abs_tol=1e-10, max_regions=100000, device=0):
@@ -26,74 +33,84 @@ def draw_batches(T, nq, rel_tol=1e-6, abs_tol=1e-10, max_regions=100000, device=
 
 
 def features(ctx, batches):
+    """Inputs of ctx's units for these batches (BF16 [units, 32])."""
     import torch
+    if ctx.options.group_mode:
+        return torch.cat([ctx.group_features(b["kind"], b["q"], b["T"]) for b in batches])
     return torch.cat([ctx.features(b["kind"], b["q"], b["lm"], b["T"]) for b in batches])
 
 
-def targets(ctx, batches):
+def traced_maps(ctx, batches):
+    """Level maps of the final partitions of an unseeded run (FP32 [units, 256])."""
     import torch
-    return torch.cat([ctx.cell_errors(b["kind"], b["q"], b["lm"], b["T"]) for b in batches])
+    maps = torch.empty((ctx.units(batches), 256), dtype=torch.float32, device=ctx.torch_device)
+    ctx.set_trace_buffer(maps)
+    ctx.integrate_multi(batches)
+    ctx.set_trace_buffer(None)
+    return maps
 
 
-def training_set(draws, nq=8, device=0):
-    """(x BF16 [M, 32], target FP32 [M, 256]) over parameter draws (t', mu, T)."""
+def training_set(draws, nq=12, device=0, **options):
+    """(x BF16 [M, 32], target FP32 [M, 256]) over parameter draws (t', mu, T):
+    every unit of a traced plain run of each draw's ph + pp batches."""
     import torch
     xs, ts = [], []
     for tp, mu, T in draws:
-        ctx = P.Context(1.0, tp, mu, ffset=9, device=device)
+        ctx = P.Context(1.0, tp, mu, ffset=9, device=device, trace=1, **options)
         bs = draw_batches(T, nq, device=device)
         xs.append(features(ctx, bs))
-        ts.append(targets(ctx, bs))
+        ts.append(traced_maps(ctx, bs))
         ctx.close()
     return torch.cat(xs), torch.cat(ts)
 
 
 def predict(prop, ctx, batches):
-    """Predicted maps (FP32 [n, 256]) for batches in the global order."""
-    return prop.forward(features(ctx, batches))
+    """Predicted level maps (FP32 [units, 256]) for batches in the global order."""
+    return prop.predict(ctx, batches)
 
 
-def calibrate_rate(prop, ctx, batches, rates=(1.5, 2.0, 3.0, 4.0, 6.0, 10.0)):
-    """The seeding rate with the fewest region evaluations on these batches;
-    returns (best rate, {rate: region evaluations})."""
+def calibrate_margin(prop, ctx, batches, margins=(0.0, 0.5, 1.0, 1.5, 2.0)):
+    """Region evaluations of the seeded run at each margin on these batches:
+    returns {margin: (region evaluations, rounds)}."""
     maps = predict(prop, ctx, batches)
-    evals = {}
-    for r in rates:
-        ctx.integrate_multi_seeded(batches, maps, r)
-        evals[r] = ctx.last_stats()["region_evals"]
-    best = min(evals, key=evals.get)
-    return best, evals
+    out = {}
+    for mg in margins:
+        ctx.integrate_multi_seeded(batches, maps, mg)
+        st = ctx.last_stats()
+        out[mg] = (st["region_evals"], st["rounds"])
+    return out
 
 
-def train_default(device=0, n_draws=24, nq=8, epochs=30, seed=0, log=None):
-    """The proposal trained on n_draws seeded parameter draws (seeds 0..n-1):
+def train_default(device=0, n_draws=48, nq=12, epochs=150, seed=0, log=None, **options):
+    """The proposal trained on n_draws seeded parameter draws (seeds 0..n-1)
+    for the given integrate options (default: the shared-partition path):
     returns (Proposal, training-loss history, seconds)."""
     import time
     import torch
+    opts = dict(GROUP_OPTIONS, **options)
     t0 = time.perf_counter()
-    x, t = training_set(W.parameter_draws(n_draws, 0), nq, device)
+    x, t = training_set(W.parameter_draws(n_draws, 0), nq, device, **opts)
     prop = P.Proposal(device=device, seed=seed)
-    hist = prop.train(x, t, epochs=epochs, batch=4096, lr=2e-3, weight_decay=1e-4, seed=seed)
+    hist = prop.train(x, t, epochs=epochs, batch=1024, lr=2e-3, weight_decay=1e-4, seed=seed)
     torch.cuda.synchronize()
     if log:
         log("proposal trained on %d rows: loss %.3f -> %.3f" % (x.shape[0], hist[0], hist[-1]))
     return prop, hist, time.perf_counter() - t0
 
 
-def calibrate_default(prop, device=0, n_draws=24, nq=4, t_range=(0.02, 0.3), eval_fp32=1,
-                      group_mode=0):
-    """Seeding rate calibrated on the training draws whose T lies in t_range
-    (smaller q grid) for the given evaluation mode; returns
-    (rate, {rate: summed region evaluations})."""
+def calibrate_default(prop, device=0, n_draws=48, nq=8, t_range=(0.01, 0.3), **options):
+    """Margin with the fewest region evaluations summed over the training draws
+    whose T lies in t_range (smaller q grid); returns (margin, {margin:
+    (region evaluations, rounds)})."""
+    opts = dict(GROUP_OPTIONS, **options)
     tot = {}
     for tp, mu, T in W.parameter_draws(n_draws, 0):
         if not (t_range[0] <= T <= t_range[1]):
             continue
-        ctx = P.Context(1.0, tp, mu, ffset=9, device=device, eval_fp32=eval_fp32,
-                        group_mode=group_mode)
-        _, ev = calibrate_rate(prop, ctx, draw_batches(T, nq, device=device))
-        for r, e in ev.items():
-            tot[r] = tot.get(r, 0) + e
+        ctx = P.Context(1.0, tp, mu, ffset=9, device=device, **opts)
+        for mg, (ev, rd) in calibrate_margin(prop, ctx, draw_batches(T, nq, device=device)).items():
+            e0, r0 = tot.get(mg, (0, 0))
+            tot[mg] = (e0 + ev, r0 + rd)
         ctx.close()
-    best = min(tot, key=tot.get) if tot else 4.0
+    best = min(tot, key=lambda k: tot[k][0]) if tot else 1.0
     return best, tot

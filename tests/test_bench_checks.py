@@ -57,6 +57,25 @@ def test_accuracy_sides_with_the_brute_force(bench):
     assert len(d) == 1 and d[0]["value_within_2tol_of_brute_force"]
 
 
+def test_accuracy_counts_integrals_left_unconverged(bench):
+    # the reference converged, the checked side stopped on its budget, the
+    # round cap or a full pool with a value that may look right: each one is a
+    # parity failure
+    b, v, s, ident = _first_shell_sample()
+    for status in (1, 3, 4):
+        st = s.copy()
+        st[[3, 7]] = status
+        got = bench.accuracy(v.copy(), st, v, s, b.rel_tol, b.abs_tol, "planted", ident,
+                             W.LATTICE)
+        assert got["unconverged_where_reference_converged"] == 2
+        assert got["parity_failures"] == 2
+    # the reverse (the reference stopped, the checked side converged) is not
+    st = s.copy()
+    st[5] = 1
+    got = bench.accuracy(v.copy(), s, v, st, b.rel_tol, b.abs_tol, "planted", ident, W.LATTICE)
+    assert got["parity_failures"] == 0
+
+
 def test_group_global_check(bench):
     w = W.config_flow_step(T=0.5, nq=2)
     vals, stats = [], []

@@ -64,9 +64,7 @@ def test_host_side_calls_without_gpu(lib):
     assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
     bad.rule_n = 8   # N = 8, 10, 12 only with the shared-partition kernel
     assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
-    bad.group_mode, bad.eval_fp32 = 1, 1   # group mode is FP64
-    assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
-    bad.group_mode = 2                     # the global-error group mode is FP64 too
+    bad.rule_n, bad.eval_fp32 = 4, 2       # precision modes are 0 (FP64) and 1 (FP32 pipe)
     assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
     bad.group_mode, bad.eval_fp32 = 3, 0   # modes are 0, 1, 2
     assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG

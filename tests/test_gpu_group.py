@@ -266,3 +266,26 @@ def test_group_higher_order_flow_step_matches_oracle(paid, torch, N):
             o = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
                                        b.max_regions, rule_n=rn)
             assert assert_parity(g, o, b.rel_tol, b.abs_tol, batch_ident(b)) >= 0.9 * b.n
+
+
+@pytest.mark.parametrize("eval_fp32", [0, 1])
+def test_group_temperature_sweep_in_one_call(paid, torch, eval_fp32):
+    # the batching workload's recipe on a 4 x 4 q grid: 12 temperatures from 1
+    # to 0.005 x {ph, pp} x 81 pairs = 31,104 integrals of very uneven depth in
+    # one call (24 batches in one pool), shared partitions at N = 12; a seeded
+    # oracle sample across all temperatures, one by one
+    w = W.config_temperature_sweep(nq=4)
+    ctx = paid.Context(*w.lattice, ffset=9, group_mode=1, rule_n=12, cover=1.0,
+                       eval_fp32=eval_fp32)
+    gs = _run(paid, torch, ctx, w.batches)
+    assert ctx.last_rc == paid.OK
+    g = tuple(np.concatenate([x[i] for x in gs]) for i in range(4))
+    assert np.all(g[3] == 0)
+    flat = W.flatten(w)
+    idx = W.sample_indices(w.n, 240, seed=4321)
+    o = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
+                              flat["T"][idx], LAT, 1e-6, 1e-10, 100000, rule_n=12)
+    assert_parity(tuple(x[idx] for x in g), o, 1e-6, 1e-10, flat_ident(flat, idx))
+    # lower temperatures need deeper partitions
+    per_T = [np.mean(x[2]) for x in gs[::2]]
+    assert per_T[-1] > per_T[0]

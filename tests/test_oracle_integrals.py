@@ -182,3 +182,38 @@ def test_heuristic_error_estimate_can_miss():
     assert s[0] == oracle.CONVERGED and np.isfinite(truth)
     assert abs(v[0] - truth) > 2 * e[0]
     assert abs(v[0] - truth) < 1e-7
+
+
+def _ph00_q0(T, lat):
+    v, e, _, s = oracle.integrate_batch(0, np.zeros((1, 2)), np.array([(0, 0)]), T, lat,
+                                        1e-8, 1e-13, 100000)
+    assert s[0] == 0
+    return v[0]
+
+
+@pytest.mark.parametrize("tp", [-0.25, -0.35, -0.1])
+def test_band_edges_and_van_hove_energy_fix_the_hopping_terms(tp):
+    # ph_00(q = 0, T) = int -nF'(e) d^2k/(2pi)^2 is the density of states at the
+    # Fermi level smeared over ~T.  Hand-derived features of the t-t' band,
+    # independent of the oracle's formula, fix both hopping terms:
+    #  * band bottom at k = 0: e ~ -4t - 4t' + (t + 2t') k^2, a 2-D step of
+    #    height 1 / (4 pi (t + 2t')); at mu on the edge the smeared DOS is half
+    #    the step;
+    #  * band top at (pi, pi): e ~ 4t - 4t' - (t - 2t') k^2, half of
+    #    1 / (4 pi (t - 2t'));
+    #  * saddle points at (pi, 0), (0, pi): e = 4t' - mu, so the logarithmic
+    #    van Hove peak of the DOS sits at mu = 4t'.
+    # A wrong t' coefficient (say 2t' for 4t') moves the edges and the peak.
+    t, T = 1.0, 0.004
+    bottom = _ph00_q0(T, (t, tp, -4 * t - 4 * tp))
+    top = _ph00_q0(T, (t, tp, 4 * t - 4 * tp))
+    assert abs(bottom - 1.0 / (8 * math.pi * (t + 2 * tp))) < 0.02 * bottom
+    assert abs(top - 1.0 / (8 * math.pi * (t - 2 * tp))) < 0.02 * top
+    # well outside the band the smeared DOS vanishes
+    assert _ph00_q0(T, (t, tp, -4 * t - 4 * tp - 0.2)) < 1e-6
+    Tv = 0.02
+    mus = 4 * tp + np.arange(-0.3, 0.3001, 0.01)
+    dos = np.array([_ph00_q0(Tv, (t, tp, mu)) for mu in mus])
+    peak = mus[int(np.argmax(dos))]
+    assert abs(peak - 4 * tp) <= 0.04, peak
+    assert dos.max() > 1.5 * min(dos[0], dos[-1])

@@ -1,13 +1,15 @@
 """The allocation-free entry point, paid_integrate_batch_static.
 
 It serves callers that cannot allocate device memory when they integrate
-(inside a CUDA graph capture, under a fixed start-up memory budget, in a loop
-that must not allocate): the region pool is a fixed 64 MiB array inside the
-library instead of a caller workspace.  This file checks, through the C ABI,
-that two calls in a row give the same results as paid_integrate_batch (the
-second call runs on the scratch the first one left behind), and that a batch
-beyond the stated maximum is refused.  It is named to be collected last, and
-passes both alone in a fresh process and after the rest of the suite.
+(a runtime with a device-memory budget fixed at start-up, a plug-in inside
+another framework's memory manager, a loop that must not allocate): the region
+pool is a fixed 64 MiB array inside the library instead of a caller workspace.
+This file checks, through the C ABI, that two calls in a row give the same
+results as paid_integrate_batch (the second call runs on the scratch the first
+one left behind), and that a batch beyond the stated maximum, or one that
+breaks paid_integrate_batch's own argument rules, is refused.  It is named to
+be collected last, and passes both alone in a fresh process and after the rest
+of the suite.
 """
 import ctypes
 
@@ -62,3 +64,18 @@ def test_static_rejects_batches_beyond_its_maximum(env):
     with pytest.raises(P.PaidError) as ei:
         ctx.integrate_batch_static(P.PH, q, lm, 0.5)
     assert ei.value.rc == P.ERR_ARG
+
+
+def test_static_applies_the_same_argument_rules(env):
+    torch, P = env
+    ctx = P.Context(*W.LATTICE, ffset=9, group_mode=1)
+    q = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
+    lm = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+    for omega in (0.0, -0.1, float("nan")):        # the flow kinds need Omega > 0
+        with pytest.raises(P.PaidError) as ei:
+            ctx.integrate_batch_static(P.FLOW_PH, q, lm, omega)
+        assert ei.value.rc == P.ERR_ARG
+    with pytest.raises(ValueError):                # the binding checks layouts first
+        ctx.integrate_batch_static(P.PH, q.float(), lm, 0.5)
+    with pytest.raises(ValueError):
+        ctx.integrate_batch_static(P.PH, q, lm.long(), 0.5)
