@@ -59,6 +59,13 @@ GROUP_FP64_FLOPS_PER_REGION = {
     for n, f in {4: 2 * 4839 + 663 + 1766, 6: 2 * 8955 + 1285 + 3118,
                  8: 2 * 14367 + 2131 + 4902, 10: 2 * 21075 + 3201 + 7118,
                  12: 2 * 29079 + 4495 + 9766}.items()}
+# FP32-pipe thread instructions (FADD + FMUL + FFMA, one issue slot each) and
+# FP32 flops (FFMA counted as 2) per region of the float-float form of the
+# shared-partition kernel (k_eval_group_ff<N, 1>, ph / pp, 81 pairs), from the
+# ncu instruction counters of one launch over 6,240 regions of the flow step
+# at T = 0.05 divided by its regions (profiles/k_eval_group_ff_flow_step_q4.md).
+GROUP_FP32_INSTR_PER_REGION = {12: 292300}
+GROUP_FP32_FLOPS_PER_REGION = {12: 359000}
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
@@ -78,25 +85,20 @@ def parse_args():
     ap.add_argument("--workload", choices=["flow_step", "flow_step_q4", "first_shell", "sweep",
                                            "flow_omega", "heldout"],
                     default="flow_step")
-    ap.add_argument("--path", choices=["group", "group_fp32", "learned", "plain", "fp32",
-                                       "learned_fp32"],
-                    default="group",
-                    help="group: one shared partition per (kind, q) for all its pairs, FP64, "
-                         "uniform start; group_fp32: the same with the kernel F and the row "
-                         "sums in float-float on the FP32 pipe; learned: group with the "
-                         "learned proposal's seeded start; plain: one partition per integral, "
-                         "FP64, uniform start; fp32: per integral, FP32 / float-float "
-                         "evaluation; learned_fp32: fp32 with the seeded start")
+    ap.add_argument("--path", choices=sorted(PATHS), default="learned",
+                    help="learned (the headline): learned seeding + one shared partition per "
+                         "(kind, q) for all its pairs, FP32-pipe evaluation; group: the same "
+                         "from the uniform start; group_fp64: the same in FP64; plain: one "
+                         "partition per integral, FP64; fp32: per integral, FP32 / float-float; "
+                         "learned_fp32: fp32 with the learned seed")
     ap.add_argument("--rule-n", type=int, choices=[4, 6, 8, 10, 12], default=12,
                     help="N of the nested rule for the reference arm and for group-mode GPU runs "
                          "without the autotuner (the GPU arm's tuner chooses it otherwise; on "
                          "GB300 it picks 12)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="group paths: keep the default cover and evaluation grid")
-    ap.add_argument("--no-learned", action="store_true",
-                    help="skip the extra timed steps of the learned_fp32 path")
     ap.add_argument("--no-compare", action="store_true",
-                    help="skip the timed FP64 comparison step of an FP32 run")
+                    help="skip the comparison blocks (uniform start, FP64 group, plain FP64)")
     ap.add_argument("--no-global", action="store_true",
                     help="group path: skip the global-error group mode (group_mode = 2) block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -351,6 +353,56 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU arm
+PATHS = {
+    "learned": "learned proposal seeding (trained on traced plain runs) + batched GPU cubature, "
+               "one shared partition per (kind, q) serving all 81 (l, m) pairs, each pair to "
+               "its own tolerance; kernel F, row sums and moments in float-float on the FP32 "
+               "pipe, region values, errors and totals FP64",
+    "group": "batched GPU cubature, one shared partition per (kind, q) serving all 81 (l, m) "
+             "pairs from the uniform level-2 start; FP32-pipe evaluation as above",
+    "group_fp64": "the same shared partitions, everything FP64",
+    "plain": "plain FP64 GPU cubature, one partition per integral, uniform level-2 start",
+    "fp32": "one partition per integral, FP32 / float-float integrand, FP64 sums",
+    "learned_fp32": "learned proposal seeding + one partition per integral, FP32 / float-float "
+                    "integrand, FP64 sums",
+}
+
+
+def path_options(path, rule_n):
+    """Context options of a bench path."""
+    group = path in ("learned", "group", "group_fp64")
+    fp32 = path in ("learned", "group", "fp32", "learned_fp32")
+    o = dict(eval_fp32=1 if fp32 else 0, group_mode=1 if group else 0)
+    if group:
+        o["rule_n"] = rule_n
+    return o
+
+
+def roofline_fp32_group(n_regions, eval_s, rule_n, peaks):
+    """FP32-pipe roofline of the float-float group kernel: thread instructions
+    on the FP32 pipe (FADD, FMUL, FFMA: one issue slot of the pipe each) per
+    region from its ncu counters, over the summed event time, against the pipe's
+    instruction rate (the measured FFMA peak / 2 flops)."""
+    ipr = GROUP_FP32_INSTR_PER_REGION.get(rule_n)
+    pk = peaks.get("fp32_fma_tflops")
+    if not ipr or not pk or eval_s <= 0:
+        return None
+    achieved = n_regions * ipr / eval_s / 1e12
+    peak = pk / 2.0
+    f = GROUP_FP32_FLOPS_PER_REGION[rule_n]
+    return {"bound": "alu", "kernel": "k_eval_group_ff<%d>" % rule_n, "achieved": achieved,
+            "peak": peak, "unit": "T FP32-pipe thread instructions/s", "frac": achieved / peak,
+            "traffic": None,
+            "traffic_note": "compute-bound: ~20 B of eval list / key read and 81 x 12 B of pair "
+                            "vectors written per region for %d FP32-pipe instructions" % ipr,
+            "peak_source": "measured FFMA micro-benchmark in this run (pipe_peaks.cu), "
+                           "2 flops per FFMA instruction",
+            "instructions_per_region": ipr,
+            "flops_per_region": f, "tflops": n_regions * f / eval_s / 1e12,
+            "tflops_frac_of_fma_peak": n_regions * f / eval_s / 1e12 / pk,
+            "rule_n": rule_n}
+
+
 def run_paid(args):
     import numpy as np
     import torch
@@ -369,16 +421,13 @@ def run_paid(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w, ff = workload(args.workload, args.temperature, args.rel_tol)
-    if args.workload == "flow_omega":
+    if args.workload == "flow_omega" and args.path not in ("group", "group_fp64"):
         # the Omega-regulated flow kinds exist in the shared-partition kernel only
-        args.path, args.no_compare, args.no_learned = "group", True, True
-    args.eval = "fp64" if args.path in ("plain", "group", "learned") else "fp32"
-    group = 1 if args.path in ("group", "learned", "group_fp32") else 0
+        args.path = "group"
+    opts = path_options(args.path, args.rule_n)
+    group = opts["group_mode"]
     learned = args.path in ("learned", "learned_fp32")
-    fp32_mode = 1 if args.eval == "fp32" else 0
-    ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1,
-                    eval_fp32=fp32_mode, group_mode=group,
-                    rule_n=args.rule_n if group else 4)
+    ctx = P.Context(*w.lattice, ffset=ff, device=local, timing=1, **opts)
     dev = torch.device("cuda", local)
     # N > 1: the temperature sweep is one fixed job split across the ranks by
     # q row (cost-balanced, no exchange; strong scaling); every other workload
@@ -396,11 +445,10 @@ def run_paid(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peaks = fp64_peak(local)
-    prop_info, prop, rate = None, None, None
     tune = None
-    if group and not args.no_autotune:
-        # autotuner (outside the timed region): cover and the evaluation grid,
-        # timed on every 6th q point of each batch
+    if not args.no_autotune:
+        # autotuner (outside the timed region): rule order, cover and (group
+        # mode) the evaluation grid, timed on every 6th q point of each batch
         t0 = time.perf_counter()
         sample = [dict(d, q=d["q"][::6].contiguous()) for d in dbs]
         o = ctx.autotune(sample)
@@ -409,27 +457,33 @@ def run_paid(args):
                 "sample": "every 6th q point of each batch (%d integrals)"
                           % sum(int(d["q"].shape[0]) * int(d["lm"].shape[0]) for d in sample)}
         ctx.release_workspace()
+    tuned = dict(rule_n=ctx.options.rule_n, cover=ctx.options.cover,
+                 eval_blocks=ctx.options.eval_blocks)
+    prop_info, prop, margin = None, None, None
     if learned:
         from paper_1610_09991_gb300 import proposal as PR
-        prop, hist, t_train = PR.train_default(device=local, n_draws=24, nq=8, epochs=20)
+        popts = dict(opts, rule_n=tuned["rule_n"], cover=tuned["cover"]) if group else dict(opts)
+        prop, hist, t_train = PR.train_default(device=local, **popts)
         t0 = time.perf_counter()
-        rate, calib = PR.calibrate_default(prop, device=local,
-                                           eval_fp32=1 if args.eval == "fp32" else 0,
-                                           group_mode=group)
-        t_cal = time.perf_counter() - t0
-        prop_info = {"train_seconds": t_train, "calibrate_seconds": t_cal,
-                     "training_rows": 24 * 2 * 64 * 81, "draws": "seeds 0..23 of "
-                     "t' ~ U[-0.35,0], mu ~ U[-1.4,0], T log-U[0.005,1], 8x8 q grid, ph+pp",
-                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "rate": rate,
-                     "calibration_region_evals": {str(k): v for k, v in calib.items()}}
+        margin, calib = PR.calibrate_default(prop, device=local, **popts)
+        prop_info = {"train_seconds": t_train, "calibrate_seconds": time.perf_counter() - t0,
+                     "targets": "traced level maps of unseeded runs (options.trace): per unit "
+                                "the level of the coarsest final region in each level-4 cell",
+                     "draws": "seeds 0..127 of t' ~ U[-0.35,0], mu ~ U[-1.4,0], T log-U[0.005,1], "
+                              "12x12 q grid, ph+pp; 300 epochs",
+                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "margin": margin,
+                     "calibration_region_evals_rounds": {str(k): v for k, v in calib.items()}}
 
-    def step():
-        flush.fill_(1)
-        if prop is None:
-            return ctx.integrate_multi(dbs, stream=stream)
-        maps = PR.predict(prop, ctx, dbs)
-        return ctx.integrate_multi_seeded(dbs, maps, rate, stream=stream)
+    def make_step(c, seeded):
+        def step():
+            flush.fill_(1)
+            if not seeded:
+                return c.integrate_multi(dbs, stream=stream)
+            return c.integrate_multi_seeded(dbs, prop.predict(c, dbs, stream), margin,
+                                            stream=stream)
+        return step
 
+    step = make_step(ctx, learned)
     for _ in range(args.warmup):
         step()
     # the per-step bookkeeping below uses torch kernels that load on first use
@@ -447,10 +501,13 @@ def run_paid(args):
                eval_ms=0.0, reduce_ms=0.0, scan_ms=0.0, split_ms=0.0, rounds=0, peak_pool=0,
                df_ms=0.0, df_regions=0, escalated=0)
     ev0.record(stream)
+    # an NVTX range around the timed steps lets a profiler capture exactly them
+    torch.cuda.nvtx.range_push("timed_steps")
     step_outs, step_stats = [], []
     for _ in range(args.steps):
         step_outs.append(step())
         step_stats.append(ctx.last_stats())
+    torch.cuda.nvtx.range_pop()
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -478,18 +535,20 @@ def run_paid(args):
         conv_all = agg["conv"]
     value = conv_all / elapsed
 
-    # e2e: host numpy inputs -> pinned H2D -> integrate -> D2H, wall clock
+    # e2e: host numpy inputs -> pinned H2D -> (proposal) -> integrate -> D2H,
+    # wall clock over several steps
     e2e = None
     if not args.no_e2e:
         hb = [dict(kind=b.kind, T=b.T, q=b.q, lm=b.lm, rel_tol=b.rel_tol, abs_tol=b.abs_tol,
                    max_regions=b.max_regions) for b in w.batches]
+        ctx.integrate_host(hb, proposal=prop, margin=margin or 0.0)   # warm-up (pinned pools)
         torch.cuda.synchronize()
-        n_e2e = 1
+        n_e2e = max(5, min(args.steps, 10))
         t0 = time.perf_counter()
         conv_e2e, h2d, d2h = 0, 0, 0
         for _ in range(n_e2e):
             flush.fill_(1)
-            res, h2d, d2h = ctx.integrate_host(hb, proposal=prop, rate=rate or 2.0)
+            res, h2d, d2h = ctx.integrate_host(hb, proposal=prop, margin=margin or 0.0)
             conv_e2e += sum(int((r.status == 0).sum()) for r in res)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
@@ -498,19 +557,22 @@ def run_paid(args):
 
     eval_s = agg["eval_ms"] / 1e3
     roof = None
-    if group and eval_s > 0 and args.eval == "fp64":
+    if group and opts["eval_fp32"]:
+        roof = roofline_fp32_group(agg["region_evals"], eval_s, ctx.options.rule_n, peaks)
+    elif group and eval_s > 0:
         flow = all(b.kind in (W.FLOW_PH, W.FLOW_PP) for b in w.batches)
         fpr = (GROUP_FLOW_FP64_FLOPS_PER_REGION if flow
                else GROUP_FP64_FLOPS_PER_REGION)[ctx.options.rule_n]
         achieved = agg["region_evals"] * fpr / eval_s / 1e12
         pk = peaks.get("fp64_fma_tflops")
-        roof = {"bound": "alu", "kernel": "k_eval_group", "achieved": achieved, "peak": pk,
+        roof = {"bound": "alu", "kernel": "k_eval_group<%d>" % ctx.options.rule_n,
+                "achieved": achieved, "peak": pk,
                 "unit": "TFLOP/s", "frac": achieved / pk if pk else None, "traffic": None,
                 "traffic_note": "compute-bound: ~20 B of eval list / key read and 81 x 12 B of "
                                 "pair vectors written per region for %d FP64 flops" % fpr,
                 "peak_source": "measured FP64 FMA micro-benchmark in this run (pipe_peaks.cu)",
                 "flops_per_region": fpr, "rule_n": ctx.options.rule_n}
-    elif FP64_FLOPS_PER_NODE and eval_s > 0 and args.eval == "fp64":
+    elif FP64_FLOPS_PER_NODE and eval_s > 0 and not opts["eval_fp32"]:
         achieved = agg["node_evals"] * FP64_FLOPS_PER_NODE / eval_s / 1e12
         pk = peaks.get("fp64_fma_tflops")
         per_launch = agg["region_evals"] / max(1, agg["eval_launches"])
@@ -522,7 +584,7 @@ def run_paid(args):
                 "peak_source": "measured FP64 FMA micro-benchmark in this run (pipe_peaks.cu)",
                 "flops_per_node": FP64_FLOPS_PER_NODE}
     df_s = agg["df_ms"] / 1e3
-    if args.eval == "fp32" and DF_FP32_FLOPS_PER_REGION and df_s > 0:
+    if not group and opts["eval_fp32"] and DF_FP32_FLOPS_PER_REGION and df_s > 0:
         achieved = agg["df_regions"] * DF_FP32_FLOPS_PER_REGION / df_s / 1e12
         pk = peaks.get("fp32_fma_tflops")
         roof = {"bound": "alu", "kernel": "k_eval_df", "achieved": achieved, "peak": pk,
@@ -536,27 +598,16 @@ def run_paid(args):
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
-        "dtype": "f64" if args.eval == "fp64" else "f32+f64", "data": "synthetic",
-        "config": dict(workload_config(w_job, ff, args.eval, ctx.options.rule_n),
+        "dtype": "f32x2+f64" if opts["eval_fp32"] else "f64", "data": "synthetic",
+        "config": dict(workload_config(w_job, ff, "fp32 pipe (float-float), fp64 sums"
+                                       if opts["eval_fp32"] else "fp64", ctx.options.rule_n),
                        partition="one per (kind, q) group" if group else "one per integral",
                        parallelism="%d ranks, %s" % (world, "q rows split across ranks"
                                                      if scaling == "strong" else
                                                      "one instance per rank")),
         "clocks": clk, "roofline": roof, "gpu_launches": agg["launches"],
         "e2e": e2e,
-        "path": {"plain": "plain FP64 GPU cubature from the uniform level-2 start",
-                 "group": "FP64 GPU cubature, one shared partition per (kind, q) serving all "
-                          "81 (l, m) pairs, each pair to its own tolerance",
-                 "group_fp32": "GPU cubature, one shared partition per (kind, q) serving all "
-                               "81 (l, m) pairs, each pair to its own tolerance; kernel F and "
-                               "row sums in float-float on the FP32 pipe, moments and totals "
-                               "FP64",
-                 "learned": "learned proposal seeding + batched FP64 GPU cubature, one shared "
-                            "partition per (kind, q) serving all 81 (l, m) pairs, each pair "
-                            "to its own tolerance",
-                 "fp32": "batched GPU cubature, FP32 / float-float integrand, FP64 sums",
-                 "learned_fp32": "learned proposal seeding + batched GPU cubature, FP32 / "
-                                 "float-float integrand, FP64 sums"}[args.path],
+        "path": PATHS[args.path],
         "proposal": prop_info,
         "autotune": tune,
         "budget_integrals_per_step": agg["budget"] / args.steps,
@@ -567,84 +618,95 @@ def run_paid(args):
         "peak_pool_regions": agg["peak_pool"],
         "kernel_ms_per_step": {k: agg[k] / args.steps for k in
                                ("eval_ms", "df_ms", "reduce_ms", "scan_ms", "split_ms")},
-        "float_float_regions_per_step": agg["df_regions"] / args.steps,
-        "escalated_integrals_per_step": agg["escalated"] / args.steps,
         "eval_launches": agg["eval_launches"],
         "pipe_peaks": peaks,
     }
+    if not group and opts["eval_fp32"]:
+        line["float_float_regions_per_step"] = agg["df_regions"] / args.steps
+        line["escalated_integrals_per_step"] = agg["escalated"] / args.steps
     vals = torch.cat([o.values for o in outs]).cpu().numpy()
     stats = torch.cat([o.status for o in outs]).cpu().numpy()
     # each context below sizes its own pool from the free memory
     del step_outs, outs
     ctx.release_workspace()
+
+    def timed(c, seeded, nsteps):
+        """nsteps timed steps of context c (after one warm-up): (block, values, status)."""
+        st = make_step(c, seeded)
+        st()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        os_, sts = [], []
+        for _ in range(nsteps):
+            os_.append(st())
+            sts.append(c.last_stats())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        conv = sum(int((torch.cat([o.status for o in x]) == 0).sum()) for x in os_)
+        v_ = torch.cat([x.values for x in os_[-1]]).cpu().numpy()
+        s_ = torch.cat([x.status for x in os_[-1]]).cpu().numpy()
+        blk = {"value": conv * world / t, "unit": UNIT, "ms_per_step": 1e3 * t / nsteps,
+               "steps": nsteps, "region_evals": sts[-1]["region_evals"],
+               "rounds": sts[-1]["rounds"], "kernels_per_step": sts[-1]["launches"],
+               "eval_ms": sts[-1]["eval_ms"], "rule_n": c.options.rule_n,
+               "cover": c.options.cover}
+        del os_
+        return blk, v_, s_
+
     if not args.no_device_loop:
         # the same steps with the refinement loop on the device: one CUDA graph
         # launch per call (conditional WHILE node), no per-round host sync and
         # no per-kernel events
-        cg = P.Context(*w.lattice, ffset=ff, device=local, device_loop=1,
-                       eval_fp32=fp32_mode, group_mode=group,
-                       cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks,
-                       rule_n=ctx.options.rule_n)
-
-        def gstep():
-            flush.fill_(1)
-            if prop is None:
-                return cg.integrate_multi(dbs, stream=stream)
-            maps = PR.predict(prop, ctx, dbs)
-            return cg.integrate_multi_seeded(dbs, maps, rate, stream=stream)
-
-        gstep()                                        # warm-up: workspace and graph
-        torch.cuda.synchronize()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        gouts, gst = [], []
-        for _ in range(args.steps):
-            gouts.append(gstep())
-            gst.append(cg.last_stats())
-        g1.record(stream)
-        torch.cuda.synchronize()
-        tg = g0.elapsed_time(g1) / 1e3
-        gconv = sum(int((torch.cat([o.status for o in go]) == 0).sum()) for go in gouts)
-        same = all(np.array_equal(torch.cat([a.values for a in go]).cpu().numpy(), vals)
-                   for go in gouts)
-        line["device_loop"] = {
-            "value": gconv * world / tg, "unit": UNIT, "ms_per_step": 1e3 * tg / args.steps,
-            "graph_launches_per_step": sum(x["graph_launches"] for x in gst) / args.steps,
-            "kernels_per_step": sum(x["launches"] for x in gst) / args.steps,
-            "rounds_per_step": sum(x["rounds"] for x in gst) / args.steps,
-            "values_identical_to_host_loop": bool(same)}
-        del gouts
+        cg = P.Context(*w.lattice, ffset=ff, device=local, device_loop=1, **dict(opts, **tuned))
+        blk, gv, _ = timed(cg, learned, args.steps)
+        blk["values_identical_to_host_loop"] = bool(np.array_equal(gv, vals))
+        line["device_loop"] = blk
         cg.close()
         torch.cuda.empty_cache()
+    if learned and group and not args.no_compare:
+        # what the learned seed gains: the same path from the uniform start
+        cu = P.Context(*w.lattice, ffset=ff, device=local, timing=1, **dict(opts, **tuned))
+        blk, uv, us = timed(cu, False, args.steps)
+        blk["path"] = PATHS["group"]
+        line["group_uniform_start"] = blk
+        line["speedup_of_learned_seed"] = value / blk["value"]
+        line["region_evals_saved_by_learned_seed"] = 1.0 - (
+            line["region_evals_per_step"] / max(1, blk["region_evals"]))
+        cu.close()
+        torch.cuda.empty_cache()
+    if group and opts["eval_fp32"] and not args.no_compare:
+        # the FP64 form of the shared-partition kernel, same partitions' rule
+        c64g = P.Context(*w.lattice, ffset=ff, device=local, timing=1, group_mode=1,
+                         **tuned)
+        blk, v64g, s64g = timed(c64g, False, min(args.steps, 5))
+        fpr = GROUP_FP64_FLOPS_PER_REGION[c64g.options.rule_n]
+        ev_s = blk["eval_ms"] / 1e3
+        pk = peaks.get("fp64_fma_tflops")
+        blk["path"] = PATHS["group_fp64"]
+        blk["roofline"] = {"bound": "alu", "kernel": "k_eval_group<%d>" % c64g.options.rule_n,
+                           "achieved": blk["region_evals"] * fpr / ev_s / 1e12 if ev_s else None,
+                           "peak": pk, "unit": "TFLOP/s", "flops_per_region": fpr}
+        if pk and ev_s:
+            blk["roofline"]["frac"] = blk["roofline"]["achieved"] / pk
+        line["group_fp64"] = blk
+        c64g.close()
+        torch.cuda.empty_cache()
     glob = None
-    if args.path in ("group", "group_fp32") and not args.no_global:
+    if group and not args.no_global:
         # the paper's own stopping test (Algorithm 2, global error): one error
         # sum and one tolerance per (kind, q) group, on the same shared
         # partitions, rule and grid
         cgl = P.Context(*w.lattice, ffset=ff, device=local, group_mode=2,
-                        cover=ctx.options.cover, eval_blocks=ctx.options.eval_blocks,
-                        rule_n=ctx.options.rule_n, eval_fp32=ctx.options.eval_fp32)
-
-        def glstep():
-            flush.fill_(1)
-            return cgl.integrate_multi(dbs, stream=stream)
-
-        for _ in range(max(1, args.warmup)):
-            glstep()
-        torch.cuda.synchronize()
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        hsteps = min(args.steps, 5)
-        h0.record(stream)
-        houts = [glstep() for _ in range(hsteps)]
-        h1.record(stream)
-        torch.cuda.synchronize()
-        th = h0.elapsed_time(h1) / 1e3
-        hst = cgl.last_stats()
-        hconv = sum(int((torch.cat([o.status for o in ho]) == 0).sum()) for ho in houts)
-        gv = torch.cat([o.values for o in houts[-1]]).cpu().numpy()
-        ge = torch.cat([o.errors for o in houts[-1]]).cpu().numpy()
-        gs = torch.cat([o.status for o in houts[-1]]).cpu().numpy()
+                        eval_fp32=opts["eval_fp32"], **tuned)
+        blk, gv, gs = timed(cgl, False, min(args.steps, 5))
+        ge = None
         met, ngr, off, agree = 0, 0, 0, 0.0
+        # errors of the last step for the group test
+        o_ = cgl.integrate_multi(dbs, stream=stream)
+        torch.cuda.synchronize()
+        ge = torch.cat([x.errors for x in o_]).cpu().numpy()
         for b in w.batches:
             Pn = b.lm.shape[0]
             vv, ee = gv[off:off + b.n].reshape(-1, Pn), ge[off:off + b.n].reshape(-1, Pn)
@@ -654,53 +716,37 @@ def run_paid(args):
             met += int((ee.sum(1) <= tolg * (1 + 1e-6)).sum())
             ngr += vv.shape[0]
             agree = max(agree, float((np.abs(vv - vp).sum(1) / tolg).max()))
-        hval = hconv * world / th
         glob = (gv, gs)
-        line["group_global"] = {
+        blk.update({
             "path": "group mode 2: shared partition per (kind, q), one error sum and one "
                     "tolerance per group (Algorithm 2's global error, rel_tol on sum |V_c|)",
-            "value": hval, "unit": UNIT, "ms_per_step": 1e3 * th / hsteps, "steps": hsteps,
-            "region_evals": hst["region_evals"], "rounds": hst["rounds"],
-            "speedup_vs_per_pair_group": hval / value,
+            "speedup_vs_per_pair_group": blk["value"] / value,
             "groups_meeting_group_tol": met, "groups": ngr,
-            "max_dev_from_per_pair_results_over_group_tol": agree}
-        del houts
+            "max_dev_from_per_pair_results_over_group_tol": agree})
+        line["group_global"] = blk
+        del o_
         cgl.close()
         torch.cuda.empty_cache()
-    if args.path not in ("plain",) and not args.no_compare:
-        # the plain FP64 GPU path (one partition per integral) on the same batch:
-        # with its own autotuned rule and cover, and with the library defaults
-        def timed_plain(c):
-            c.integrate_multi(dbs, stream=stream)        # warm-up (workspace)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            o = c.integrate_multi(dbs, stream=stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / 1e3
-            v_ = torch.cat([x.values for x in o]).cpu().numpy()
-            s_ = torch.cat([x.status for x in o]).cpu().numpy()
-            st_ = c.last_stats()
-            blk = {"value": float((s_ == 0).sum()) * world / t, "unit": UNIT, "ms_per_step": 1e3 * t,
-                   "region_evals": st_["region_evals"], "eval_ms": st_["eval_ms"],
-                   "rule_n": c.options.rule_n, "cover": c.options.cover}
-            del o
-            c.close()
-            torch.cuda.empty_cache()
-            return blk, v_, s_
-
+    if args.path != "plain" and not args.no_compare:
+        # the plain FP64 GPU path (one partition per integral) on the same
+        # batch: with its own autotuned rule and cover, and with the library
+        # defaults; the metric's denominator
         c64 = P.Context(*w.lattice, ffset=ff, device=local, timing=1)
         if not args.no_autotune:
             t0 = time.perf_counter()
             c64.autotune([dict(d, q=d["q"][::6].contiguous()) for d in dbs])
             c64.release_workspace()
             tune64 = time.perf_counter() - t0
-        line["plain_fp64"], v64, s64 = timed_plain(c64)
+        line["plain_fp64"], v64, s64 = timed(c64, False, 1)
+        line["plain_fp64"]["path"] = PATHS["plain"]
+        c64.close()
+        torch.cuda.empty_cache()
         if not args.no_autotune:
             line["plain_fp64"]["autotune_seconds"] = tune64
-            line["plain_fp64_default"], _, _ = timed_plain(
-                P.Context(*w.lattice, ffset=ff, device=local, timing=1))
+            cd = P.Context(*w.lattice, ffset=ff, device=local, timing=1)
+            line["plain_fp64_default"], _, _ = timed(cd, False, 1)
+            cd.close()
+            torch.cuda.empty_cache()
             line["speedup_vs_plain_fp64_default"] = value / line["plain_fp64_default"]["value"]
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
         flat = W.flatten(w)
@@ -709,47 +755,6 @@ def run_paid(args):
         line["accuracy_vs_fp64_gpu"] = accuracy(vals, stats, v64, s64, w.batches[0].rel_tol,
                                                 w.batches[0].abs_tol, "FP64 GPU path, every integral",
                                                 ident_all, w.lattice)
-        if args.path == "group" and not args.no_learned:
-            # the learned proposal's form: one partition per integral seeded by
-            # the trained network, FP32 / float-float integrand, FP64 sums
-            from paper_1610_09991_gb300 import proposal as PR
-            lprop, lhist, lt = PR.train_default(device=local, n_draws=24, nq=8, epochs=20)
-            lrate, _ = PR.calibrate_default(lprop, device=local, eval_fp32=1, group_mode=0)
-            cl = P.Context(*w.lattice, ffset=ff, device=local, timing=1, eval_fp32=1)
-
-            def lstep():
-                flush.fill_(1)
-                return cl.integrate_multi_seeded(dbs, PR.predict(lprop, cl, dbs), lrate,
-                                                 stream=stream)
-
-            for _ in range(max(1, args.warmup)):
-                lstep()
-            torch.cuda.synchronize()
-            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            lsteps = min(args.steps, 2)   # ~3.3 s per step
-            l0.record(stream)
-            louts = [lstep() for _ in range(lsteps)]
-            l1.record(stream)
-            torch.cuda.synchronize()
-            tl = l0.elapsed_time(l1) / 1e3
-            lconv = sum(int((torch.cat([o.status for o in lo]) == 0).sum()) for lo in louts)
-            lv = torch.cat([o.values for o in louts[-1]]).cpu().numpy()
-            ls = torch.cat([o.status for o in louts[-1]]).cpu().numpy()
-            lval = lconv * world / tl
-            line["learned_fp32"] = {
-                "path": "learned proposal seeding + one partition per integral, FP32 / "
-                        "float-float integrand, FP64 sums",
-                "value": lval, "unit": UNIT, "ms_per_step": 1e3 * tl / lsteps, "steps": lsteps,
-                "speedup_vs_plain_fp64": lval / line["plain_fp64"]["value"],
-                "train_seconds": lt, "rate": lrate,
-                "loss_first_epoch": lhist[0], "loss_last_epoch": lhist[-1],
-                "accuracy_vs_fp64_gpu": accuracy(lv, ls, v64, s64, w.batches[0].rel_tol,
-                                                 w.batches[0].abs_tol,
-                                                 "FP64 GPU path, every integral", ident_all,
-                                                 w.lattice)}
-            del louts
-            cl.close()
-            torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, (idx, vo, so) = cpu_baseline(w, args.cpu_sample, rule_n=ctx.options.rule_n)
         line["cpu_baseline"] = cb

@@ -50,8 +50,18 @@
  *     are in `status` (paid_status).  paid_last_error() gives a message.
  *   - A context is used by one host thread at a time.
  *   - Output order of a batch: idx = iq * npairs + ip.
- *   - The integrate calls run their round loop from the host and return when
- *     the outputs are complete (they synchronise `stream`).
+ *   - With options.device_loop = 1 (the default) and timing = 0 the integrate
+ *     calls are asynchronous on `stream`: they queue the setup, the refinement
+ *     loop (one CUDA graph launch) and its finish, and return; their return
+ *     code covers argument and launch errors only.  Per-integral outcomes land
+ *     in `status` with the values; paid_wait() waits for the call and returns
+ *     its outcome (PAID_OK, PAID_ERR_POOL, PAID_ERR_TIMEOUT) and statistics.
+ *     paid_integrate_multi_seeded waits once, before the loop, for the size of
+ *     its seeded partition.  A call on a context whose previous call is still
+ *     pending first waits for that one (they share the loop state and graph).
+ *     With device_loop = 0 or timing = 1 the round loop runs from the host and
+ *     the calls return when the outputs are complete (they synchronise
+ *     `stream`), as do paid_integrate_batch_static and paid_rule_regions.
  *   - The region pool need not hold every integral at once: integrals enter
  *     it as room frees up, and when a round's splits would overflow it the
  *     integrals split in order while the growth fits and the rest wait a
@@ -124,9 +134,9 @@ typedef struct {
     int timing;             /* 1: time every kernel class with CUDA events on the call's stream
                                (totals in paid_stats); implies device_loop = 0. Default 0 */
     int device_loop;        /* 1: the refinement loop runs on the device as one CUDA graph launch
-                               (a conditional WHILE node around one round's kernels; the host
-                               waits once, at the end).  0: the host launches every round and
-                               reads its counts back.  Default 1 */
+                               (a conditional WHILE node around one round's kernels) and the
+                               integrate calls return without waiting (see paid_wait).  0: the
+                               host launches every round and reads its counts back.  Default 1 */
     int group_mode;         /* 1: one shared partition per (kind, q) of a batch serves all of the
                                batch's (l, m) pairs (at most 81; kinds ph, pp, overlap, flow).
                                A region evaluates the kernel F once per node and every pair from
@@ -191,15 +201,16 @@ int paid_create(paid_ctx** out, double t, double tp, double mu, int ffset,
 /* Release a context (NULL is allowed). */
 void paid_destroy(paid_ctx* ctx);
 
-/* Bytes of device workspace needed for `n_integrals` integrals and a pool of
- * `pool_capacity` regions (pool_capacity >= n_integrals * 4^init_level).
- * Returns PAID_OK and *bytes, or PAID_ERR_ARG. */
-int paid_workspace_size(paid_ctx* ctx, int64_t n_integrals, int64_t pool_capacity,
+/* Bytes of device workspace needed for `n_units` units of a call -- its
+ * integrals, or with options.group_mode its (kind, q) groups (the sum of the
+ * batches' nq) -- and a pool of `pool_capacity` regions (pool_capacity >=
+ * n_units * 4^init_level).  Returns PAID_OK and *bytes, or PAID_ERR_ARG. */
+int paid_workspace_size(paid_ctx* ctx, int64_t n_units, int64_t pool_capacity,
                         size_t* bytes);
 
 /* Largest pool capacity (regions) that `ws_bytes` of workspace holds for
- * `n_integrals` integrals.  Returns PAID_OK and *capacity (0 if none fits). */
-int paid_pool_capacity(paid_ctx* ctx, int64_t n_integrals, size_t ws_bytes,
+ * `n_units` units.  Returns PAID_OK and *capacity (0 if none fits). */
+int paid_pool_capacity(paid_ctx* ctx, int64_t n_units, size_t ws_bytes,
                        int64_t* capacity);
 
 /* One batch of integrals of one kind at one temperature.
@@ -218,7 +229,19 @@ int paid_integrate_batch(paid_ctx* ctx, int kind,
                          void* workspace, size_t ws_bytes, void* stream);
 
 /* Several batches (kinds and temperatures) drained together in one pool:
- * the argument meanings are those of paid_integrate_batch, per batch. */
+ * the argument meanings are those of paid_integrate_batch, per batch.
+ *
+ * tu_v, tu_out: the truncated-unity right-hand sides of the flow equations
+ * (Eqs. matmul-P, matmul-C, matmul-D, Sec. 2) formed in the same call, as each
+ * (kind, q) group finishes, from its bubble matrix X[l][m] (the group's values
+ * of pair l * nff + m) -- only for the flow kinds with options.group_mode and
+ * every pair (l, m), l-major (npairs = nff^2); NULL pointers: no products.
+ *   PAID_FLOW_PP: tu_v[0] = V^P, tu_out[0] = dP = V^P X V^P;
+ *   PAID_FLOW_PH: tu_v[0] = V^C, tu_v[1] = V^D, tu_out[0] = dC = -V^C X V^C,
+ *                 tu_out[1] = dD = 2 V^D X V^D - V^C X V^D - V^D X V^C;
+ * all device double [nq][nff][nff], row-major, the outputs not aliasing the
+ * inputs.  A batch whose pairs are not in that order gets NaN products; a
+ * group the call never started gets NaN products. */
 typedef struct {
     int kind;
     double T;
@@ -233,6 +256,8 @@ typedef struct {
     double* errors;
     int64_t* regions;
     int32_t* status;
+    const double* tu_v[2];
+    double* tu_out[2];
 } paid_batch;
 
 int paid_integrate_multi(paid_ctx* ctx, const paid_batch* batches, int nb,
@@ -457,7 +482,15 @@ int paid_proposal_train(float* params, float* m, float* v, const uint16_t* x, co
 int paid_proposal_save(const float* params, const char* path, void* stream);
 int paid_proposal_load(float* params, const char* path, void* stream);
 
-/* Statistics of the last integrate call.  Returns PAID_OK or PAID_ERR_ARG. */
+/* Waits for the last integrate call on ctx (a no-op for a synchronous one)
+ * and writes its outcome to *call_rc (may be NULL): PAID_OK, PAID_ERR_POOL
+ * (the pool could make no progress; unfinished integrals have status
+ * PAID_POOL), PAID_ERR_TIMEOUT (round cap) or PAID_ERR_CUDA.  Returns PAID_OK,
+ * or PAID_ERR_CUDA / PAID_ERR_ARG when waiting itself fails. */
+int paid_wait(paid_ctx* ctx, int* call_rc);
+
+/* Statistics of the last integrate call (waits for it when it is still
+ * pending).  Returns PAID_OK or PAID_ERR_ARG. */
 int paid_last_stats(paid_ctx* ctx, paid_stats* out);
 
 /* Static message for a paid_rc. */

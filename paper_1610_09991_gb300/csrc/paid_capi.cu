@@ -40,6 +40,7 @@ struct LoopGraph {
     int nb = 0, vstride = 0;
     int rule_n = 0, eval_fp32 = 0, max_rounds = 0, eval_blocks = 0;
     const float* tmap = nullptr;       // trace buffer it writes (null: none)
+    int kinds = 0;                     // the kernel F variant it launches
     double cover = 0.0;
 };
 
@@ -57,6 +58,11 @@ struct paid_ctx {
     paid_stats stats{};
     float* trace_buf = nullptr;        // paid_set_trace_buffer
     int64_t trace_units = 0;
+    // the outcome of an asynchronous call (device loop): read by paid_wait
+    cudaEvent_t done = nullptr;        // recorded after the copy of the final loop state
+    bool pending = false;
+    int64_t pend_n = 0, pend_cap = 0;
+    int last_rc = PAID_OK;
 };
 
 namespace {
@@ -192,6 +198,8 @@ int64_t capacity_for(int64_t n, size_t ws_bytes, bool group)
     return cap;
 }
 
+int settle(paid_ctx* ctx, bool no_alloc);
+
 int fail(paid_ctx* ctx, int rc, const std::string& msg)
 {
     if (ctx) ctx->last_error = msg;
@@ -302,6 +310,10 @@ int paid_create(paid_ctx** out, double t, double tp, double mu, int ffset,
             return PAID_ERR_CUDA;
         }
     }
+    if (cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
+        paid_destroy(c);
+        return PAID_ERR_CUDA;
+    }
     *out = c;
     return PAID_OK;
 }
@@ -316,6 +328,10 @@ void paid_destroy(paid_ctx* ctx)
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
     for (auto e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->done) {
+        if (ctx->pending) cudaEventSynchronize(ctx->done);
+        cudaEventDestroy(ctx->done);
+    }
     delete ctx;
 }
 
@@ -339,8 +355,18 @@ int paid_pool_capacity(paid_ctx* ctx, int64_t n_integrals, size_t ws_bytes, int6
 int paid_last_stats(paid_ctx* ctx, paid_stats* out)
 {
     if (!ctx || !out) return PAID_ERR_ARG;
+    settle(ctx, false);
     *out = ctx->stats;
     return PAID_OK;
+}
+
+int paid_wait(paid_ctx* ctx, int* call_rc)
+{
+    if (!ctx) return PAID_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    const int rc = settle(ctx, false);
+    if (call_rc) *call_rc = ctx->last_rc;
+    return rc;
 }
 
 }  // extern "C"
@@ -365,6 +391,14 @@ const char* batch_error(const paid_batch& b, int64_t nl0, bool group)
         return "max_regions must be in [4^init_level, 2^23]";
     if (group && b.kind == PAID_MONOMIAL) return "group_mode takes the ph, pp, overlap and flow kinds";
     if (group && b.npairs > kGroupPairs) return "group_mode takes at most 81 pairs per batch";
+    const bool tu = b.tu_v[0] || b.tu_v[1] || b.tu_out[0] || b.tu_out[1];
+    if (tu) {
+        if (!group || !flow) return "truncated-unity products take the flow kinds in group_mode";
+        const bool pp = b.kind == PAID_FLOW_PP;
+        if (!b.tu_v[0] || !b.tu_out[0] || (pp ? (b.tu_v[1] || b.tu_out[1])
+                                              : (!b.tu_v[1] || !b.tu_out[1])))
+            return "truncated-unity products: flow pp takes tu_v[0], tu_out[0]; flow ph all four";
+    }
     return nullptr;
 }
 
@@ -373,6 +407,9 @@ const char* batch_error(const paid_batch& b, int64_t nl0, bool group)
 int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, size_t ws_bytes,
             int64_t n0, cudaStream_t s, Work& w, int64_t& n, int64_t& cap, bool group)
 {
+    // an earlier asynchronous call on this context completes first: its loop
+    // state and the graph are shared with this call
+    settle(ctx, false);
     ctx->last_error.clear();
     ctx->stats = paid_stats{};
     if (nb < 0 || nb > kMaxBatches || (nb > 0 && !batches))
@@ -406,6 +443,13 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
         d.errors = b.errors;
         d.regions = b.regions;
         d.status = b.status;
+        d.tu_v0 = b.tu_v[0];
+        d.tu_v1 = b.tu_v[1];
+        d.tu_out0 = b.tu_out[0];
+        d.tu_out1 = b.tu_out[1];
+        if (d.tu_out0 && int64_t(b.npairs) != int64_t(ctx->nff) * ctx->nff)
+            return fail(ctx, PAID_ERR_ARG, "truncated-unity products need every pair (l, m), "
+                                           "npairs = nff^2");
         hb.push_back(d);
         n += group ? int64_t(b.nq) : nbi;
         n_int += nbi;
@@ -426,6 +470,9 @@ int prepare(paid_ctx* ctx, const paid_batch* batches, int nb, void* workspace, s
     const Layout L = layout(n, cap, group);
     w = make_work(static_cast<char*>(workspace), L, n, cap, int(hb.size()), group, ctx->nff);
     w.gglobal = group && ctx->opt.group_mode == 2;
+    bool any_flow = false, any_other = false;
+    for (const DevBatch& d : hb) (is_flow(d.kind) ? any_flow : any_other) = true;
+    w.kinds = any_flow && any_other ? 0 : (any_flow ? 2 : 1);
     cudaError_t e = cudaMemcpyAsync(w.batches, hb.data(), sizeof(DevBatch) * hb.size(),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
@@ -494,7 +541,7 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     if (G.exec && G.base == w.batches && G.n == w.n && G.cap == w.cap && G.nb == w.nb &&
         G.vstride == w.vstride &&
         G.rule_n == o.rule_n && G.eval_fp32 == o.eval_fp32 && G.max_rounds == o.max_rounds &&
-        G.eval_blocks == o.eval_blocks && G.tmap == w.tmap &&
+        G.eval_blocks == o.eval_blocks && G.tmap == w.tmap && G.kinds == w.kinds &&
         G.cover == o.cover) {
         *out = G.exec;
         return PAID_OK;
@@ -553,8 +600,61 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
     G.max_rounds = o.max_rounds;
     G.eval_blocks = o.eval_blocks;
     G.tmap = w.tmap;
+    G.kinds = w.kinds;
     G.cover = o.cover;
     *out = exec;
+    return PAID_OK;
+}
+
+// Statistics and return code of a finished loop from its final state.
+int loop_outcome(paid_ctx* ctx, const LoopState& L, const RoundTotals& t, int64_t cap,
+                 bool no_alloc)
+{
+    const paid_options& o = ctx->opt;
+    paid_stats& st = ctx->stats;
+    st.rounds = L.rounds_done;
+    st.region_evals = L.region_evals;
+    st.peak_pool = L.peak_pool;
+    st.throttled_rounds = L.throttled_rounds;
+    st.escalated = int64_t(t.escalated);
+    st.df_regions = int64_t(t.df_regions);
+    st.node_evals = st.region_evals * int64_t(2 * o.rule_n + 1) * (2 * o.rule_n + 1);
+    st.pool_capacity = cap;
+    if (st.graph_launches) {
+        st.launches += int64_t(L.rounds_done) * round_kernels(o, 1, 1, true);
+        st.eval_launches += L.rounds_done;
+    }
+    // (the allocation-free entry point keeps the message alone: no strings)
+    auto rfail = [&](int rc, const char* msg) { return no_alloc ? rc : fail(ctx, rc, msg); };
+    switch (L.stop) {
+    case kDone:
+        return t.roundcap > 0 ? rfail(PAID_ERR_TIMEOUT, "round cap reached") : int(PAID_OK);
+    case kStuck:
+        if (no_alloc) return PAID_ERR_POOL;
+        return fail(ctx, PAID_ERR_POOL, "region pool full (capacity " + std::to_string(cap) + ")");
+    case kNoRoom:
+        return rfail(PAID_ERR_POOL, "region pool too small for one integral's start");
+    case kHardCap:
+        return rfail(PAID_ERR_TIMEOUT, "round cap reached");
+    default:
+        return rfail(PAID_ERR_CUDA, "device loop ended without a stop decision");
+    }
+}
+
+// Completes an asynchronous call still pending on ctx: waits for its final
+// loop state, then records its statistics and outcome (ctx->last_rc).
+int settle(paid_ctx* ctx, bool no_alloc)
+{
+    if (!ctx->pending) return PAID_OK;
+    ctx->pending = false;
+    const cudaError_t e = cudaEventSynchronize(ctx->done);
+    if (e != cudaSuccess) {
+        ctx->last_rc = no_alloc ? int(PAID_ERR_CUDA) : cuda_fail(ctx, e, "device loop");
+        return ctx->last_rc;
+    }
+    const LoopState L = *ctx->h_state;
+    const RoundTotals t = *ctx->h_totals;
+    ctx->last_rc = loop_outcome(ctx, L, t, ctx->pend_cap, no_alloc);
     return PAID_OK;
 }
 
@@ -563,9 +663,10 @@ int loop_graph(paid_ctx* ctx, const Work& w, cudaGraphExec_t* out)
 // (uniform level-L0 start) as room frees up.  In a round whose splits would
 // overflow the pool, integrals split in slot order while the growth fits and
 // the rest wait a round unsplit; only a round that can neither grow nor
-// retire anything ends the call with PAID_ERR_POOL.  no_alloc = true (the
-// allocation-free entry point) keeps the loop on the host, since building a
-// graph allocates, and leaves the error message alone.
+// retire anything ends the call with PAID_ERR_POOL.  With the device loop the
+// call only queues its work and returns (paid_wait reads the outcome);
+// no_alloc = true (the allocation-free entry point) keeps the loop on the
+// host, since building a graph allocates, and leaves the error message alone.
 int run_loop(paid_ctx* ctx, const Work& w, int64_t admitted, int64_t n_eval, int64_t pool, int L0,
              cudaStream_t s, bool no_alloc = false)
 {
@@ -576,7 +677,6 @@ int run_loop(paid_ctx* ctx, const Work& w, int64_t admitted, int64_t n_eval, int
     auto cfail = [&](cudaError_t e, const char* where) {
         return no_alloc ? int(PAID_ERR_CUDA) : cuda_fail(ctx, e, where);
     };
-    auto rfail = [&](int rc, const char* msg) { return no_alloc ? rc : fail(ctx, rc, msg); };
     // the loop's own bound: every integral has at most max_rounds rounds from
     // its admission; streaming admission spreads them over more rounds
     const int hard = admitted >= n ? o.max_rounds
@@ -605,81 +705,75 @@ int run_loop(paid_ctx* ctx, const Work& w, int64_t admitted, int64_t n_eval, int
     LoopState L{};
     RoundTotals t{};
     if (graph) {
+        // asynchronous: the loop, the device-decided finish and the copy of the
+        // final loop state are queued; paid_wait reads the outcome
         cudaGraphExec_t exec = nullptr;
         const int rc = loop_graph(ctx, w, &exec);
         if (rc != PAID_OK) return rc;
         if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cfail(e, "graph launch");
+        if ((e = launch_finish_device(w, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ctx->h_state, w.ls, sizeof(LoopState), cudaMemcpyDeviceToHost,
+                                 s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ctx->h_totals, w.totals, sizeof(RoundTotals),
+                                 cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaEventRecord(ctx->done, s)) != cudaSuccess)
+            return cfail(e, "device loop");
         st.graph_launches = 1;
-        if ((e = read_state(L, t)) != cudaSuccess) return cfail(e, "device loop");
-        st.launches += int64_t(L.rounds_done) * round_kernels(o, 1, 1, true);
-        st.eval_launches += L.rounds_done;
-    } else {
-        L.n_eval = n_eval;
-        L.n_active = admitted;
-        for (;;) {
-            const int64_t ne = L.n_eval, na = L.n_active;
-            if ((e = launch_round(ctx, w, ne, na, o.group_mode ? w.cap : 0, 0, 0, s,
-                                  timed ? ev : nullptr)) != cudaSuccess)
-                return cfail(e, "round");
-            st.launches += round_kernels(o, ne, na, false);
-            st.eval_launches += ne > 0 ? 1 : 0;
-            if ((e = read_state(L, t)) != cudaSuccess) return cfail(e, "round sync");
-            if (timed) {
-                st.eval_ms += span(0, 1);
-                if (o.eval_fp32 && !o.group_mode && ne > 0) st.df_ms += span(6, 1);
-                st.reduce_ms += span(1, 2);
-                st.scan_ms += span(2, 3);
-                st.split_ms += span(3, 4);
-            }
-            if (L.stop != kRunning) break;
-            if (L.wave_g1 > L.wave_g0) {
-                if ((e = launch_setup_wave(w, L.wave_g1 - L.wave_g0, ctx->nff, o.eval_fp32 ? 0 : 1,
-                                           s)) != cudaSuccess)
-                    return cfail(e, "admit");
-                st.launches += 1;
-            }
+        st.launches += w.vstride > 0 ? 3 : 2;
+        ctx->pending = true;
+        ctx->pend_n = n;
+        ctx->pend_cap = cap;
+        return PAID_OK;
+    }
+    L.n_eval = n_eval;
+    L.n_active = admitted;
+    for (;;) {
+        const int64_t ne = L.n_eval, na = L.n_active;
+        if ((e = launch_round(ctx, w, ne, na, o.group_mode ? w.cap : 0, 0, 0, s,
+                              timed ? ev : nullptr)) != cudaSuccess)
+            return cfail(e, "round");
+        st.launches += round_kernels(o, ne, na, false);
+        st.eval_launches += ne > 0 ? 1 : 0;
+        if ((e = read_state(L, t)) != cudaSuccess) return cfail(e, "round sync");
+        if (timed) {
+            st.eval_ms += span(0, 1);
+            if (o.eval_fp32 && !o.group_mode && ne > 0) st.df_ms += span(6, 1);
+            st.reduce_ms += span(1, 2);
+            st.scan_ms += span(2, 3);
+            st.split_ms += span(3, 4);
+        }
+        if (L.stop != kRunning) break;
+        if (L.wave_g1 > L.wave_g0) {
+            if ((e = launch_setup_wave(w, L.wave_g1 - L.wave_g0, ctx->nff, o.eval_fp32 ? 0 : 1,
+                                       s)) != cudaSuccess)
+                return cfail(e, "admit");
+            st.launches += 1;
         }
     }
-    st.rounds = L.rounds_done;
-    st.region_evals = L.region_evals;
-    st.peak_pool = L.peak_pool;
-    st.throttled_rounds = L.throttled_rounds;
-    st.escalated = int64_t(t.escalated);
-    st.df_regions = int64_t(t.df_regions);
-    st.node_evals = st.region_evals * int64_t(2 * o.rule_n + 1) * (2 * o.rule_n + 1);
-    st.pool_capacity = cap;
-    int rc = PAID_OK;
     switch (L.stop) {
-    case kDone:
-        if (t.roundcap > 0) rc = rfail(PAID_ERR_TIMEOUT, "round cap reached");
-        break;
     case kStuck:
         if ((e = launch_finalize(w, L.n_active, POOL, s)) != cudaSuccess ||
             (e = launch_mark_unadmitted(w, L.admitted, n, POOL, s)) != cudaSuccess)
             return cfail(e, "finalize");
         st.launches += 2;
-        rc = no_alloc ? int(PAID_ERR_POOL)
-                      : fail(ctx, PAID_ERR_POOL,
-                             "region pool full (capacity " + std::to_string(cap) + ")");
         break;
     case kNoRoom:
         if ((e = launch_mark_unadmitted(w, L.admitted, n, POOL, s)) != cudaSuccess)
             return cfail(e, "finalize");
         st.launches += 1;
-        rc = rfail(PAID_ERR_POOL, "region pool too small for one integral's start");
         break;
     case kHardCap:
         if ((e = launch_mark_unadmitted(w, L.admitted, n, ROUNDCAP, s)) != cudaSuccess)
             return cfail(e, "finalize");
         st.launches += 1;
-        rc = rfail(PAID_ERR_TIMEOUT, "round cap reached");
         break;
     default:
-        return rfail(PAID_ERR_CUDA, "device loop ended without a stop decision");
+        break;
     }
     if (L.stop != kDone && (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cfail(e, "finalize sync");
-    return rc;
+    ctx->last_rc = loop_outcome(ctx, L, t, cap, no_alloc);
+    return ctx->last_rc;
 }
 
 }  // namespace
@@ -824,6 +918,7 @@ int paid_rule_regions(paid_ctx* ctx, int kind, double T, const double* q, int np
     DeviceGuard guard(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Work w = make_work(static_cast<char*>(workspace), Lw, 1, nreg, 1, false, ctx->nff);
+    w.kinds = is_flow(kind) ? 2 : 1;
     DevBatch d{};
     d.kind = kind;
     d.nq = 1;
@@ -988,14 +1083,17 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
         ctx->opt.cover = c;
         ctx->opt.eval_blocks = g;
         if (!warm) {   // first call: graph capture, tables, caches
-            paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+            if (paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream) == PAID_OK)
+                paid_wait(ctx, nullptr);
             warm = true;
         }
         cudaEventRecord(e0, s);
-        const int rc = paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
+        int rc = paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream);
         cudaEventRecord(e1, s);
         float ms = 0.f;
-        if (rc != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
+        int outcome = PAID_OK;
+        if (rc == PAID_OK) rc = paid_wait(ctx, &outcome);
+        if (rc != PAID_OK || outcome != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
             return;
         if (ms < best_ms) { best_ms = ms; best_cover = c; best_blocks = g; best_rule = rn; }
@@ -1045,7 +1143,7 @@ int paid_integrate_batch(paid_ctx* ctx, int kind, int nq, const double* q, int n
                          int64_t max_regions, double* values, double* errors, int64_t* regions,
                          int32_t* status, void* workspace, size_t ws_bytes, void* stream)
 {
-    paid_batch b;
+    paid_batch b{};
     b.kind = kind;
     b.T = T;
     b.nq = nq;
@@ -1140,6 +1238,8 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     b.status = status;
     // the same argument rules as paid_integrate_batch
     if (batch_error(b, n0, group)) return PAID_ERR_ARG;
+    // an earlier asynchronous call on this context completes first
+    if (settle(ctx, true) != PAID_OK) return PAID_ERR_CUDA;
     const int64_t n = int64_t(nq) * npairs;
     if (n > kStaticMaxIntegrals) return PAID_ERR_ARG;
     ctx->stats = paid_stats{};
@@ -1159,6 +1259,7 @@ extern "C" int paid_integrate_batch_static(paid_ctx* ctx, int kind, int nq, cons
     char* base = static_cast<char*>(scratch);
     Work w = make_work(base, L, units, cap, 1, group, ctx->nff);
     w.gglobal = group && o.group_mode == 2;
+    w.kinds = is_flow(kind) ? 2 : 1;
 
     // The scratch keeps whatever the previous call left in it.  Every array
     // is written before it is read within a call; the totals block is cleared

@@ -54,6 +54,8 @@ __constant__ int c_ffa[9][2];
 __constant__ int c_ffb[9][2];
 __constant__ double c_ffc[9][2];
 __constant__ double c_exp2d[64];                  // 2^(j/64), j = 0..63 (FP64 exp of the group path)
+// c_ffc[l][k1] c_ffc[m][k2] as float-float pairs (the FP32-pipe group kernel)
+__constant__ float2 c_ffpair[9][2][9][2];
 
 // Clenshaw-Curtis weights for n intervals (n even), from the cosine-series
 // form of the rule: w_j = (c_j / n) (1 - sum_{k=1}^{n/2} b_k cos(2 k j pi/n)/(4k^2 - 1)).
@@ -162,6 +164,12 @@ cudaError_t init_rule_tables(int device)
     if ((e = cudaMemcpyToSymbol(c_ffa, ffa, sizeof(ffa))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_ffb, ffb, sizeof(ffb))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_ffc, ffc, sizeof(ffc))) != cudaSuccess) return e;
+    float2 ffpair[9][2][9][2] = {};
+    for (int l = 0; l < 9; ++l)
+        for (int k1 = 0; k1 < 2; ++k1)
+            for (int m = 0; m < 9; ++m)
+                for (int k2 = 0; k2 < 2; ++k2) ffpair[l][k1][m][k2] = split(ffc[l][k1] * ffc[m][k2]);
+    if ((e = cudaMemcpyToSymbol(c_ffpair, ffpair, sizeof(ffpair))) != cudaSuccess) return e;
     double e2d[64];
     for (int j = 0; j < 64; ++j) e2d[j] = std::exp2(j / 64.0);
     if ((e = cudaMemcpyToSymbol(c_exp2d, e2d, sizeof(e2d))) != cudaSuccess) return e;
@@ -1230,81 +1238,19 @@ struct GroupSmem {
     double tab[64];          // 2^(j/64)
 };
 
-// The FP32-pipe variant: every per-node and per-row quantity in float-float,
-// the column data with the column's rule weight folded in (fine, and coarse on
-// the even columns); the moments reuse the column data's memory once the row
-// sums are done.
 template <int N>
-struct GroupSmemF {
-    static constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
-    float2 X[R][NF][9];          // X_ac at the fine rows
-    union {
-        struct {
-            float2 Yf[R][NF][9];     // wf_j Y_bd(y_j)
-            float2 Yc[R][N + 1][9];  // wc_j Y_bd(y_2j)
-            float2 CY[R][NF][2];     // cos ky, cos ky' (flow kinds: cos(ky +- qy/2))
-        } c;
-        struct {
-            double Mf[R][9][9];
-            double Mc[R][9][9];
-        } m;
-    } u;
-    float2 Rf[R][NF][9];         // row sums with the row's fine weight
-    float2 Rc[R][N + 1][9];      // coarse (even rows)
-    double C[R][4];
-    float2 tab[64];              // 2^(j/64) as float-float
-    float2 wr[NF];               // fine row weights, float-float
-    float2 wrc[N + 1];           // coarse row weights
-};
-
-template <int N>
-__device__ __forceinline__ auto& group_Mf(GroupSmem<N>& S) { return S.Mf; }
-template <int N>
-__device__ __forceinline__ auto& group_Mc(GroupSmem<N>& S) { return S.Mc; }
-template <int N>
-__device__ __forceinline__ auto& group_Mf(GroupSmemF<N>& S) { return S.u.m.Mf; }
-template <int N>
-__device__ __forceinline__ auto& group_Mc(GroupSmemF<N>& S) { return S.u.m.Mc; }
-
-template <int N, int PREC>
-using GroupSmemOf = typename std::conditional<PREC == 0, GroupSmem<N>, GroupSmemF<N>>::type;
-
-__device__ __forceinline__ f2 ff_ld(float2 v) { return {v.x, v.y}; }
-__device__ __forceinline__ float2 ff_st(f2 a) { return make_float2(a.hi, a.lo); }
-
-// PREC 0: everything FP64.  PREC 1 (options.eval_fp32): the kernel F, the row
-// sums and the moments in float-float on the FP32 pipe; each region's pair
-// values Q_2N, Q_N, their difference and every total in FP64.
-template <int N, int PREC>
 __global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1))
 k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
 {
     constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using Smem = GroupSmemOf<N, PREC>;
-    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    GroupSmem<N>& S = *reinterpret_cast<GroupSmem<N>*>(smem_raw);
     const int v = rule_variant(N);
     const int cur = w.ls->cur;
     const int64_t n_eval = w.ls->n_eval;
     const int rho = threadIdx.x / NF, i = threadIdx.x % NF;
     const double tA = -2.0 * lat.t, tB = -4.0 * lat.tp;
-    if constexpr (PREC == 0) {
-        if (threadIdx.x < 64) S.tab[threadIdx.x] = c_exp2d[threadIdx.x];
-    } else {
-        if (threadIdx.x < 64) {
-            const double x = c_exp2d[threadIdx.x];
-            const float h = __double2float_rn(x);
-            S.tab[threadIdx.x] = make_float2(h, __double2float_rn(x - double(h)));
-        }
-        if (threadIdx.x < NF) {
-            const f2 a = ff_from(c_wf[v][threadIdx.x]);
-            S.wr[threadIdx.x] = make_float2(a.hi, a.lo);
-        }
-        if (threadIdx.x <= N) {
-            const f2 a = ff_from(c_wc[v][threadIdx.x]);
-            S.wrc[threadIdx.x] = make_float2(a.hi, a.lo);
-        }
-    }
+    if (threadIdx.x < 64) S.tab[threadIdx.x] = c_exp2d[threadIdx.x];
     for (int64_t chunk = blockIdx.x; chunk * R < n_eval; chunk += gridDim.x) {
         const int64_t t = chunk * R + rho;
         const bool live = t < n_eval;
@@ -1348,66 +1294,27 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
             // flow kinds: both form factors at k (symmetric routing)
             const double gx[3] = {1.0, cx, sx};
             const double gx2[3] = {1.0, flow ? cx : cx2, flow ? sx : sx2};
-            if constexpr (PREC == 1) {
-                const f2 one = {1.0f, 0.0f};
-                const f2 fcx = ff_from(cx), fsx = ff_from(sx);
-                const f2 fx[3] = {one, fcx, fsx};
-                const f2 fx2[3] = {one, flow ? fcx : ff_from(cx2), flow ? fsx : ff_from(sx2)};
+            const double gy[3] = {1.0, cy, sy};
+            const double gy2[3] = {1.0, flow ? cy : cy2, flow ? sy : sy2};
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
+            for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        S.X[rho][i][3 * a + c] =
-                            ff_st(a == 0 ? fx2[c] : (c == 0 ? fx[a] : ff_mul(fx[a], fx2[c])));
-            } else {
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) S.X[rho][i][3 * a + c] = gx[a] * gx2[c];
-            }
-            if constexpr (PREC == 0) {
-                const double gy[3] = {1.0, cy, sy};
-                const double gy2[3] = {1.0, flow ? cy : cy2, flow ? sy : sy2};
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) S.Y[rho][i][3 * a + c] = gy[a] * gy2[c];
-            } else {
-                // Y_bd(y_i) in float-float, times the column's fine and coarse weights
-                const f2 one = {1.0f, 0.0f};
-                const f2 fcy = ff_from(cy), fsy = ff_from(sy);
-                const f2 gy[3] = {one, fcy, fsy};
-                const f2 gy2[3] = {one, flow ? fcy : ff_from(cy2), flow ? fsy : ff_from(sy2)};
-                const float2 wj = S.wr[i];
-                const f2 wf = {wj.x, wj.y};
-                f2 wc = {0.0f, 0.0f};
-                if ((i & 1) == 0) { const float2 c = S.wrc[i >> 1]; wc = {c.x, c.y}; }
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const f2 y = (a == 0) ? gy2[c] : (c == 0 ? gy[a] : ff_mul(gy[a], gy2[c]));
-                        const f2 yf = ff_mul(wf, y);
-                        S.u.c.Yf[rho][i][3 * a + c] = make_float2(yf.hi, yf.lo);
-                        if ((i & 1) == 0) {
-                            const f2 yc = ff_mul(wc, y);
-                            S.u.c.Yc[rho][i >> 1][3 * a + c] = make_float2(yc.hi, yc.lo);
-                        }
-                    }
-            }
-            double cy_a, cy_b;
+                for (int c = 0; c < 3; ++c) {
+                    S.X[rho][i][3 * a + c] = gx[a] * gx2[c];
+                    S.Y[rho][i][3 * a + c] = gy[a] * gy2[c];
+                }
             if (flow) {
                 // e(k + q/2) and e(k - q/2): cos(k +- q/2) = cos k cos q/2 -+ sin k sin q/2
                 const double cxp = fma(cx, tq.cqx, -sx * tq.sqx), cxm = fma(cx, tq.cqx, sx * tq.sqx);
-                cy_a = fma(cy, tq.cqy, -sy * tq.sqy);
-                cy_b = fma(cy, tq.cqy, sy * tq.sqy);
+                S.CY[rho][i][0] = fma(cy, tq.cqy, -sy * tq.sqy);
+                S.CY[rho][i][1] = fma(cy, tq.cqy, sy * tq.sqy);
                 A1 = fma(tA, cxp, -lat.mu);
                 B1 = fma(tB, cxp, tA);
                 A2 = fma(tA, cxm, -lat.mu);
                 B2 = fma(tB, cxm, tA);
             } else {
-                cy_a = cy;
-                cy_b = cy2;
+                S.CY[rho][i][0] = cy;
+                S.CY[rho][i][1] = cy2;
                 // x = e / 2T = A + B cos ky along row i, for k and for k' (for pp
                 // the second energy enters with its sign flipped)
                 const double h1 = B->inv2T, h2 = pp ? -B->inv2T : B->inv2T;
@@ -1416,128 +1323,55 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 A2 = fma(tA, cx2, -lat.mu) * h2;
                 B2 = fma(tB, cx2, tA) * h2;
             }
-            if constexpr (PREC == 0) {
-                S.CY[rho][i][0] = cy_a;
-                S.CY[rho][i][1] = cy_b;
-            } else {
-                const f2 a = ff_from(cy_a), b = ff_from(cy_b);
-                S.u.c.CY[rho][i][0] = make_float2(a.hi, a.lo);
-                S.u.c.CY[rho][i][1] = make_float2(b.hi, b.lo);
-            }
         }
         __syncthreads();
         if (live) {
-            if constexpr (PREC == 0) {
-                double rf[9], rc[9];
+            double rf[9], rc[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) { rf[k] = 0.0; rc[k] = 0.0; }
+            for (int k = 0; k < 9; ++k) { rf[k] = 0.0; rc[k] = 0.0; }
 #pragma unroll
-                for (int j = 0; j < NF; ++j) {
-                    // OVERLAP: 1; bubbles: 2T F (1/2T is in the Jacobian); flow: dF/dOmega
-                    double F = 1.0;
-                    const double x1 = fma(B1, S.CY[rho][j][0], A1);
-                    const double x2 = fma(B2, S.CY[rho][j][1], A2);
-                    if (is_flow(kind))
-                        F = flow_Fdot(x1, x2, B->T, kind == FLOW_PP);
-                    else if (kind != OVERLAP)
-                        F = bubble_F2T(x1, x2, S.tab);
-                    const double wf = c_wf[v][j] * F;
+            for (int j = 0; j < NF; ++j) {
+                // OVERLAP: 1; bubbles: 2T F (1/2T is in the Jacobian); flow: dF/dOmega
+                double F = 1.0;
+                const double x1 = fma(B1, S.CY[rho][j][0], A1);
+                const double x2 = fma(B2, S.CY[rho][j][1], A2);
+                if (is_flow(kind))
+                    F = flow_Fdot(x1, x2, B->T, kind == FLOW_PP);
+                else if (kind != OVERLAP)
+                    F = bubble_F2T(x1, x2, S.tab);
+                const double wf = c_wf[v][j] * F;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) rf[k] = fma(wf, S.Y[rho][j][k], rf[k]);
-                    if ((j & 1) == 0) {
-                        const double wc = c_wc[v][j >> 1] * F;
+                for (int k = 0; k < 9; ++k) rf[k] = fma(wf, S.Y[rho][j][k], rf[k]);
+                if ((j & 1) == 0) {
+                    const double wc = c_wc[v][j >> 1] * F;
 #pragma unroll
-                        for (int k = 0; k < 9; ++k) rc[k] = fma(wc, S.Y[rho][j][k], rc[k]);
-                    }
+                    for (int k = 0; k < 9; ++k) rc[k] = fma(wc, S.Y[rho][j][k], rc[k]);
                 }
-                // the row's own rule weight (fine, and coarse on the even rows)
-                // goes into its sums, so the moments below are plain dot products
-                const double wr = c_wf[v][i];
+            }
+            // the row's own rule weight (fine, and coarse on the even rows)
+            // goes into its sums, so the moments below are plain dot products
+            const double wr = c_wf[v][i];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = wr * rf[k];
-                if ((i & 1) == 0) {
-                    const double wrc = c_wc[v][i >> 1];
+            for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = wr * rf[k];
+            if ((i & 1) == 0) {
+                const double wrc = c_wc[v][i >> 1];
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) S.Rc[rho][i >> 1][k] = wrc * rc[k];
-                }
-            } else {
-                const f2 fA1 = ff_from(A1), fB1 = ff_from(B1), fA2 = ff_from(A2), fB2 = ff_from(B2);
-                const f2 W = ff_from(B->T);
-                f2 rf[9], rc[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) { rf[k] = {0.0f, 0.0f}; rc[k] = {0.0f, 0.0f}; }
-                // one node (i, j): the kernel F once, then every row sum
-                auto node = [&](int j, bool even) {
-                    const f2 x1 = ff_fma(fB1, ff_ld(S.u.c.CY[rho][j][0]), fA1);
-                    const f2 x2 = ff_fma(fB2, ff_ld(S.u.c.CY[rho][j][1]), fA2);
-                    f2 F = {1.0f, 0.0f};
-                    if (is_flow(kind))
-                        F = flow_Fdot_ff(x1, x2, W, kind == FLOW_PP);
-                    else if (kind != OVERLAP)
-                        F = bubble_F2T_ff(x1, x2, S.tab);
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yf[rho][j][k]), rf[k]);
-                    if (even) {
-#pragma unroll
-                        for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yc[rho][j >> 1][k]), rc[k]);
-                    }
-                };
-                // two columns per trip (even, then odd) keeps the coarse-rule
-                // columns static without unrolling all 2N+1 nodes of the row:
-                // the float-float node is ~400 instructions, and a fully
-                // unrolled row overflows the instruction cache
-#pragma unroll 1
-                for (int j = 0; j < 2 * N; j += 2) {
-                    node(j, true);
-                    node(j + 1, false);
-                }
-                node(2 * N, true);
-                // the row weight in float-float; one value per sum
-                const f2 wr = ff_ld(S.wr[i]);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const f2 r = ff_mul(wr, ff_fast(rf[k].hi, rf[k].lo));
-                    S.Rf[rho][i][k] = ff_st(r);
-                }
-                if ((i & 1) == 0) {
-                    const f2 wrc = ff_ld(S.wrc[i >> 1]);
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) {
-                        const f2 r = ff_mul(wrc, ff_fast(rc[k].hi, rc[k].lo));
-                        S.Rc[rho][i >> 1][k] = ff_st(r);
-                    }
-                }
+                for (int k = 0; k < 9; ++k) S.Rc[rho][i >> 1][k] = wrc * rc[k];
             }
         }
         __syncthreads();
-        auto& Mf = group_Mf(S);
-        auto& Mc = group_Mc(S);
         if (live) {
             // moments M[ac][bd]: the 81 (ac, bd) cells dealt over the region's
             // NF threads (all of them busy, rather than one thread per ac)
             for (int u = i; u < 81; u += NF) {
                 const int ac = u / 9, bd = u - 9 * (u / 9);
-                if constexpr (PREC == 1) {
-                    // float-float dot products on the FP32 pipe, one FP64 value each
-                    f2 mf = {0.0f, 0.0f}, mc = {0.0f, 0.0f};
+                double mf = 0.0, mc = 0.0;
 #pragma unroll
-                    for (int r = 0; r < NF; ++r)
-                        ff_acc(ff_ld(S.X[rho][r][ac]), ff_ld(S.Rf[rho][r][bd]), mf);
+                for (int r = 0; r < NF; ++r) mf = fma(S.X[rho][r][ac], S.Rf[rho][r][bd], mf);
 #pragma unroll
-                    for (int r = 0; r <= N; ++r)
-                        ff_acc(ff_ld(S.X[rho][2 * r][ac]), ff_ld(S.Rc[rho][r][bd]), mc);
-                    Mf[rho][ac][bd] = ff_to(ff_fast(mf.hi, mf.lo));
-                    Mc[rho][ac][bd] = ff_to(ff_fast(mc.hi, mc.lo));
-                } else {
-                    double mf = 0.0, mc = 0.0;
-#pragma unroll
-                    for (int r = 0; r < NF; ++r) mf = fma(S.X[rho][r][ac], S.Rf[rho][r][bd], mf);
-#pragma unroll
-                    for (int r = 0; r <= N; ++r)
-                        mc = fma(S.X[rho][2 * r][ac], S.Rc[rho][r][bd], mc);
-                    Mf[rho][ac][bd] = mf;
-                    Mc[rho][ac][bd] = mc;
-                }
+                for (int r = 0; r <= N; ++r) mc = fma(S.X[rho][2 * r][ac], S.Rc[rho][r][bd], mc);
+                S.Mf[rho][ac][bd] = mf;
+                S.Mc[rho][ac][bd] = mc;
             }
         }
         __syncthreads();
@@ -1553,8 +1387,8 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
                             const double c = c_ffc[l][k1] * c_ffc[m][k2];
                             const int ac = 3 * c_ffa[l][k1] + c_ffa[m][k2];
                             const int bd = 3 * c_ffb[l][k1] + c_ffb[m][k2];
-                            q2 = fma(c, Mf[rho][ac][bd], q2);
-                            q1 = fma(c, Mc[rho][ac][bd], q1);
+                            q2 = fma(c, S.Mf[rho][ac][bd], q2);
+                            q1 = fma(c, S.Mc[rho][ac][bd], q1);
                         }
                 }
                 q2 *= scale;
@@ -1573,52 +1407,310 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
     }
 }
 
-template <int N, int PREC>
-static cudaError_t group_attr()
+// ---------------------------------------------------------------------------
+// The FP32-pipe form of the shared-partition kernel (options.eval_fp32 with
+// group_mode).  Same rule, moments and data flow as k_eval_group, with every
+// per-node, per-row and per-region quantity an unevaluated pair of FP32
+// numbers on the FP32 pipe (64x the FP64 pipe on this GPU): the node abscissae
+// (rotations of the region centre), the reduced energies, the kernel F, the
+// row sums, the moments and the pair combinations.  FP64 remains for the two
+// sincospi of the exact dyadic centre, the conversions of the per-region
+// inputs, and each pair's Q_2N and Q_N - Q_2N times the Jacobian.
+template <int N>
+struct GroupSmemF {
+    static constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
+    float2 X[R][NF][9];          // X_ac at the fine rows
+    union {
+        struct {
+            float2 Yf[R][NF][9];     // wf_j Y_bd(y_j)
+            float2 Yc[R][N + 1][9];  // wc_j Y_bd(y_2j)
+            float2 CY[R][NF][2];     // cos ky, cos ky' (flow kinds: cos(ky -+ qy/2))
+        } c;
+        struct {
+            float2 Mf[R][9][9];      // fine moments
+            float2 Mc[R][9][9];      // coarse moments
+        } m;
+    } u;
+    float2 Rf[R][NF][9];         // row sums with the row's fine weight
+    float2 Rc[R][N + 1][9];      // coarse (even rows)
+    float2 C[R][4];              // sin, cos of the region centre (x, y) times pi
+    float2 Q[R][4];              // cos qx, sin qx, cos qy, sin qy (flow: of q/2)
+    float2 H[R][2];              // 1/2T, T (Omega for the flow kinds)
+    float2 tab[64];              // 2^(j/64)
+    float2 wr[NF];               // fine weights
+    float2 wrc[N + 1];           // coarse weights
+    float2 lat[3];               // -2t, -4t', mu
+};
+
+__device__ __forceinline__ f2 ff_ld(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 ff_st(f2 a) { return make_float2(a.hi, a.lo); }
+// (c, s) rotated by the angle with cosine co and sine so
+__device__ __forceinline__ void ff_rot(f2 c, f2 s, f2 co, f2 so, f2& c2, f2& s2)
 {
-    return cudaFuncSetAttribute(k_eval_group<N, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(sizeof(GroupSmemOf<N, PREC>)));
+    c2 = ff_sub(ff_mul(c, co), ff_mul(s, so));
+    s2 = ff_add(ff_mul(s, co), ff_mul(c, so));
 }
 
-template <int PREC>
-static cudaError_t group_prec_attrs()
+// KF: the kinds the launch may meet -- 0 any, 1 no flow kind, 2 flow kinds
+// only -- so that a launch carries only the kernel F it needs (the row loop's
+// code stays within the instruction cache).
+template <int N, int KF>
+__global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1))
+k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
 {
-    cudaError_t e = group_attr<4, PREC>();
-    if (e == cudaSuccess) e = group_attr<6, PREC>();
-    if (e == cudaSuccess) e = group_attr<8, PREC>();
-    if (e == cudaSuccess) e = group_attr<10, PREC>();
-    if (e == cudaSuccess) e = group_attr<12, PREC>();
+    constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GroupSmemF<N>& S = *reinterpret_cast<GroupSmemF<N>*>(smem_raw);
+    const int v = rule_variant(N);
+    const int cur = w.ls->cur;
+    const int64_t n_eval = w.ls->n_eval;
+    const int rho = threadIdx.x / NF, i = threadIdx.x % NF;
+    if (threadIdx.x < 64) S.tab[threadIdx.x] = ff_st(ff_from(c_exp2d[threadIdx.x]));
+    if (threadIdx.x < NF) S.wr[threadIdx.x] = ff_st(ff_from(c_wf[v][threadIdx.x]));
+    if (threadIdx.x <= N) S.wrc[threadIdx.x] = ff_st(ff_from(c_wc[v][threadIdx.x]));
+    if (threadIdx.x < 3)
+        S.lat[threadIdx.x] = ff_st(ff_from(threadIdx.x == 0 ? -2.0 * lat.t
+                                           : threadIdx.x == 1 ? -4.0 * lat.tp : lat.mu));
+    for (int64_t chunk = blockIdx.x; chunk * R < n_eval; chunk += gridDim.x) {
+        const int64_t t = chunk * R + rho;
+        const bool live = t < n_eval;
+        uint32_t pos = 0, g = 0, L = 0;
+        int kind = PH, P = 0;
+        const DevBatch* B = nullptr;
+        f2 A1 = {0.0f, 0.0f}, B1 = A1, A2 = A1, B2 = A1;
+        if (live) {
+            const uint2 e = w.evl[t];
+            pos = e.x;
+            g = e.y;
+            const uint64_t key = w.key[cur][pos];
+            L = key_level(key);
+            // the per-region inputs, one thread each: the exact dyadic centre
+            // / pi = -1 + (2 ix + 1) 2^-L (x, then y), the transfer momentum,
+            // the temperature
+            if (i < 2) {
+                const uint32_t ic = i == 0 ? key_ix(key) : key_iy(key);
+                double sn, cs;
+                sincospi(fma(double(2 * ic + 1), ldexp(1.0, -int(L)), -1.0), &sn, &cs);
+                S.C[rho][2 * i] = ff_st(ff_from(sn));
+                S.C[rho][2 * i + 1] = ff_st(ff_from(cs));
+            } else if (i == 2) {
+                const QTrig tq = w.trig[g];
+                S.Q[rho][0] = ff_st(ff_from(tq.cqx));
+                S.Q[rho][1] = ff_st(ff_from(tq.sqx));
+                S.Q[rho][2] = ff_st(ff_from(tq.cqy));
+                S.Q[rho][3] = ff_st(ff_from(tq.sqy));
+            } else if (i == 3) {
+                const DevBatch& Bt = w.batches[meta_batch(w.meta[g])];
+                S.H[rho][0] = ff_st(ff_from(Bt.inv2T));
+                S.H[rho][1] = ff_st(ff_from(Bt.T));
+            }
+        }
+        __syncthreads();
+        if (live) {
+            const uint32_t mt = w.meta[g];
+            B = &w.batches[meta_batch(mt)];
+            kind = meta_kind(mt);
+            P = B->npairs;
+            const bool pp = kind == PP, flow = KF == 2 || (KF == 0 && is_flow(kind));
+            const int ii = i <= N ? i : 2 * N - i;
+            const f2 co = ff_from(c_co[v][L][ii]);
+            const f2 so0 = ff_from(c_so[v][L][ii]);
+            const f2 so = i <= N ? so0 : ff_neg(so0);
+            const f2 cqx = ff_ld(S.Q[rho][0]), sqx = ff_ld(S.Q[rho][1]);
+            const f2 cqy = ff_ld(S.Q[rho][2]), sqy = ff_ld(S.Q[rho][3]);
+            // row i (x) and column i (y) of the fine grid
+            f2 cx, sx, cy, sy;
+            ff_rot(ff_ld(S.C[rho][1]), ff_ld(S.C[rho][0]), co, so, cx, sx);
+            ff_rot(ff_ld(S.C[rho][3]), ff_ld(S.C[rho][2]), co, so, cy, sy);
+            // the shifted k' (q + k: rotate by q; q - k: rotate -k by q);
+            // flow kinds: both form factors at k
+            f2 cx2 = cx, sx2 = sx, cy2 = cy, sy2 = sy;
+            if (!flow) {
+                if (pp) {
+                    ff_rot(cx, ff_neg(sx), cqx, sqx, cx2, sx2);
+                    ff_rot(cy, ff_neg(sy), cqy, sqy, cy2, sy2);
+                } else {
+                    ff_rot(cx, sx, cqx, sqx, cx2, sx2);
+                    ff_rot(cy, sy, cqy, sqy, cy2, sy2);
+                }
+            }
+            const f2 one = {1.0f, 0.0f};
+            const f2 gx[3] = {one, cx, sx}, gx2[3] = {one, cx2, sx2};
+            const f2 gy[3] = {one, cy, sy}, gy2[3] = {one, cy2, sy2};
+            const f2 wf = ff_ld(S.wr[i]);
+            const f2 wc = (i & 1) == 0 ? ff_ld(S.wrc[i >> 1]) : f2{0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    S.X[rho][i][3 * a + c] =
+                        ff_st(a == 0 ? gx2[c] : (c == 0 ? gx[a] : ff_mul(gx[a], gx2[c])));
+                    const f2 y = a == 0 ? gy2[c] : (c == 0 ? gy[a] : ff_mul(gy[a], gy2[c]));
+                    S.u.c.Yf[rho][i][3 * a + c] = ff_st(ff_mul(wf, y));
+                    if ((i & 1) == 0) S.u.c.Yc[rho][i >> 1][3 * a + c] = ff_st(ff_mul(wc, y));
+                }
+            const f2 tA = ff_ld(S.lat[0]), tB = ff_ld(S.lat[1]), nmu = ff_neg(ff_ld(S.lat[2]));
+            if (flow) {
+                // e(k + q/2) and e(k - q/2), tq the rotation by q/2
+                f2 cxp, sxp, cxm, sxm, cyp, syp, cym, sym;
+                ff_rot(cx, sx, cqx, sqx, cxp, sxp);
+                ff_rot(cx, sx, cqx, ff_neg(sqx), cxm, sxm);
+                ff_rot(cy, sy, cqy, sqy, cyp, syp);
+                ff_rot(cy, sy, cqy, ff_neg(sqy), cym, sym);
+                S.u.c.CY[rho][i][0] = ff_st(cyp);
+                S.u.c.CY[rho][i][1] = ff_st(cym);
+                A1 = ff_fma(tA, cxp, nmu);
+                B1 = ff_fma(tB, cxp, tA);
+                A2 = ff_fma(tA, cxm, nmu);
+                B2 = ff_fma(tB, cxm, tA);
+            } else {
+                S.u.c.CY[rho][i][0] = ff_st(cy);
+                S.u.c.CY[rho][i][1] = ff_st(cy2);
+                // x = e / 2T = A + B cos ky along row i, for k and for k' (for pp
+                // the second energy enters with its sign flipped)
+                const f2 h1 = ff_ld(S.H[rho][0]), h2 = pp ? ff_neg(h1) : h1;
+                A1 = ff_mul(ff_fma(tA, cx, nmu), h1);
+                B1 = ff_mul(ff_fma(tB, cx, tA), h1);
+                A2 = ff_mul(ff_fma(tA, cx2, nmu), h2);
+                B2 = ff_mul(ff_fma(tB, cx2, tA), h2);
+            }
+        }
+        __syncthreads();
+        if (live) {
+            const f2 W = ff_ld(S.H[rho][1]);
+            f2 rf[9], rc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) { rf[k] = {0.0f, 0.0f}; rc[k] = {0.0f, 0.0f}; }
+            // one node (i, j): the kernel F once, then every row sum
+            auto node = [&](int j, bool even) {
+                const f2 x1 = ff_fma(B1, ff_ld(S.u.c.CY[rho][j][0]), A1);
+                const f2 x2 = ff_fma(B2, ff_ld(S.u.c.CY[rho][j][1]), A2);
+                f2 F = {1.0f, 0.0f};
+                if (KF != 1 && is_flow(kind))
+                    F = flow_Fdot_ff(x1, x2, W, kind == FLOW_PP);
+                else if (KF != 2 && kind != OVERLAP)
+                    F = bubble_F2T_ff(x1, x2, S.tab);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yf[rho][j][k]), rf[k]);
+                if (even) {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yc[rho][j >> 1][k]), rc[k]);
+                }
+            };
+            // two columns per trip (even, then odd) keeps the coarse-rule
+            // columns static without unrolling all 2N+1 nodes of the row: the
+            // node is ~400 instructions, and a fully unrolled row overflows
+            // the instruction cache; the last (even) column runs in the same
+            // code under a uniform branch
+#pragma unroll 1
+            for (int j = 0; j < NF; j += 2) {
+                node(j, true);
+                if (j + 1 < NF) node(j + 1, false);
+            }
+            // the row's own weight in float-float
+            const f2 wr = ff_ld(S.wr[i]);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = ff_st(ff_mul(wr, ff_fast(rf[k].hi, rf[k].lo)));
+            if ((i & 1) == 0) {
+                const f2 wrc = ff_ld(S.wrc[i >> 1]);
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    S.Rc[rho][i >> 1][k] = ff_st(ff_mul(wrc, ff_fast(rc[k].hi, rc[k].lo)));
+            }
+        }
+        __syncthreads();
+        if (live) {
+            // moments M[ac][bd]: the 81 (ac, bd) cells dealt over the region's
+            // NF threads, float-float dot products over the rows
+            for (int u = i; u < 81; u += NF) {
+                const int ac = u / 9, bd = u - 9 * (u / 9);
+                f2 mf = {0.0f, 0.0f}, mc = {0.0f, 0.0f};
+#pragma unroll 5
+                for (int r = 0; r < NF; ++r)
+                    ff_acc(ff_ld(S.X[rho][r][ac]), ff_ld(S.Rf[rho][r][bd]), mf);
+#pragma unroll
+                for (int r = 0; r <= N; ++r)
+                    ff_acc(ff_ld(S.X[rho][2 * r][ac]), ff_ld(S.Rc[rho][r][bd]), mc);
+                S.u.m.Mf[rho][ac][bd] = ff_st(ff_fast(mf.hi, mf.lo));
+                S.u.m.Mc[rho][ac][bd] = ff_st(ff_fast(mc.hi, mc.lo));
+            }
+        }
+        __syncthreads();
+        if (live) {
+            const double scale =
+                ldexp(0.25, -2 * int(L)) * (kind == PH || kind == PP ? B->inv2T : 1.0);
+            for (int p = i; p < P; p += NF) {
+                const int l = B->lm[2 * p], m = B->lm[2 * p + 1];
+                f2 q2 = {0.0f, 0.0f}, q1 = {0.0f, 0.0f};
+                if (l >= 0 && m >= 0 && l < w.nff && m < w.nff) {
+                    for (int k1 = 0; k1 < c_ffn[l]; ++k1)
+                        for (int k2 = 0; k2 < c_ffn[m]; ++k2) {
+                            const f2 c = ff_ld(c_ffpair[l][k1][m][k2]);
+                            const int ac = 3 * c_ffa[l][k1] + c_ffa[m][k2];
+                            const int bd = 3 * c_ffb[l][k1] + c_ffb[m][k2];
+                            ff_acc(c, ff_ld(S.u.m.Mf[rho][ac][bd]), q2);
+                            ff_acc(c, ff_ld(S.u.m.Mc[rho][ac][bd]), q1);
+                        }
+                }
+                q2 = ff_fast(q2.hi, q2.lo);
+                q1 = ff_fast(q1.hi, q1.lo);
+                // FP64 from here: Q_2N and the embedded-rule difference
+                const double v2 = ff_to(q2) * scale;
+                const double dq = ff_to(ff_sub(q1, q2)) * scale;
+                if (rule_q2) {
+                    rule_q2[t * P + p] = v2;
+                    rule_d[t * P + p] = dq;
+                } else {
+                    const size_t o = size_t(pos) * size_t(w.vstride) + size_t(p);
+                    w.vval[cur][o] = v2;
+                    w.verr[cur][o] = float(fabs(dq));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int N>
+static cudaError_t group_attr()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_eval_group<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(GroupSmem<N>)));
+    for (int kf = 0; kf < 3 && e == cudaSuccess; ++kf)
+        e = cudaFuncSetAttribute(kf == 0 ? k_eval_group_ff<N, 0>
+                                 : kf == 1 ? k_eval_group_ff<N, 1> : k_eval_group_ff<N, 2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(sizeof(GroupSmemF<N>)));
     return e;
 }
 
 static cudaError_t group_kernel_attributes()
 {
-    cudaError_t e = group_prec_attrs<0>();
-    if (e == cudaSuccess) e = group_prec_attrs<1>();
+    cudaError_t e = group_attr<4>();
+    if (e == cudaSuccess) e = group_attr<6>();
+    if (e == cudaSuccess) e = group_attr<8>();
+    if (e == cudaSuccess) e = group_attr<10>();
+    if (e == cudaSuccess) e = group_attr<12>();
     return e;
 }
 
-template <int N, int PREC>
-static void group_launch(const Work& w, int64_t hint_eval, int64_t cap, Lattice lat, cudaStream_t s,
-                         double* rule_q2, double* rule_d)
+template <int N>
+static void group_launch(const Work& w, int64_t hint_eval, int64_t cap, int fp32, Lattice lat,
+                         cudaStream_t s, double* rule_q2, double* rule_d)
 {
     constexpr int R = GroupShape<N>::R;
     const int64_t blocks = std::min<int64_t>((hint_eval + R - 1) / R, cap);
-    k_eval_group<N, PREC><<<int(blocks), R * (2 * N + 1), sizeof(GroupSmemOf<N, PREC>), s>>>(
-        w, lat, rule_q2, rule_d);
-}
-
-template <int PREC>
-static void group_dispatch(const Work& w, int64_t hint_eval, int rule_n, int64_t cap, Lattice lat,
-                           cudaStream_t s, double* rule_q2, double* rule_d)
-{
-    switch (rule_n) {
-    case 4: group_launch<4, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    case 6: group_launch<6, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    case 8: group_launch<8, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    case 10: group_launch<10, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    default: group_launch<12, PREC>(w, hint_eval, cap, lat, s, rule_q2, rule_d); break;
-    }
+    const dim3 grid(static_cast<unsigned>(blocks)), block(R * (2 * N + 1));
+    const size_t sm = sizeof(GroupSmemF<N>);
+    if (fp32 && w.kinds == 1)
+        k_eval_group_ff<N, 1><<<grid, block, sm, s>>>(w, lat, rule_q2, rule_d);
+    else if (fp32 && w.kinds == 2)
+        k_eval_group_ff<N, 2><<<grid, block, sm, s>>>(w, lat, rule_q2, rule_d);
+    else if (fp32)
+        k_eval_group_ff<N, 0><<<grid, block, sm, s>>>(w, lat, rule_q2, rule_d);
+    else
+        k_eval_group<N><<<int(blocks), R * (2 * N + 1), sizeof(GroupSmem<N>), s>>>(
+            w, lat, rule_q2, rule_d);
 }
 
 cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, int fp32, Lattice lat,
@@ -1626,8 +1718,13 @@ cudaError_t launch_eval_group(const Work& w, int64_t hint_eval, int rule_n, int 
 {
     if (hint_eval <= 0) return cudaSuccess;
     const int64_t cap = max_blocks > 0 ? max_blocks : 152 * 32;
-    if (fp32) group_dispatch<1>(w, hint_eval, rule_n, cap, lat, s, rule_q2, rule_d);
-    else      group_dispatch<0>(w, hint_eval, rule_n, cap, lat, s, rule_q2, rule_d);
+    switch (rule_n) {
+    case 4: group_launch<4>(w, hint_eval, cap, fp32, lat, s, rule_q2, rule_d); break;
+    case 6: group_launch<6>(w, hint_eval, cap, fp32, lat, s, rule_q2, rule_d); break;
+    case 8: group_launch<8>(w, hint_eval, cap, fp32, lat, s, rule_q2, rule_d); break;
+    case 10: group_launch<10>(w, hint_eval, cap, fp32, lat, s, rule_q2, rule_d); break;
+    default: group_launch<12>(w, hint_eval, cap, fp32, lat, s, rule_q2, rule_d); break;
+    }
     return cudaGetLastError();
 }
 

@@ -55,6 +55,9 @@ constexpr int kGroupSplit = 8;
 enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3, FLOW_PH = 4, FLOW_PP = 5 };
 __host__ __device__ inline bool is_flow(int kind) { return kind == FLOW_PH || kind == FLOW_PP; }
 enum Status : int { CONVERGED = 0, BUDGET = 1, NONFINITE = 2, ROUNDCAP = 3, POOL = 4, RUNNING = -1 };
+// force_status of the test kernels: finalize with POOL only if the device
+// loop stopped on a pool that could make no progress
+constexpr int kFinalizeIfStuck = -2;
 
 __host__ __device__ inline uint64_t make_key(uint32_t L, uint32_t ix, uint32_t iy)
 {
@@ -96,6 +99,12 @@ struct DevBatch {
     double* errors;
     int64_t* regions;
     int32_t* status;
+    // flow kinds in group mode: couplings and outputs of the truncated-unity
+    // products (pp: V^P -> dP; ph: V^C, V^D -> dC, dD), or null
+    const double* tu_v0;
+    const double* tu_v1;
+    double* tu_out0;
+    double* tu_out1;
 };
 
 // cos/sin of the transfer momentum of one integral
@@ -194,6 +203,7 @@ struct Work {
     int* gstate;
     int vstride;
     int nff;
+    int kinds;                 // the call's kinds: 1 no flow kind, 2 flow kinds only, 0 mixed
     int gglobal;               // group mode 2: one error sum and one tolerance per group
 };
 
@@ -269,6 +279,10 @@ cudaError_t launch_split(const Work& w, int64_t hint_active, cudaStream_t s);
 cudaError_t launch_copy_vectors(const Work& w, int64_t hint_pool, cudaStream_t s);
 // finish every slot still refining with `status` (after a stop)
 cudaError_t launch_finalize(const Work& w, int64_t hint_active, int status, cudaStream_t s);
+// after the device loop, decided on the device from its stop reason: a pool
+// that could make no progress finishes the slots still refining with PAID_POOL;
+// integrals never admitted get PAID_POOL or PAID_ROUNDCAP
+cudaError_t launch_finish_device(const Work& w, cudaStream_t s);
 cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int status, cudaStream_t s);
 // after launch_scan, when its pool total exceeds the capacity: integrals past
 // cap - pool regions of cumulative growth keep their regions unsplit this round

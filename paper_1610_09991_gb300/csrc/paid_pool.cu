@@ -585,6 +585,10 @@ constexpr int kWarpsPerBlock = 8;
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_reduce_test(Work w, int max_rounds, double cover, int force_status)
 {
+    if (force_status == kFinalizeIfStuck) {   // after the device loop: decided on the device
+        if (w.ls->stop != kStuck) return;
+        force_status = POOL;
+    }
     const int cur = w.ls->cur;
     const int64_t n_active = w.ls->n_active;
     const int round = w.ls->round;
@@ -779,10 +783,60 @@ __device__ void group_outputs(const Work& w, const DevBatch& B, uint32_t g, uint
     B.status[o] = !valid || !finite ? NONFINITE : (conv ? CONVERGED : st);
 }
 
+// Truncated-unity products of a finished flow group (Eqs. matmul-P/C/D):
+// with X its bubble matrix (the group's values, pair l * nff + m at X[l][m]),
+//   pp: dP = V^P X V^P;   ph: dC = -V^C X V^C, dD = 2 V^D X V^D - V^C X V^D - V^D X V^C,
+// for the group's transfer momentum.  X: the values in shared memory; called by
+// every thread of the block (at least nff^2 of them).  Pairs not in l-major
+// order give NaN products.
+__device__ void group_tu(const Work& w, const DevBatch& B, int64_t iq, const double* X)
+{
+    __shared__ double A[kGroupPairs], C[kGroupPairs];
+    const int n = w.nff, nn = n * n, tid = threadIdx.x;
+    const bool ordered = __syncthreads_and(
+        tid >= nn || (B.lm[2 * tid] == tid / n && B.lm[2 * tid + 1] == tid % n));
+    const size_t o = size_t(iq) * nn;
+    const double* V0 = B.tu_v0 + o;
+    const double* V1 = B.tu_v1 ? B.tu_v1 + o : nullptr;
+    if (tid < nn) {
+        // A = X V0, C = X V1: the right factors of every product
+        const int a = tid / n, b = tid % n;
+        double sa = 0.0, sc = 0.0;
+        for (int k = 0; k < n; ++k) {
+            sa = fma(X[a * n + k], V0[k * n + b], sa);
+            if (V1) sc = fma(X[a * n + k], V1[k * n + b], sc);
+        }
+        A[tid] = sa;
+        C[tid] = sc;
+    }
+    __syncthreads();
+    if (tid < nn) {
+        const int a = tid / n, b = tid % n;
+        double p = 0.0, d = 0.0;
+        if (!V1) {                          // pp: V^P (X V^P)
+            for (int k = 0; k < n; ++k) p = fma(V0[a * n + k], A[k * n + b], p);
+            B.tu_out0[o + tid] = ordered ? p : NAN;
+        } else {                            // ph: V0 = V^C, V1 = V^D
+            for (int k = 0; k < n; ++k) {
+                p = fma(V0[a * n + k], A[k * n + b], p);           // V^C X V^C
+                d = fma(2.0 * V1[a * n + k], C[k * n + b], d);     // 2 V^D X V^D
+                d = fma(-V0[a * n + k], C[k * n + b], d);          // - V^C X V^D
+                d = fma(-V1[a * n + k], A[k * n + b], d);          // - V^D X V^C
+            }
+            B.tu_out0[o + tid] = ordered ? -p : NAN;
+            B.tu_out1[o + tid] = ordered ? d : NAN;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128)
 k_group_test(Work w, int max_rounds, int force_status)
 {
     const LoopState& Ls = *w.ls;
+    if (force_status == kFinalizeIfStuck) {   // after the device loop: decided on the device
+        if (Ls.stop != kStuck) return;
+        force_status = POOL;
+    }
     const int64_t s = blockIdx.x;
     if (s >= Ls.n_active) return;
     const int cur = Ls.cur, round = Ls.round;
@@ -846,6 +900,12 @@ k_group_test(Work w, int max_rounds, int force_status)
         if (st == ROUNDCAP && force_status < 0) atomicAdd(&w.totals->roundcap, 1ull);
         w.cnt_new[s] = 0;
         w.cnt_eval[s] = 0;
+    }
+    if (B.tu_out0) {   // the flow step's products, as the group finishes
+        __shared__ double X[kGroupPairs];
+        if (tid < P) X[tid] = V;
+        __syncthreads();
+        group_tu(w, B, int64_t(g) - B.first, X);
     }
 }
 
@@ -932,6 +992,12 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_select(Work w, doubl
                           w.gsum[size_t(s) * 2 * kGroupPairs + kGroupPairs + tid], BUDGET,
                           w.gglobal ? 0 : -1);
         if (tid == 0) { w.cnt_new[s] = 0; w.cnt_eval[s] = 0; }
+        if (B.tu_out0) {
+            __shared__ double X[kGroupPairs];
+            if (tid < B.npairs) X[tid] = w.gsum[size_t(s) * 2 * kGroupPairs + tid];
+            __syncthreads();
+            group_tu(w, B, int64_t(g) - B.first, X);
+        }
         return;
     }
     for (int b = tid; b < kHistBins; b += blockDim.x) { hsum[b] = 0ull; hcnt[b] = 0u; }
@@ -1023,7 +1089,52 @@ __global__ void k_mark_unadmitted(Work w, int64_t g0, int64_t g1, int status)
         B.errors[o] = NAN;
         B.regions[o] = 0;
         B.status[o] = status;
+        if (B.tu_out0) B.tu_out0[o] = NAN;
+        if (B.tu_out1) B.tu_out1[o] = NAN;
     }
+}
+
+// After the device loop: the integrals it never admitted, with the status its
+// stop reason gives (pool: PAID_POOL, hard round bound: PAID_ROUNDCAP).
+__global__ void k_mark_unadmitted_dev(Work w)
+{
+    const LoopState& L = *w.ls;
+    if (L.stop != kStuck && L.stop != kNoRoom && L.stop != kHardCap) return;
+    const int64_t g = L.admitted + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= w.n) return;
+    const int status = L.stop == kHardCap ? ROUNDCAP : POOL;
+    int lo = 0, hi = w.nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.batches[mid].first <= g) lo = mid; else hi = mid - 1;
+    }
+    const DevBatch& B = w.batches[lo];
+    const int64_t local = g - B.first;
+    const int width = w.vstride > 0 ? B.npairs : 1;
+    for (int p = 0; p < width; ++p) {
+        const int64_t o = local * width + p;
+        B.values[o] = NAN;
+        B.errors[o] = NAN;
+        B.regions[o] = 0;
+        B.status[o] = status;
+        if (B.tu_out0) B.tu_out0[o] = NAN;
+        if (B.tu_out1) B.tu_out1[o] = NAN;
+    }
+}
+
+cudaError_t launch_finish_device(const Work& w, cudaStream_t s)
+{
+    if (w.n <= 0) return cudaSuccess;
+    const int64_t n = w.n;
+    if (w.vstride > 0) {
+        k_group_sums<<<int(n) * kGroupSplit, kGroupWarps * 32, 0, s>>>(w);
+        k_group_test<<<int(n), 128, 0, s>>>(w, 0, kFinalizeIfStuck);
+    } else {
+        const int64_t blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        k_reduce_test<<<int(blocks), kWarpsPerBlock * 32, 0, s>>>(w, 0, 0.0, kFinalizeIfStuck);
+    }
+    k_mark_unadmitted_dev<<<int((n + 255) / 256), 256, 0, s>>>(w);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mark_unadmitted(const Work& w, int64_t g0, int64_t g1, int status, cudaStream_t s)

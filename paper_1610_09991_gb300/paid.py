@@ -34,7 +34,8 @@ EXPORTS = ("paid_options_default", "paid_create", "paid_destroy", "paid_workspac
            "paid_mlp_grad", "paid_mlp_adamw", "paid_rule_regions", "paid_check_math",
            "paid_get_options", "paid_autotune", "paid_tu_flow_rhs", "paid_integrate_batch_static",
            "paid_set_trace_buffer", "paid_mlp_group_features", "paid_proposal_train",
-           "paid_proposal_train_workspace_size", "paid_proposal_save", "paid_proposal_load")
+           "paid_proposal_train_workspace_size", "paid_proposal_save", "paid_proposal_load",
+           "paid_wait")
 
 
 class paid_options(ctypes.Structure):
@@ -64,7 +65,8 @@ class paid_batch(ctypes.Structure):
                 ("rel_tol", ctypes.c_double), ("abs_tol", ctypes.c_double),
                 ("max_regions", ctypes.c_int64), ("values", ctypes.c_void_p),
                 ("errors", ctypes.c_void_p), ("regions", ctypes.c_void_p),
-                ("status", ctypes.c_void_p)]
+                ("status", ctypes.c_void_p), ("tu_v", ctypes.c_void_p * 2),
+                ("tu_out", ctypes.c_void_p * 2)]
 
 
 _lock = threading.Lock()
@@ -120,6 +122,7 @@ def load(path: str = LIB_PATH):
         lib.paid_mlp_grad.argtypes = [P, P, P, I64, P, P, P, ctypes.c_size_t, P]
         lib.paid_mlp_adamw.argtypes = [P, P, P, P, I, ctypes.c_float, ctypes.c_float, P]
         lib.paid_set_trace_buffer.argtypes = [P, P, I64]
+        lib.paid_wait.argtypes = [P, ctypes.POINTER(I)]
         lib.paid_mlp_group_features.argtypes = [P, I, I, P, D, P, P]
         lib.paid_proposal_train_workspace_size.argtypes = [I64, I64, ctypes.POINTER(ctypes.c_size_t)]
         lib.paid_proposal_train.argtypes = [P, P, P, P, P, I64, I, I64, ctypes.c_float,
@@ -226,28 +229,54 @@ class Context:
         torch = _torch()
         need = self.workspace_size(n_integrals, pool_capacity)
         if self._ws is None or self._ws.numel() < need:
+            # hand cached blocks back first: one large block is needed, and the
+            # cache may hold the memory in pieces
             self._ws = None
+            torch.cuda.empty_cache()
             self._ws = torch.empty(need, dtype=torch.uint8, device=self.torch_device)
         return self._ws
 
-    def default_capacity(self, n_integrals: int, max_regions: int) -> int:
-        """Pool capacity used when none is given: every integral at its budget,
-        bounded by 70 % of the device's free memory."""
+    #: regions per unit the default pool is sized for: an integral's regions
+    #: take 64 bytes, a (kind, q) group's ~2 KB (every pair's values); the pool
+    #: streams units in when it holds fewer, and a call that cannot progress
+    #: grows it
+    DEFAULT_REGIONS_PER_UNIT = 8192
+    DEFAULT_GROUP_REGIONS_PER_UNIT = 2048
+
+    def default_capacity(self, n_units: int, max_regions: int) -> int:
+        """Pool capacity used when none is given: every unit at min(its budget,
+        8192 regions per integral or 2048 per (kind, q) group), or the capacity
+        an earlier call had to grow to, bounded by 70 % of the device's free
+        memory."""
         torch = _torch()
         free, _ = torch.cuda.mem_get_info(self.device)
         # memory torch holds in its cache is available to this allocation too
         cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
         n0 = 4 ** self.options.init_level
-        want = max(n_integrals * n0, n_integrals * max_regions)
+        per = (self.DEFAULT_GROUP_REGIONS_PER_UNIT if self.options.group_mode
+               else self.DEFAULT_REGIONS_PER_UNIT)
+        want = max(n_units * n0, n_units * min(max_regions, per),
+                   getattr(self, "_grown_capacity", 0))
         held = self._ws.numel() if self._ws is not None else 0
-        limit = self.pool_capacity(n_integrals, int(0.7 * (free + cached + held)))
-        return int(max(n_integrals * n0, min(want, limit, 2 ** 32 - 1)))
+        limit = self.pool_capacity(n_units, int(0.7 * (free + cached + held)))
+        return int(max(n_units * n0, min(want, limit, 2 ** 32 - 1)))
 
-    def integrate_multi(self, batches, pool_capacity=None, stream=None):
+    def integrate_multi(self, batches, pool_capacity=None, stream=None, asynchronous=False):
         """Device-resident batches: a list of dicts with keys kind, T, q (cuda
         float64 [nq, 2]), lm (cuda int32 [npairs, 2]), rel_tol, abs_tol,
-        max_regions.  Returns one Result of cuda tensors per batch."""
-        return self._integrate(batches, pool_capacity, stream, None)
+        max_regions.  Returns one Result of cuda tensors per batch.  With
+        asynchronous=True (device loop only) the call returns once the work is
+        queued: wait() gives its outcome, and a full pool is not retried."""
+        return self._integrate(batches, pool_capacity, stream, None, asynchronous)
+
+    def wait(self) -> int:
+        """paid_wait: the outcome code of the last integrate call."""
+        out = ctypes.c_int(OK)
+        rc = self._lib.paid_wait(self._h, ctypes.byref(out))
+        if rc != OK:
+            raise PaidError(rc, self.last_error())
+        self.last_rc = out.value
+        return out.value
 
     def integrate_multi_seeded(self, batches, proposal=None, margin=1.0, pool_capacity=None,
                                stream=None):
@@ -389,7 +418,8 @@ class Context:
         if stream is None:
             stream = torch.cuda.current_stream(self.torch_device)
         path = cache_path.encode() if cache_path else None
-        arr, outs, n, maxr = self._batch_array(batches or [])
+        arr, outs, n_int, maxr = self._batch_array(batches or [])
+        n = self.units(batches or [])
         nbytes = 0
         ws = None
         if n:
@@ -430,13 +460,28 @@ class Context:
             a.max_regions = int(b.get("max_regions", 100000))
             a.values, a.errors = r.values.data_ptr(), r.errors.data_ptr()
             a.regions, a.status = r.regions.data_ptr(), r.status.data_ptr()
+            # flow kinds, group mode: truncated-unity products formed in the
+            # call (tu_v: couplings, tu_out: outputs; cuda float64 [nq, nff, nff])
+            for f in ("tu_v", "tu_out"):
+                ts = b.get(f) or ()
+                for j, t_ in enumerate(ts):
+                    if t_ is None:
+                        continue
+                    if (t_.device != dev or t_.dtype != torch.float64 or not t_.is_contiguous()
+                            or t_.numel() != nq * npairs):
+                        raise ValueError("%s tensors must be contiguous float64 [nq, nff, nff] "
+                                         "on %s" % (f, dev))
+                    getattr(a, f)[j] = t_.data_ptr()
             n += nq * npairs
             maxr = max(maxr, a.max_regions)
         return arr, outs, n, maxr
 
-    def _integrate(self, batches, pool_capacity, stream, seeded):
+    def _integrate(self, batches, pool_capacity, stream, seeded, asynchronous=False):
         torch = _torch()
-        arr, outs, n, maxr = self._batch_array(batches)
+        arr, outs, n_int, maxr = self._batch_array(batches)
+        # workspace and pool are sized per unit: a (kind, q) group in group
+        # mode, else an integral
+        n = self.units(batches)
         if stream is None:
             stream = torch.cuda.current_stream(self.torch_device)
         cap = pool_capacity or self.default_capacity(n, maxr)
@@ -451,17 +496,25 @@ class Context:
                                                     ctypes.c_void_p(stream.cuda_stream))
             else:
                 prop, margin = seeded
-                units = self.units(batches)
                 if prop is not None and (prop.dtype != torch.float32
-                                         or tuple(prop.shape) != (units, 256)
+                                         or tuple(prop.shape) != (n, 256)
                                          or not prop.is_contiguous()
                                          or prop.device != self.torch_device):
-                    raise ValueError("proposal must be contiguous float32 [%d, 256]" % units)
+                    raise ValueError("proposal must be contiguous float32 [%d, 256]" % n)
                 rc = self._lib.paid_integrate_multi_seeded(
                     self._h, arr, len(batches), prop.data_ptr() if prop is not None else None,
                     margin, ctypes.c_void_p(ws.data_ptr()), nbytes,
                     ctypes.c_void_p(stream.cuda_stream))
-            if rc == ERR_POOL and pool_capacity is None and cap < 2 ** 32 - 1:
+            if rc == OK and not asynchronous:
+                # the device-loop calls return at once: their outcome (pool,
+                # round cap) comes from paid_wait
+                out = ctypes.c_int(OK)
+                rc = self._lib.paid_wait(self._h, ctypes.byref(out))
+                rc = out.value if rc == OK else rc
+            # a pool that could not progress, or (seeded start) one too small
+            # for the seed: grow it and run again
+            grow = rc == ERR_POOL or (rc == ERR_OOM and seeded is not None)
+            if grow and pool_capacity is None and cap < 2 ** 32 - 1:
                 # drop every reference to the old workspace before sizing the next
                 del ws
                 self.release_workspace()
@@ -469,6 +522,7 @@ class Context:
                 bigger = min(4 * cap, self.pool_capacity(n, int(0.9 * free)), 2 ** 32 - 1)
                 if bigger > cap:
                     cap = bigger
+                    self._grown_capacity = cap
                     continue
                 ws = None
             if rc not in (OK, ERR_TIMEOUT, ERR_POOL):

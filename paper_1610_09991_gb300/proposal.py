@@ -69,7 +69,7 @@ def predict(prop, ctx, batches):
     return prop.predict(ctx, batches)
 
 
-def calibrate_margin(prop, ctx, batches, margins=(0.0, 0.5, 1.0, 1.5, 2.0)):
+def calibrate_margin(prop, ctx, batches, margins=(0.0, 0.5, 1.0)):
     """Region evaluations of the seeded run at each margin on these batches:
     returns {margin: (region evaluations, rounds)}."""
     maps = predict(prop, ctx, batches)
@@ -81,7 +81,7 @@ def calibrate_margin(prop, ctx, batches, margins=(0.0, 0.5, 1.0, 1.5, 2.0)):
     return out
 
 
-def train_default(device=0, n_draws=48, nq=12, epochs=150, seed=0, log=None, **options):
+def train_default(device=0, n_draws=128, nq=12, epochs=300, seed=0, log=None, **options):
     """The proposal trained on n_draws seeded parameter draws (seeds 0..n-1)
     for the given integrate options (default: the shared-partition path):
     returns (Proposal, training-loss history, seconds)."""

@@ -126,3 +126,31 @@ def test_graph_is_reused_across_calls(paid, torch):
     for (va, sa), r in zip(a, b):
         assert torch.equal(va, r.values) and torch.equal(sa, r.status)
     assert ctx.last_stats()["graph_launches"] == 1
+
+
+def test_device_loop_call_is_asynchronous(paid, torch):
+    # the call returns once its work is queued on the stream (the stream is
+    # still busy when it returns); paid_wait gives the outcome, and the outputs
+    # equal those of the synchronous form bit for bit
+    w = W.config_flow_step(T=0.05, nq=12)
+    dbs = _dbs(torch, w.batches)
+    ctx = paid.Context(*LAT, ffset=9, group_mode=1, rule_n=12, cover=1.0, eval_fp32=1)
+    sync = ctx.integrate_multi(dbs)
+    ref = [r.values.clone() for r in sync]
+    torch.cuda.synchronize()
+    outs = ctx.integrate_multi(dbs, asynchronous=True)
+    busy = not torch.cuda.current_stream().query()
+    assert ctx.wait() == paid.OK
+    torch.cuda.synchronize()
+    assert busy
+    for a, r in zip(ref, outs):
+        assert torch.equal(a, r.values)
+    st = ctx.last_stats()
+    assert st["graph_launches"] == 1 and st["rounds"] > 2
+    # a pool that cannot progress: the call itself returns OK, paid_wait
+    # reports the full pool, and the unfinished integrals say so
+    b = W.Batch(W.PH, 0.05, W.q_grid_bz(2), W.all_pairs(5), 1e-8, 1e-12, 100000)
+    c2 = paid.Context(*LAT, ffset=9)
+    (r,) = c2.integrate_multi(_dbs(torch, [b]), pool_capacity=b.n * 16 + 64, asynchronous=True)
+    assert c2.wait() == paid.ERR_POOL
+    assert (r.status == 4).any()

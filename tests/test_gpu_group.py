@@ -160,7 +160,11 @@ def test_group_streaming_small_pool(paid, torch):
     ctx = paid.Context(*LAT, ffset=9, group_mode=1)
     (full,) = _run(paid, torch, ctx, [b])
     peak = ctx.last_stats()["peak_pool"]
-    cap = max(peak // 3, 2000)
+    # room for half the batch's peak and at least four of its largest groups:
+    # admitted groups grow ~30x from their 16-region start, and the first
+    # group's round must fit beside the others for the pool to progress
+    cap = max(peak // 2, 4 * int(full[2].max()))
+    assert cap < peak
     (g,) = _run(paid, torch, ctx, [b], pool_capacity=cap)
     st = ctx.last_stats()
     assert ctx.last_rc == paid.OK and st["peak_pool"] <= cap < peak

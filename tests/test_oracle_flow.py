@@ -120,3 +120,44 @@ def test_flow_routing_symmetries():
         assert np.all(np.abs(I[0] - I[0].T) <= E[0] + E[0].T + 1e-13)
         if kind == oracle.FLOW_PH:
             assert np.all(np.abs(I[0] - I[1]) <= E[0] + E[1] + 1e-13)
+
+
+def _bubble_quad(e1, e2, om):
+    """int dk0/2pi theta(k0)^2 / ((i k0 - e1)(i k0 - e2)): the ph bubble's
+    frequency integral itself (no derivative)."""
+    def f(k0):
+        th = k0 * k0 / (k0 * k0 + om * om)
+        return (th * th / ((1j * k0 - e1) * (1j * k0 - e2))).real
+    pts = sorted({om} | {abs(x) for x in (e1, e2) if abs(x) > 1e-9})
+    a, total = 0.0, 0.0
+    for b in pts + [math.inf]:
+        if b > a:
+            v, _ = integrate.quad(f, a, b, limit=400, epsabs=0.0, epsrel=1e-13)
+            total += v
+            a = b
+    return 2.0 * total / (2.0 * math.pi)
+
+
+@pytest.mark.parametrize("e1,e2,om", [(0.7, -0.3, 0.5), (-1.3, -1.29, 0.2), (0.0, 0.8, 0.3),
+                                      (2.5, -3.1, 1.0)])
+def test_flow_kernel_is_the_omega_derivative_of_the_bubble(e1, e2, om):
+    # the TU flow equations (Eqs. matmul-P/C/D) take the derivative of the
+    # bubble of Eqs. chi_pp / chi_ph; the text after the T-equations says the
+    # frequency integrals are the Omega derivative of a product of two
+    # propagators.  A central difference of the undifferentiated bubble pins
+    # that reading (the regulators of both propagators vary), independently
+    # of differentiating under the integral
+    h = 1e-4 * om
+    fd = (_bubble_quad(e1, e2, om + h) - _bubble_quad(e1, e2, om - h)) / (2 * h)
+    got = oracle.kernel_flow_ph(e1, e2, om)
+    assert abs(got - fd) <= 1e-6 * max(abs(fd), 1e-3 / om ** 2)
+    # the single-scale reading (only one propagator's regulator varies) is
+    # half of it for the ph bubble's symmetric frequency integrand
+    def half(k0):
+        if k0 == 0.0:
+            return 0.0
+        th = k0 * k0 / (k0 * k0 + om * om)
+        dth = -2.0 * om * k0 * k0 / (k0 * k0 + om * om) ** 2
+        return (dth * th / ((1j * k0 - e1) * (1j * k0 - e2))).real
+    v, _ = integrate.quad(half, 0, math.inf, limit=400, epsabs=0.0, epsrel=1e-12)
+    assert abs(2 * v / (2 * math.pi) - 0.5 * got) <= 1e-6 * max(abs(got), 1e-3 / om ** 2)
