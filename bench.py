@@ -453,33 +453,36 @@ def run_paid(args):
         sample = [dict(d, q=d["q"][::6].contiguous()) for d in dbs]
         o = ctx.autotune(sample)
         tune = {"rule_n": o.rule_n, "cover": o.cover, "eval_blocks": o.eval_blocks,
+                "init_level": o.init_level,
                 "seconds": time.perf_counter() - t0,
                 "sample": "every 6th q point of each batch (%d integrals)"
                           % sum(int(d["q"].shape[0]) * int(d["lm"].shape[0]) for d in sample)}
         ctx.release_workspace()
     tuned = dict(rule_n=ctx.options.rule_n, cover=ctx.options.cover,
-                 eval_blocks=ctx.options.eval_blocks)
+                 eval_blocks=ctx.options.eval_blocks, init_level=ctx.options.init_level)
     prop_info, prop, margin = None, None, None
     if learned:
         from paper_1610_09991_gb300 import proposal as PR
         popts = dict(opts, rule_n=tuned["rule_n"], cover=tuned["cover"]) if group else dict(opts)
         prop, hist, t_train = PR.train_default(device=local, **popts)
         t0 = time.perf_counter()
-        margin, calib = PR.calibrate_default(prop, device=local, **popts)
+        margin, calib = PR.calibrate_default(prop, device=local, **popts)   # a MarginPolicy
         prop_info = {"train_seconds": t_train, "calibrate_seconds": time.perf_counter() - t0,
                      "targets": "traced level maps of unseeded runs (options.trace): per unit "
                                 "the level of the coarsest final region in each level-4 cell",
-                     "draws": "seeds 0..127 of t' ~ U[-0.35,0], mu ~ U[-1.4,0], T log-U[0.005,1], "
-                              "12x12 q grid, ph+pp; 300 epochs",
-                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "margin": margin,
-                     "calibration_region_evals_rounds": {str(k): v for k, v in calib.items()}}
+                     "draws": "seeds 0..191 of t' ~ U[-0.35,0], mu ~ U[-1.4,0], T log-U[0.005,1], "
+                              "12x12 q grid, ph+pp; 300 epochs; margin policy calibrated per "
+                              "temperature band on seeds 0..95 (8x8 q grid)",
+                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                     "margin_policy": margin.as_dict(),
+                     "calibration_region_evals_rounds": calib}
 
     def make_step(c, seeded):
         def step():
             flush.fill_(1)
             if not seeded:
                 return c.integrate_multi(dbs, stream=stream)
-            return c.integrate_multi_seeded(dbs, prop.predict(c, dbs, stream), margin,
+            return c.integrate_multi_seeded(dbs, PR.seed_maps(prop, c, dbs, margin), 0.0,
                                             stream=stream)
         return step
 
@@ -541,14 +544,14 @@ def run_paid(args):
     if not args.no_e2e:
         hb = [dict(kind=b.kind, T=b.T, q=b.q, lm=b.lm, rel_tol=b.rel_tol, abs_tol=b.abs_tol,
                    max_regions=b.max_regions) for b in w.batches]
-        ctx.integrate_host(hb, proposal=prop, margin=margin or 0.0)   # warm-up (pinned pools)
+        ctx.integrate_host(hb, proposal=prop, margin=margin)   # warm-up (pinned pools)
         torch.cuda.synchronize()
         n_e2e = max(5, min(args.steps, 10))
         t0 = time.perf_counter()
         conv_e2e, h2d, d2h = 0, 0, 0
         for _ in range(n_e2e):
             flush.fill_(1)
-            res, h2d, d2h = ctx.integrate_host(hb, proposal=prop, margin=margin or 0.0)
+            res, h2d, d2h = ctx.integrate_host(hb, proposal=prop, margin=margin)
             conv_e2e += sum(int((r.status == 0).sum()) for r in res)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0

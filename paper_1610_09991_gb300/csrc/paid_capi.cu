@@ -996,7 +996,7 @@ std::vector<std::string> read_lines(const char* path)
 }
 
 bool cached_choice(const char* path, const std::string& key, int& rule_n, double& cover,
-                   int& blocks)
+                   int& blocks, int& init_level)
 {
     const std::string tag = "\"key\": \"" + key + "\"";
     for (const std::string& l : read_lines(path)) {
@@ -1012,16 +1012,23 @@ bool cached_choice(const char* path, const std::string& key, int& rule_n, double
             std::sscanf(l.c_str() + pb + 15, "%d", &b) != 1)
             continue;
         if (r < 4 || r > 12 || r % 2 != 0 || !(c >= 0.0 && c <= 1.0) || b < 0) continue;
+        // the start level is optional (older entries have none)
+        const size_t pl = l.find("\"init_level\": ");
+        int lv = init_level;
+        if (pl != std::string::npos && (std::sscanf(l.c_str() + pl + 14, "%d", &lv) != 1 ||
+                                        lv < 0 || lv > 8))
+            continue;
         rule_n = r;
         cover = c;
         blocks = b;
+        init_level = lv;
         return true;
     }
     return false;
 }
 
 void store_choice(const char* path, const std::string& key, int rule_n, double cover, int blocks,
-                  double ms)
+                  int init_level, double ms)
 {
     const std::string tag = "\"key\": \"" + key + "\"";
     std::vector<std::string> keep;
@@ -1029,8 +1036,9 @@ void store_choice(const char* path, const std::string& key, int rule_n, double c
         if (l.find(tag) == std::string::npos) keep.push_back(l);
     char line[512];
     std::snprintf(line, sizeof(line),
-                  "{%s, \"rule_n\": %d, \"cover\": %.17g, \"eval_blocks\": %d, \"ms\": %.6g}",
-                  tag.c_str(), rule_n, cover, blocks, ms);
+                  "{%s, \"rule_n\": %d, \"cover\": %.17g, \"eval_blocks\": %d, "
+                  "\"init_level\": %d, \"ms\": %.6g}",
+                  tag.c_str(), rule_n, cover, blocks, init_level, ms);
     keep.push_back(line);
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
@@ -1052,10 +1060,12 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
     int rule_n = ctx->opt.rule_n;
     double cover = ctx->opt.cover;
     int blocks = ctx->opt.eval_blocks;
-    if (cache_path && cached_choice(cache_path, key, rule_n, cover, blocks)) {
+    int init_level = ctx->opt.init_level;
+    if (cache_path && cached_choice(cache_path, key, rule_n, cover, blocks, init_level)) {
         ctx->opt.rule_n = rule_n;
         ctx->opt.cover = cover;
         ctx->opt.eval_blocks = blocks;
+        ctx->opt.init_level = init_level;
         return PAID_OK;
     }
     if (nb <= 0 || !sample) return fail(ctx, PAID_ERR_ARG, "autotune needs a sample batch");
@@ -1075,13 +1085,14 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
         return fail(ctx, PAID_ERR_CUDA, "autotune events");
     }
     double best_ms = 1e300, best_cover = saved.cover;
-    int best_blocks = saved.eval_blocks, best_rule = saved.rule_n;
+    int best_blocks = saved.eval_blocks, best_rule = saved.rule_n, best_level = saved.init_level;
     bool warm = false;
     // time one candidate; keep it when it is the fastest so far
-    auto trial = [&](int rn, double c, int g) {
+    auto trial = [&](int rn, double c, int g, int lv) {
         ctx->opt.rule_n = rn;
         ctx->opt.cover = c;
         ctx->opt.eval_blocks = g;
+        ctx->opt.init_level = lv;
         if (!warm) {   // first call: graph capture, tables, caches
             if (paid_integrate_multi(ctx, sample, nb, workspace, ws_bytes, stream) == PAID_OK)
                 paid_wait(ctx, nullptr);
@@ -1096,15 +1107,26 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
         if (rc != PAID_OK || outcome != PAID_OK || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
             return;
-        if (ms < best_ms) { best_ms = ms; best_cover = c; best_blocks = g; best_rule = rn; }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_cover = c;
+            best_blocks = g;
+            best_rule = rn;
+            best_level = lv;
+        }
     };
     // stagewise: the rule order at cover 1 and the largest grid, then cover,
-    // then the grid, each with the choices made so far
-    for (int rn : rules) trial(rn, 1.0, grids.back());
+    // then the grid, then the start level (the first batch of regions of every
+    // unit: 16 or 64), each with the choices made so far
+    const int lv0 = saved.init_level;
+    for (int rn : rules) trial(rn, 1.0, grids.back(), lv0);
     const int rule_pick = best_rule;
-    for (double c : covers) trial(rule_pick, c, grids.back());
+    for (double c : covers) trial(rule_pick, c, grids.back(), lv0);
     const double cover_pick = best_cover;
-    for (int g : grids) trial(rule_pick, cover_pick, g);
+    for (int g : grids) trial(rule_pick, cover_pick, g, lv0);
+    const int grid_pick = best_blocks;
+    for (int lv : {2, 3})
+        if (lv != lv0) trial(rule_pick, cover_pick, grid_pick, lv);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->opt = saved;
@@ -1112,7 +1134,9 @@ int paid_autotune(paid_ctx* ctx, const paid_batch* sample, int nb, const char* c
     ctx->opt.rule_n = best_rule;
     ctx->opt.cover = best_cover;
     ctx->opt.eval_blocks = best_blocks;
-    if (cache_path) store_choice(cache_path, key, best_rule, best_cover, best_blocks, best_ms);
+    ctx->opt.init_level = best_level;
+    if (cache_path)
+        store_choice(cache_path, key, best_rule, best_cover, best_blocks, best_level, best_ms);
     return PAID_OK;
 }
 

@@ -1420,19 +1420,19 @@ template <int N>
 struct GroupSmemF {
     static constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
     float2 X[R][NF][9];          // X_ac at the fine rows
-    union {
-        struct {
+    union {                      // the column data until every row is summed,
+        struct {                 // then the row sums
             float2 Yf[R][NF][9];     // wf_j Y_bd(y_j)
             float2 Yc[R][N + 1][9];  // wc_j Y_bd(y_2j)
             float2 CY[R][NF][2];     // cos ky, cos ky' (flow kinds: cos(ky -+ qy/2))
         } c;
         struct {
-            float2 Mf[R][9][9];      // fine moments
-            float2 Mc[R][9][9];      // coarse moments
-        } m;
+            float2 Rf[R][NF][9];     // row sums with the row's fine weight
+            float2 Rc[R][N + 1][9];  // coarse (even rows)
+        } r;
     } u;
-    float2 Rf[R][NF][9];         // row sums with the row's fine weight
-    float2 Rc[R][N + 1][9];      // coarse (even rows)
+    float2 Mf[R][9][9];          // fine moments
+    float2 Mc[R][9][9];          // coarse moments
     float2 C[R][4];              // sin, cos of the region centre (x, y) times pi
     float2 Q[R][4];              // cos qx, sin qx, cos qy, sin qy (flow: of q/2)
     float2 H[R][2];              // 1/2T, T (Omega for the flow kinds)
@@ -1455,7 +1455,7 @@ __device__ __forceinline__ void ff_rot(f2 c, f2 s, f2 co, f2 so, f2& c2, f2& s2)
 // only -- so that a launch carries only the kernel F it needs (the row loop's
 // code stays within the instruction cache).
 template <int N, int KF>
-__global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1))
+__global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1), 6)
 k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
 {
     constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
@@ -1576,11 +1576,11 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
             }
         }
         __syncthreads();
+        f2 rf[9], rc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { rf[k] = {0.0f, 0.0f}; rc[k] = {0.0f, 0.0f}; }
         if (live) {
             const f2 W = ff_ld(S.H[rho][1]);
-            f2 rf[9], rc[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) { rf[k] = {0.0f, 0.0f}; rc[k] = {0.0f, 0.0f}; }
             // one node (i, j): the kernel F once, then every row sum
             auto node = [&](int j, bool even) {
                 const f2 x1 = ff_fma(B1, ff_ld(S.u.c.CY[rho][j][0]), A1);
@@ -1607,15 +1607,20 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 node(j, true);
                 if (j + 1 < NF) node(j + 1, false);
             }
+        }
+        // the row sums take the column data's memory: every row is done first
+        __syncthreads();
+        if (live) {
             // the row's own weight in float-float
             const f2 wr = ff_ld(S.wr[i]);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) S.Rf[rho][i][k] = ff_st(ff_mul(wr, ff_fast(rf[k].hi, rf[k].lo)));
+            for (int k = 0; k < 9; ++k)
+                S.u.r.Rf[rho][i][k] = ff_st(ff_mul(wr, ff_fast(rf[k].hi, rf[k].lo)));
             if ((i & 1) == 0) {
                 const f2 wrc = ff_ld(S.wrc[i >> 1]);
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
-                    S.Rc[rho][i >> 1][k] = ff_st(ff_mul(wrc, ff_fast(rc[k].hi, rc[k].lo)));
+                    S.u.r.Rc[rho][i >> 1][k] = ff_st(ff_mul(wrc, ff_fast(rc[k].hi, rc[k].lo)));
             }
         }
         __syncthreads();
@@ -1627,12 +1632,12 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 f2 mf = {0.0f, 0.0f}, mc = {0.0f, 0.0f};
 #pragma unroll 5
                 for (int r = 0; r < NF; ++r)
-                    ff_acc(ff_ld(S.X[rho][r][ac]), ff_ld(S.Rf[rho][r][bd]), mf);
+                    ff_acc(ff_ld(S.X[rho][r][ac]), ff_ld(S.u.r.Rf[rho][r][bd]), mf);
 #pragma unroll
                 for (int r = 0; r <= N; ++r)
-                    ff_acc(ff_ld(S.X[rho][2 * r][ac]), ff_ld(S.Rc[rho][r][bd]), mc);
-                S.u.m.Mf[rho][ac][bd] = ff_st(ff_fast(mf.hi, mf.lo));
-                S.u.m.Mc[rho][ac][bd] = ff_st(ff_fast(mc.hi, mc.lo));
+                    ff_acc(ff_ld(S.X[rho][2 * r][ac]), ff_ld(S.u.r.Rc[rho][r][bd]), mc);
+                S.Mf[rho][ac][bd] = ff_st(ff_fast(mf.hi, mf.lo));
+                S.Mc[rho][ac][bd] = ff_st(ff_fast(mc.hi, mc.lo));
             }
         }
         __syncthreads();
@@ -1648,8 +1653,8 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
                             const f2 c = ff_ld(c_ffpair[l][k1][m][k2]);
                             const int ac = 3 * c_ffa[l][k1] + c_ffa[m][k2];
                             const int bd = 3 * c_ffb[l][k1] + c_ffb[m][k2];
-                            ff_acc(c, ff_ld(S.u.m.Mf[rho][ac][bd]), q2);
-                            ff_acc(c, ff_ld(S.u.m.Mc[rho][ac][bd]), q1);
+                            ff_acc(c, ff_ld(S.Mf[rho][ac][bd]), q2);
+                            ff_acc(c, ff_ld(S.Mc[rho][ac][bd]), q1);
                         }
                 }
                 q2 = ff_fast(q2.hi, q2.lo);

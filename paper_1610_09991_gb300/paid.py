@@ -420,18 +420,31 @@ class Context:
         path = cache_path.encode() if cache_path else None
         arr, outs, n_int, maxr = self._batch_array(batches or [])
         n = self.units(batches or [])
-        nbytes = 0
-        ws = None
-        if n:
-            cap = self.default_capacity(n, maxr)
-            ws = self.workspace(n, cap)
-            nbytes = self.workspace_size(n, cap)
-        rc = self._lib.paid_autotune(self._h, arr if batches else None, len(batches or []), path,
-                                     ctypes.c_void_p(ws.data_ptr()) if ws is not None else None,
-                                     nbytes, ctypes.c_void_p(stream.cuda_stream))
-        if rc != OK:
-            raise PaidError(rc, self.last_error())
-        return self.get_options()
+        cap = self.default_capacity(n, maxr) if n else 0
+        while True:
+            nbytes = 0
+            ws = None
+            if n:
+                ws = self.workspace(n, cap)
+                nbytes = self.workspace_size(n, cap)
+            rc = self._lib.paid_autotune(self._h, arr if batches else None, len(batches or []),
+                                         path,
+                                         ctypes.c_void_p(ws.data_ptr()) if ws is not None else None,
+                                         nbytes, ctypes.c_void_p(stream.cuda_stream))
+            if rc == ERR_CUDA and n:
+                # no candidate completed: a pool too small for the sample
+                # stops every one of them; grow it while memory allows
+                del ws
+                self.release_workspace()
+                free, _ = torch.cuda.mem_get_info(self.device)
+                bigger = min(4 * cap, self.pool_capacity(n, int(0.9 * free)), 2 ** 32 - 1)
+                if bigger > cap:
+                    cap = bigger
+                    self._grown_capacity = max(getattr(self, "_grown_capacity", 0), cap)
+                    continue
+            if rc != OK:
+                raise PaidError(rc, self.last_error())
+            return self.get_options()
 
     def _batch_array(self, batches):
         """ctypes paid_batch array and fresh output tensors for dict batches."""
@@ -546,7 +559,9 @@ class Context:
     def integrate_host(self, batches, pool_capacity=None, proposal=None, margin=1.0):
         """End-to-end call on host (numpy) inputs: copies q and lm from pinned
         host memory to the device, integrates (seeded from `proposal`, a
-        Proposal network, with `margin`, when given), and copies the results back.
+        Proposal network, with `margin` -- a number, or a function of the
+        batch temperature giving a margin or None for the uniform start -- when
+        given), and copies the results back.
         Returns (list of numpy Result, bytes host->device, bytes device->host)."""
         torch = _torch()
         dev = self.torch_device
@@ -562,6 +577,12 @@ class Context:
             dbs.append(d)
         if proposal is None:
             outs = self.integrate_multi(dbs, pool_capacity=pool_capacity, stream=stream)
+        elif callable(margin):
+            # a margin per batch temperature (None: the uniform start)
+            from . import proposal as PR
+            maps = PR.seed_maps(proposal, self, dbs, margin)
+            outs = self.integrate_multi_seeded(dbs, maps, 0.0, pool_capacity=pool_capacity,
+                                               stream=stream)
         else:
             maps = proposal.predict(self, dbs, stream)
             outs = self.integrate_multi_seeded(dbs, maps, margin, pool_capacity=pool_capacity,

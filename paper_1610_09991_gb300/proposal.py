@@ -22,6 +22,14 @@ from . import workloads as W
 GROUP_OPTIONS = dict(group_mode=1, rule_n=12, cover=1.0)
 
 
+def _options(options):
+    """Integrate options of the proposal's runs: the shared-partition path's
+    rule and cover unless one partition per integral is asked for."""
+    if options.get("group_mode", 1):
+        return dict(GROUP_OPTIONS, **options)
+    return dict(options)
+
+
 def draw_batches(T, nq, rel_tol=1e-6, abs_tol=1e-10, max_regions=100000, device=0):
     """ph + pp batches of all 81 pairs on an nq x nq zone grid, on the device."""
     import torch
@@ -69,25 +77,69 @@ def predict(prop, ctx, batches):
     return prop.predict(ctx, batches)
 
 
-def calibrate_margin(prop, ctx, batches, margins=(0.0, 0.5, 1.0)):
-    """Region evaluations of the seeded run at each margin on these batches:
-    returns {margin: (region evaluations, rounds)}."""
+#: temperature bands of the margin policy (upper edges) and the margins tried;
+#: None = no seed (the uniform start)
+T_BANDS = (0.015, 0.03, 0.045, 0.07, float("inf"))
+MARGINS = (0.0, 0.5, 1.0, 2.0, None)
+
+
+class MarginPolicy:
+    """Seed margin per temperature band, calibrated on training draws: a
+    batch at temperature T starts each cell at floor(level - margin(T)), or
+    from the uniform start where the band's best choice is no seed."""
+
+    def __init__(self, margins, bands=T_BANDS):
+        self.bands = tuple(bands)
+        self.margins = tuple(margins)
+
+    def __call__(self, T):
+        for edge, m in zip(self.bands, self.margins):
+            if T <= edge:
+                return m
+        return self.margins[-1]
+
+    def as_dict(self):
+        return {("T <= %g" % e): m for e, m in zip(self.bands, self.margins)}
+
+
+def seed_maps(prop, ctx, batches, policy):
+    """Level maps with each batch's margin applied (for a call with margin 0):
+    map - margin(T), or the context's start level everywhere (no seed)."""
+    maps = predict(prop, ctx, batches)
+    off = 0
+    for b in batches:
+        n = int(b["q"].shape[0]) * (1 if ctx.options.group_mode else int(b["lm"].shape[0]))
+        m = policy(float(b["T"]))
+        if m is None:
+            maps[off:off + n] = float(ctx.options.init_level)
+        elif m:
+            maps[off:off + n] -= m
+        off += n
+    return maps
+
+
+def calibrate_margin(prop, ctx, batches, margins=MARGINS):
+    """Region evaluations and rounds of the seeded run at each margin (None:
+    the uniform start) on these batches: {margin: (region evaluations, rounds)}."""
     maps = predict(prop, ctx, batches)
     out = {}
     for mg in margins:
-        ctx.integrate_multi_seeded(batches, maps, mg)
+        if mg is None:
+            ctx.integrate_multi(batches)
+        else:
+            ctx.integrate_multi_seeded(batches, maps, mg)
         st = ctx.last_stats()
         out[mg] = (st["region_evals"], st["rounds"])
     return out
 
 
-def train_default(device=0, n_draws=128, nq=12, epochs=300, seed=0, log=None, **options):
+def train_default(device=0, n_draws=192, nq=12, epochs=300, seed=0, log=None, **options):
     """The proposal trained on n_draws seeded parameter draws (seeds 0..n-1)
     for the given integrate options (default: the shared-partition path):
     returns (Proposal, training-loss history, seconds)."""
     import time
     import torch
-    opts = dict(GROUP_OPTIONS, **options)
+    opts = _options(options)
     t0 = time.perf_counter()
     x, t = training_set(W.parameter_draws(n_draws, 0), nq, device, **opts)
     prop = P.Proposal(device=device, seed=seed)
@@ -98,19 +150,21 @@ def train_default(device=0, n_draws=128, nq=12, epochs=300, seed=0, log=None, **
     return prop, hist, time.perf_counter() - t0
 
 
-def calibrate_default(prop, device=0, n_draws=48, nq=8, t_range=(0.01, 0.3), **options):
-    """Margin with the fewest region evaluations summed over the training draws
-    whose T lies in t_range (smaller q grid); returns (margin, {margin:
-    (region evaluations, rounds)})."""
-    opts = dict(GROUP_OPTIONS, **options)
-    tot = {}
+def calibrate_default(prop, device=0, n_draws=96, nq=8, **options):
+    """The margin policy: per temperature band (T_BANDS) the margin of MARGINS
+    with the fewest region evaluations summed over the band's training draws
+    (seeds 0..n_draws-1, smaller q grid); returns (MarginPolicy, {band:
+    {margin: (region evaluations, rounds)}})."""
+    opts = _options(options)
+    tot = [dict() for _ in T_BANDS]
     for tp, mu, T in W.parameter_draws(n_draws, 0):
-        if not (t_range[0] <= T <= t_range[1]):
-            continue
+        k = next(i for i, e in enumerate(T_BANDS) if T <= e)
         ctx = P.Context(1.0, tp, mu, ffset=9, device=device, **opts)
         for mg, (ev, rd) in calibrate_margin(prop, ctx, draw_batches(T, nq, device=device)).items():
-            e0, r0 = tot.get(mg, (0, 0))
-            tot[mg] = (e0 + ev, r0 + rd)
+            e0, r0 = tot[k].get(mg, (0, 0))
+            tot[k][mg] = (e0 + ev, r0 + rd)
         ctx.close()
-    best = min(tot, key=lambda k: tot[k][0]) if tot else 1.0
-    return best, tot
+    best = [min(t, key=lambda m: t[m][0]) if t else None for t in tot]
+    policy = MarginPolicy(best)
+    return policy, {("T <= %g" % e): {str(m): v for m, v in t.items()}
+                    for e, t in zip(T_BANDS, tot)}

@@ -237,18 +237,19 @@ def test_autotune_picks_a_candidate_and_caches_it(paid, torch, tmp_path):
     ctx = paid.Context(*LAT, ffset=9, group_mode=1)
     o = ctx.autotune(dbs, path)
     assert o.cover in (0.5, 0.75, 0.9, 1.0) and o.eval_blocks in (608, 1216, 4864)
-    assert o.rule_n in (4, 6, 8, 10, 12)
+    assert o.rule_n in (4, 6, 8, 10, 12) and o.init_level in (2, 3)
     lines = open(path).read().splitlines()
-    assert len(lines) == 1 and "group_mode=1" in lines[0]
+    assert len(lines) == 1 and "group_mode=1" in lines[0] and '"init_level": ' in lines[0]
     # a second context applies the cached choice without a sample
     c2 = paid.Context(*LAT, ffset=9, group_mode=1)
     o2 = c2.autotune(None, path)
-    assert (o2.rule_n, o2.cover, o2.eval_blocks) == (o.rule_n, o.cover, o.eval_blocks)
+    assert ((o2.rule_n, o2.cover, o2.eval_blocks, o2.init_level)
+            == (o.rule_n, o.cover, o.eval_blocks, o.init_level))
     # tuned options keep parity with the oracle on the sample
     gs = _run(paid, torch, ctx, w.batches)
     for b, g in zip(w.batches, gs):
         o_ = oracle.integrate_batch(b.kind, b.q, b.lm, b.T, LAT, b.rel_tol, b.abs_tol,
-                                    b.max_regions, rule_n=o.rule_n)
+                                    b.max_regions, rule_n=o.rule_n, init_level=o.init_level)
         assert assert_parity(g, o_, b.rel_tol, b.abs_tol, batch_ident(b)) >= 0.9 * b.n
     # a per-integral context keeps its own entry (another key)
     c3 = paid.Context(*LAT, ffset=9)

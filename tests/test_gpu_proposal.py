@@ -189,16 +189,16 @@ def test_seeded_start_keeps_parity(paid, torch, mode, group_mode):
 @pytest.fixture(scope="module")
 def trained(paid, torch):
     # the default training (128 draws of the shared-partition path, FP32 pipe,
-    # N = 12; ~15 s), margin calibrated on the training draws
+    # N = 12; ~15 s), the margin policy calibrated on the training draws
     from paper_1610_09991_gb300 import proposal as PR
     prop, hist, secs = PR.train_default(eval_fp32=1)
-    margin, tot = PR.calibrate_default(prop, n_draws=32, nq=6, eval_fp32=1)
-    return prop, hist, margin, tot
+    policy, tot = PR.calibrate_default(prop, eval_fp32=1)
+    return prop, hist, policy, tot
 
 
 def test_trained_proposal_saves_region_evaluations(paid, torch, trained):
     from paper_1610_09991_gb300 import proposal as PR
-    prop, hist, margin, tot = trained
+    prop, hist, policy, tot = trained
     assert hist[-1] < 0.1 * hist[0]
     # a held-out draw (seed 10000: t' = -0.169, mu = -0.807, T = 0.105)
     tp, mu, T = W.parameter_draws(1, 10000)[0]
@@ -206,12 +206,12 @@ def test_trained_proposal_saves_region_evaluations(paid, torch, trained):
     bs = PR.draw_batches(T, 8)
     plain = _np(ctx.integrate_multi(bs))
     st_plain = ctx.last_stats()
-    maps = PR.predict(prop, ctx, bs)
-    seeded = _np(ctx.integrate_multi_seeded(bs, maps, margin))
+    assert policy(T) is not None
+    seeded = _np(ctx.integrate_multi_seeded(bs, PR.seed_maps(prop, ctx, bs, policy), 0.0))
     st_seed = ctx.last_stats()
-    _np(ctx.integrate_multi_seeded(bs, None, margin))
+    _np(ctx.integrate_multi_seeded(bs, None, 0.0))
     st_uni = ctx.last_stats()
-    print("margin", margin, tot, "region evals plain / seeded / uniform level 4:",
+    print("policy", policy.as_dict(), tot, "region evals plain / seeded / uniform level 4:",
           st_plain["region_evals"], st_seed["region_evals"], st_uni["region_evals"],
           "rounds", st_plain["rounds"], st_seed["rounds"], st_uni["rounds"])
     # fewer region evaluations than both the unseeded and the uniform start
@@ -230,11 +230,11 @@ def test_trained_proposal_saves_region_evaluations(paid, torch, trained):
 def test_trained_seed_matches_oracle(paid, torch, trained):
     # the trained-map seeded run, integral by integral against the oracle
     from paper_1610_09991_gb300 import proposal as PR
-    prop, hist, margin, tot = trained
+    prop, hist, policy, tot = trained
     w = W.config_heldout(nq=6)
     ctx = paid.Context(*w.lattice, ffset=9, eval_fp32=1, **PR.GROUP_OPTIONS)
     dbs = _dbs(torch, w.batches)
-    outs = _np(ctx.integrate_multi_seeded(dbs, PR.predict(prop, ctx, dbs), margin))
+    outs = _np(ctx.integrate_multi_seeded(dbs, PR.seed_maps(prop, ctx, dbs, policy), 0.0))
     for b, g in zip(w.batches, outs):
         assert np.all(g[3] == 0)
         idx = np.arange(0, b.n, 3)
@@ -246,3 +246,23 @@ def test_trained_seed_matches_oracle(paid, torch, trained):
         ident = lambda i: (b.kind, b.q[idx[i] // P_], int(b.lm[idx[i] % P_][0]),
                            int(b.lm[idx[i] % P_][1]), b.T)
         assert_parity(sub, osub, b.rel_tol, b.abs_tol, ident)
+
+
+def test_margin_policy_never_loses_much_on_a_temperature_sweep(paid, torch, trained):
+    # the calibrated policy across temperatures (12 from 1 to 0.005, 4 x 4 q
+    # grid, ph + pp): where the seed does not pay (low T) the policy falls back
+    # to the uniform start, so the sweep needs at most a few per cent more
+    # region evaluations than without the network, and every integral converges
+    from paper_1610_09991_gb300 import proposal as PR
+    prop, hist, policy, tot = trained
+    w = W.config_temperature_sweep(nq=4)
+    ctx = paid.Context(*w.lattice, ffset=9, eval_fp32=1, **PR.GROUP_OPTIONS)
+    dbs = _dbs(torch, w.batches)
+    plain = _np(ctx.integrate_multi(dbs))
+    ev_plain = ctx.last_stats()["region_evals"]
+    seeded = _np(ctx.integrate_multi_seeded(dbs, PR.seed_maps(prop, ctx, dbs, policy), 0.0))
+    ev_seed = ctx.last_stats()["region_evals"]
+    print("policy", policy.as_dict(), "sweep region evals plain / seeded", ev_plain, ev_seed)
+    assert ev_seed <= 1.05 * ev_plain
+    for a, c in zip(seeded, plain):
+        assert np.all(a[3] == 0) and np.all(c[3] == 0)
