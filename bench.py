@@ -45,27 +45,29 @@ EVAL_DRAM_BYTES_PER_REGION = 18.3
 # (profiles/k_eval_df_first_shell.md).
 DF_FP32_FLOPS_PER_REGION = 2 * 7774.8 + 29243.1 + 3018.3   # 47,811
 # FP64 flops per region of the shared-partition kernel (k_eval_group, 81 pairs)
-# by rule order N: DFMA counted as 2, DADD / DMUL as 1, from the ncu
-# instruction counters of one launch over 10^5 regions per N divided by the
-# regions (profiles/k_eval_group_flow_step_q4.md), taken when every node still
-# evaluated the near-degenerate series of the kernel F.  That series (d^2,
-# four FMA, two products: 11 flops per node) now runs only in warps that hold a
-# node with |x1 - x2| <= 1/16, so the figure used is the count minus
-# 11 (2N+1)^2: a lower bound on the work done, which keeps the roofline
-# fraction conservative.
+# by rule order N: DFMA counted as 2, DADD / DMUL as 1, from ncu instruction
+# counters divided by the regions of the launch
+# (profiles/k_eval_group_flow_step_q4.md).  N = 12: the current kernel, one
+# launch over 6,240 regions of the flow step at T = 0.05 (DFMA 26,843, DADD
+# 4,495, DMUL 8,089 per region).  Other N: counts taken when every node still
+# evaluated the near-degenerate series of the kernel F, minus that series (11
+# flops per node; it now runs only in warps holding a node with |x1 - x2| <=
+# 1/16): lower bounds on the work done.
 GROUP_NEAR_FLOPS_PER_NODE = 2 * 4 + 3
 GROUP_FP64_FLOPS_PER_REGION = {
     n: f - GROUP_NEAR_FLOPS_PER_NODE * (2 * n + 1) ** 2
     for n, f in {4: 2 * 4839 + 663 + 1766, 6: 2 * 8955 + 1285 + 3118,
-                 8: 2 * 14367 + 2131 + 4902, 10: 2 * 21075 + 3201 + 7118,
-                 12: 2 * 29079 + 4495 + 9766}.items()}
+                 8: 2 * 14367 + 2131 + 4902, 10: 2 * 21075 + 3201 + 7118}.items()}
+GROUP_FP64_FLOPS_PER_REGION[12] = 2 * 26843 + 4495 + 8089      # 66,270
 # FP32-pipe thread instructions (FADD + FMUL + FFMA, one issue slot each) and
 # FP32 flops (FFMA counted as 2) per region of the float-float form of the
-# shared-partition kernel (k_eval_group_ff<N, 1>, ph / pp, 81 pairs), from the
-# ncu instruction counters of one launch over 6,240 regions of the flow step
-# at T = 0.05 divided by its regions (profiles/k_eval_group_ff_flow_step_q4.md).
-GROUP_FP32_INSTR_PER_REGION = {12: 292300}
-GROUP_FP32_FLOPS_PER_REGION = {12: 359000}
+# shared-partition kernel (k_eval_group_ff<N, 1>, ph / pp, 81 pairs, moments in
+# the Fourier basis), from the ncu instruction counters of one launch over
+# 6,240 regions of the flow step at T = 0.05 divided by its regions
+# (profiles/k_eval_group_ff_flow_step_q4.md: FADD 150,617, FMUL 23,533, FFMA
+# 49,621 per region).
+GROUP_FP32_INSTR_PER_REGION = {12: 150617 + 23533 + 49621}              # 223,771
+GROUP_FP32_FLOPS_PER_REGION = {12: 150617 + 23533 + 2 * 49621}          # 273,392
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
@@ -75,7 +77,7 @@ GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["paid", "reference"], default="paid")
     ap.add_argument("--temperature", type=float, default=None,
@@ -160,7 +162,11 @@ def workload_config(w, ff, eval_mode, rule_n=4):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling every 50 ms, started before the warm-up steps so
+    that the tool is running when the timed region begins; only the samples
+    stamped inside the marked window (mark_start / mark_stop, wall clock) are
+    kept."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -168,6 +174,7 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = None
+        self.window = [None, None]
 
     def start(self):
         try:
@@ -175,12 +182,19 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
+    def mark_start(self):
+        self.window[0] = time.time()
+
+    def mark_stop(self):
+        self.window[1] = time.time()
+
     def stop(self):
+        import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -188,24 +202,30 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        t0, t1 = self.window
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                mhz, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
+            if t0 is not None and not (t0 - 0.05 <= ts <= (t1 or ts) + 0.05):
+                continue
+            sm.append(mhz)
+            smax.append(mx)
+            for n, v in zip(names, f[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "sampling": "nvidia-smi every 50 ms, samples inside the timed region"}
 
 
 # --------------------------------------------------------------------------- peaks
@@ -487,6 +507,8 @@ def run_paid(args):
         return step
 
     step = make_step(ctx, learned)
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step()
     # the per-step bookkeeping below uses torch kernels that load on first use
@@ -494,11 +516,11 @@ def run_paid(args):
     int((torch.cat([warm, warm]) == 0).sum())
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
-    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark_start()
+    prop_l0 = prop.launches if prop is not None else 0
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = dict(conv=0, budget=0, region_evals=0, node_evals=0, launches=0, eval_launches=0,
                eval_ms=0.0, reduce_ms=0.0, scan_ms=0.0, split_ms=0.0, rounds=0, peak_pool=0,
@@ -513,6 +535,8 @@ def run_paid(args):
     torch.cuda.nvtx.range_pop()
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_stop()
+    prop_launches = (prop.launches - prop_l0) if prop is not None else 0
     if dist:
         dist.barrier()
     for outs, st in zip(step_outs, step_stats):
@@ -608,7 +632,9 @@ def run_paid(args):
                        parallelism="%d ranks, %s" % (world, "q rows split across ranks"
                                                      if scaling == "strong" else
                                                      "one instance per rank")),
-        "clocks": clk, "roofline": roof, "gpu_launches": agg["launches"],
+        "clocks": clk, "roofline": roof, "gpu_launches": agg["launches"] + prop_launches,
+        "gpu_launches_split": {"integrate_calls": agg["launches"],
+                               "proposal_inference": prop_launches},
         "e2e": e2e,
         "path": PATHS[args.path],
         "proposal": prop_info,

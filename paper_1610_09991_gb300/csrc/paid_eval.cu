@@ -555,7 +555,10 @@ __device__ __forceinline__ f2 df_exp_neg(f2 a, const float2* tab)
     const float C1 = 0.010833740234375f;          // 0x1.63p-7
     const float C2 = -3.3155381515825866e-06f;
     const float C3 = 2.572804640231345e-14f;
-    const float k = rintf(a.hi * 92.33248138427734f);
+    // k = rint(64 a_hi / ln2) by the shift 1.5 * 2^23 (a_hi 64/ln2 < 2^13):
+    // the low encoding bits of the sum are k
+    const float kt = fmaf(a.hi, 92.33248138427734f, 12582912.0f);
+    const float k = __fsub_rn(kt, 12582912.0f);
     const float t1 = fmaf(-k, C1, a.hi);          // exact (Sterbenz)
     f2 r = two_sum(t1, a.lo);
     const f2 kc2 = {k * C2, fmaf(k, C2, -k * C2)};
@@ -567,7 +570,7 @@ __device__ __forceinline__ f2 df_exp_neg(f2 a, const float2* tab)
     f2 P = df_add_f(df_mul_f(t, p), 0.5f);
     P = df_add_f(df_mul(t, P), 1.0f);
     P = df_add_f(df_mul(t, P), 1.0f);
-    const int n = -int(k);
+    const int n = 0x4B400000 - __float_as_int(kt);   // -k
     const int m = n >> 6;                         // floor(n / 64)
     const int j = n & 63;
     f2 res = df_mul(P, df_c(tab[j]));
@@ -1074,7 +1077,12 @@ __device__ __forceinline__ f2 ff_exp_neg(f2 a, const float2* tab)
     const float C1 = 0.010833740234375f;          // 0x1.63p-7
     const float C2 = -3.3155381515825866e-06f;
     const float C3 = 2.572804640231345e-14f;
-    const float k = rintf(a.hi * 92.33248138427734f);
+    // k = rint(64 a_hi / ln2) by the shift 1.5 * 2^23: the sum lies in
+    // [2^23, 2^24), where the float grid is the integers, so its low encoding
+    // bits are k (two FP32-pipe instructions in place of a float rounding and
+    // a float-to-integer conversion)
+    const float kt = fmaf(a.hi, 92.33248138427734f, 12582912.0f);
+    const float k = __fsub_rn(kt, 12582912.0f);
     const float t1 = fmaf(-k, C1, a.hi);          // exact
     const f2 s1 = ff_two_sum(t1, a.lo);
     const float p2 = __fmul_rn(k, C2);
@@ -1097,7 +1105,7 @@ __device__ __forceinline__ f2 ff_exp_neg(f2 a, const float2* tab)
     sl = __fadd_rn(sl, c);
     const f2 P0 = ff_fast(1.0f, S.hi);
     const f2 P = ff_fast(P0.hi, __fadd_rn(P0.lo, sl));
-    const int n = -int(k);
+    const int n = 0x4B400000 - __float_as_int(kt);   // -k
     const int m = n >> 6;                         // floor(n / 64)
     const int j = n & 63;
     const float2 tj = tab[j];
@@ -1409,30 +1417,40 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
 
 // ---------------------------------------------------------------------------
 // The FP32-pipe form of the shared-partition kernel (options.eval_fp32 with
-// group_mode).  Same rule, moments and data flow as k_eval_group, with every
-// per-node, per-row and per-region quantity an unevaluated pair of FP32
-// numbers on the FP32 pipe (64x the FP64 pipe on this GPU): the node abscissae
-// (rotations of the region centre), the reduced energies, the kernel F, the
-// row sums, the moments and the pair combinations.  FP64 remains for the two
-// sincospi of the exact dyadic centre, the conversions of the per-region
-// inputs, and each pair's Q_2N and Q_N - Q_2N times the Jacobian.
+// group_mode).  Same rule and data flow as k_eval_group, with every per-node,
+// per-row and per-region quantity an unevaluated pair of FP32 numbers on the
+// FP32 pipe (64x the FP64 pipe on this GPU): the node abscissae (rotations of
+// the region centre), the reduced energies, the kernel F, the row sums, the
+// moments and the pair combinations.  FP64 remains for the two sincospi of the
+// exact dyadic centre, the conversions of the per-region inputs, and each
+// pair's Q_2N and Q_N - Q_2N times the Jacobian.
+//
+// The moments are taken in the Fourier basis phi = (1, cos k, sin k, cos 2k,
+// sin 2k) of each direction instead of the nine products X_ac = g_a(k) g'_c(k')
+// (g = (1, cos k, sin k) at k, g' the same at k' = k + q, or q - k for pp, or
+// k for the flow kinds): every product is a fixed combination of the five
+// (cos k cos k' = cos q (1 + cos 2k) / 2 - s sin q sin 2k / 2, ...), so a row
+// needs 5 sums instead of 9 and a region 25 moments instead of 81, and the 81
+// product moments follow from two small exact transforms per rule
+// (ff_fourier_to_products).
 template <int N>
 struct GroupSmemF {
     static constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;
-    float2 X[R][NF][9];          // X_ac at the fine rows
+    float2 X[R][NF][5];          // phi_u(kx_i) at the fine rows
     union {                      // the column data until every row is summed,
-        struct {                 // then the row sums
-            float2 Yf[R][NF][9];     // wf_j Y_bd(y_j)
-            float2 Yc[R][N + 1][9];  // wc_j Y_bd(y_2j)
+        struct {                 // then the row sums, then the x-transformed moments
+            float2 Yf[R][NF][5];     // wf_j phi_v(ky_j)
+            float2 Yc[R][N + 1][5];  // wc_j phi_v(ky_2j)
             float2 CY[R][NF][2];     // cos ky, cos ky' (flow kinds: cos(ky -+ qy/2))
         } c;
         struct {
-            float2 Rf[R][NF][9];     // row sums with the row's fine weight
-            float2 Rc[R][N + 1][9];  // coarse (even rows)
+            float2 Rf[R][NF][5];     // row sums with the row's fine weight
+            float2 Rc[R][N + 1][5];  // coarse (even rows)
         } r;
+        float2 T[R][2][9][5];        // G with the x index taken to X_ac (fine, coarse)
     } u;
-    float2 Mf[R][9][9];          // fine moments
-    float2 Mc[R][9][9];          // coarse moments
+    float2 G[R][2][5][5];        // Fourier moments (fine, coarse)
+    float2 M[R][2][9][9];        // product moments M[ac][bd] (fine, coarse)
     float2 C[R][4];              // sin, cos of the region centre (x, y) times pi
     float2 Q[R][4];              // cos qx, sin qx, cos qy, sin qy (flow: of q/2)
     float2 H[R][2];              // 1/2T, T (Omega for the flow kinds)
@@ -1449,6 +1467,34 @@ __device__ __forceinline__ void ff_rot(f2 c, f2 s, f2 co, f2 so, f2& c2, f2& s2)
 {
     c2 = ff_sub(ff_mul(c, co), ff_mul(s, so));
     s2 = ff_add(ff_mul(s, co), ff_mul(c, so));
+}
+
+// Coefficients g_u of a function in the basis phi = (1, c, s, cos 2k, sin 2k)
+// (c, s = cos k, sin k) to its products with (1, c, s) x (1, c', s'), index
+// 3a + c, where (c', s') is (c, sg s) rotated by the angle with cosine cq and
+// sine sq (sg = -1 for pp's k' = q - k).  With c^2 = (1 + cos 2k) / 2,
+// s^2 = (1 - cos 2k) / 2 and s c = sin 2k / 2:
+//   c'   = cq c - sg sq s           s'   = sq c + sg cq s
+//   c c' = cq (1 + cos 2k)/2 - sg sq sin 2k/2
+//   c s' = sq (1 + cos 2k)/2 + sg cq sin 2k/2
+//   s c' = cq sin 2k/2 - sg sq (1 - cos 2k)/2
+//   s s' = sq sin 2k/2 + sg cq (1 - cos 2k)/2
+__device__ __forceinline__ void ff_fourier_to_products(const f2 g[5], f2 cq, f2 sq, bool flip,
+                                                       f2 out[9])
+{
+    const f2 cs = flip ? ff_neg(cq) : cq, ss = flip ? ff_neg(sq) : sq;   // sg cq, sg sq
+    const f2 hc = {0.5f * cq.hi, 0.5f * cq.lo}, hs = {0.5f * sq.hi, 0.5f * sq.lo};
+    const f2 hcs = {0.5f * cs.hi, 0.5f * cs.lo}, hss = {0.5f * ss.hi, 0.5f * ss.lo};
+    const f2 pl = ff_add(g[0], g[3]), mi = ff_sub(g[0], g[3]);
+    out[0] = g[0];
+    out[1] = ff_sub(ff_mul(cq, g[1]), ff_mul(ss, g[2]));
+    out[2] = ff_add(ff_mul(sq, g[1]), ff_mul(cs, g[2]));
+    out[3] = g[1];
+    out[4] = ff_sub(ff_mul(hc, pl), ff_mul(hss, g[4]));
+    out[5] = ff_add(ff_mul(hs, pl), ff_mul(hcs, g[4]));
+    out[6] = g[2];
+    out[7] = ff_sub(ff_mul(hc, g[4]), ff_mul(hss, mi));
+    out[8] = ff_add(ff_mul(hs, g[4]), ff_mul(hcs, mi));
 }
 
 // KF: the kinds the launch may meet -- 0 any, 1 no flow kind, 2 flow kinds
@@ -1534,21 +1580,20 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
                     ff_rot(cy, sy, cqy, sqy, cy2, sy2);
                 }
             }
+            // the Fourier basis at row i (x) and column i (y)
             const f2 one = {1.0f, 0.0f};
-            const f2 gx[3] = {one, cx, sx}, gx2[3] = {one, cx2, sx2};
-            const f2 gy[3] = {one, cy, sy}, gy2[3] = {one, cy2, sy2};
+            const f2 px[5] = {one, cx, sx, ff_mul(ff_sub(cx, sx), ff_add(cx, sx)),
+                              ff_mul(f2{2.0f * sx.hi, 2.0f * sx.lo}, cx)};
+            const f2 py[5] = {one, cy, sy, ff_mul(ff_sub(cy, sy), ff_add(cy, sy)),
+                              ff_mul(f2{2.0f * sy.hi, 2.0f * sy.lo}, cy)};
             const f2 wf = ff_ld(S.wr[i]);
             const f2 wc = (i & 1) == 0 ? ff_ld(S.wrc[i >> 1]) : f2{0.0f, 0.0f};
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    S.X[rho][i][3 * a + c] =
-                        ff_st(a == 0 ? gx2[c] : (c == 0 ? gx[a] : ff_mul(gx[a], gx2[c])));
-                    const f2 y = a == 0 ? gy2[c] : (c == 0 ? gy[a] : ff_mul(gy[a], gy2[c]));
-                    S.u.c.Yf[rho][i][3 * a + c] = ff_st(ff_mul(wf, y));
-                    if ((i & 1) == 0) S.u.c.Yc[rho][i >> 1][3 * a + c] = ff_st(ff_mul(wc, y));
-                }
+            for (int u = 0; u < 5; ++u) {
+                S.X[rho][i][u] = ff_st(px[u]);
+                S.u.c.Yf[rho][i][u] = ff_st(ff_mul(wf, py[u]));
+                if ((i & 1) == 0) S.u.c.Yc[rho][i >> 1][u] = ff_st(ff_mul(wc, py[u]));
+            }
             const f2 tA = ff_ld(S.lat[0]), tB = ff_ld(S.lat[1]), nmu = ff_neg(ff_ld(S.lat[2]));
             if (flow) {
                 // e(k + q/2) and e(k - q/2), tq the rotation by q/2
@@ -1576,9 +1621,9 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
             }
         }
         __syncthreads();
-        f2 rf[9], rc[9];
+        f2 rf[5], rc[5];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) { rf[k] = {0.0f, 0.0f}; rc[k] = {0.0f, 0.0f}; }
+        for (int k = 0; k < 5; ++k) { rf[k] = {0.0f, 0.0f}; rc[k] = {0.0f, 0.0f}; }
         if (live) {
             const f2 W = ff_ld(S.H[rho][1]);
             // one node (i, j): the kernel F once, then every row sum
@@ -1591,10 +1636,10 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 else if (KF != 2 && kind != OVERLAP)
                     F = bubble_F2T_ff(x1, x2, S.tab);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yf[rho][j][k]), rf[k]);
+                for (int k = 0; k < 5; ++k) ff_acc(F, ff_ld(S.u.c.Yf[rho][j][k]), rf[k]);
                 if (even) {
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) ff_acc(F, ff_ld(S.u.c.Yc[rho][j >> 1][k]), rc[k]);
+                    for (int k = 0; k < 5; ++k) ff_acc(F, ff_ld(S.u.c.Yc[rho][j >> 1][k]), rc[k]);
                 }
             };
             // two columns per trip (even, then odd) keeps the coarse-rule
@@ -1614,30 +1659,64 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
             // the row's own weight in float-float
             const f2 wr = ff_ld(S.wr[i]);
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
+            for (int k = 0; k < 5; ++k)
                 S.u.r.Rf[rho][i][k] = ff_st(ff_mul(wr, ff_fast(rf[k].hi, rf[k].lo)));
             if ((i & 1) == 0) {
                 const f2 wrc = ff_ld(S.wrc[i >> 1]);
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
+                for (int k = 0; k < 5; ++k)
                     S.u.r.Rc[rho][i >> 1][k] = ff_st(ff_mul(wrc, ff_fast(rc[k].hi, rc[k].lo)));
             }
         }
         __syncthreads();
         if (live) {
-            // moments M[ac][bd]: the 81 (ac, bd) cells dealt over the region's
-            // NF threads, float-float dot products over the rows
-            for (int u = i; u < 81; u += NF) {
-                const int ac = u / 9, bd = u - 9 * (u / 9);
-                f2 mf = {0.0f, 0.0f}, mc = {0.0f, 0.0f};
+            // Fourier moments G[u][v]: the 25 cells dealt over the region's NF
+            // threads, float-float dot products over the rows
+            for (int c = i; c < 25; c += NF) {
+                const int u = c / 5, v = c - 5 * (c / 5);
+                f2 gf = {0.0f, 0.0f}, gc = {0.0f, 0.0f};
 #pragma unroll 5
                 for (int r = 0; r < NF; ++r)
-                    ff_acc(ff_ld(S.X[rho][r][ac]), ff_ld(S.u.r.Rf[rho][r][bd]), mf);
+                    ff_acc(ff_ld(S.X[rho][r][u]), ff_ld(S.u.r.Rf[rho][r][v]), gf);
 #pragma unroll
                 for (int r = 0; r <= N; ++r)
-                    ff_acc(ff_ld(S.X[rho][2 * r][ac]), ff_ld(S.u.r.Rc[rho][r][bd]), mc);
-                S.Mf[rho][ac][bd] = ff_st(ff_fast(mf.hi, mf.lo));
-                S.Mc[rho][ac][bd] = ff_st(ff_fast(mc.hi, mc.lo));
+                    ff_acc(ff_ld(S.X[rho][2 * r][u]), ff_ld(S.u.r.Rc[rho][r][v]), gc);
+                S.G[rho][0][u][v] = ff_st(ff_fast(gf.hi, gf.lo));
+                S.G[rho][1][u][v] = ff_st(ff_fast(gc.hi, gc.lo));
+            }
+        }
+        __syncthreads();
+        // the rotation of k' and its orientation: (cos q, sin q) per direction
+        // for ph / pp (pp: k' = q - k), none for the flow kinds (both form
+        // factors at k)
+        const bool flowk = live && (KF == 2 || (KF == 0 && is_flow(kind)));
+        const bool flip = live && !flowk && kind == PP;
+        const f2 one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};
+        if (live) {
+            // x: each column v of G (per rule) to the nine X_ac
+            for (int c = i; c < 10; c += NF) {
+                const int rule = c / 5, v = c - 5 * (c / 5);
+                f2 g[5], o[9];
+#pragma unroll
+                for (int u = 0; u < 5; ++u) g[u] = ff_ld(S.G[rho][rule][u][v]);
+                ff_fourier_to_products(g, flowk ? one : ff_ld(S.Q[rho][0]),
+                                       flowk ? zero : ff_ld(S.Q[rho][1]), flip, o);
+#pragma unroll
+                for (int ac = 0; ac < 9; ++ac) S.u.T[rho][rule][ac][v] = ff_st(o[ac]);
+            }
+        }
+        __syncthreads();
+        if (live) {
+            // y: each row ac (per rule) to the nine Y_bd
+            for (int c = i; c < 18; c += NF) {
+                const int rule = c / 9, ac = c - 9 * (c / 9);
+                f2 g[5], o[9];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) g[v] = ff_ld(S.u.T[rho][rule][ac][v]);
+                ff_fourier_to_products(g, flowk ? one : ff_ld(S.Q[rho][2]),
+                                       flowk ? zero : ff_ld(S.Q[rho][3]), flip, o);
+#pragma unroll
+                for (int bd = 0; bd < 9; ++bd) S.M[rho][rule][ac][bd] = ff_st(o[bd]);
             }
         }
         __syncthreads();
@@ -1653,8 +1732,8 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
                             const f2 c = ff_ld(c_ffpair[l][k1][m][k2]);
                             const int ac = 3 * c_ffa[l][k1] + c_ffa[m][k2];
                             const int bd = 3 * c_ffb[l][k1] + c_ffb[m][k2];
-                            ff_acc(c, ff_ld(S.Mf[rho][ac][bd]), q2);
-                            ff_acc(c, ff_ld(S.Mc[rho][ac][bd]), q1);
+                            ff_acc(c, ff_ld(S.M[rho][0][ac][bd]), q2);
+                            ff_acc(c, ff_ld(S.M[rho][1][ac][bd]), q1);
                         }
                 }
                 q2 = ff_fast(q2.hi, q2.lo);

@@ -22,6 +22,9 @@ LIB_PATH = os.path.join(_HERE, "libpaid.so")
 PH, PP, MONOMIAL, OVERLAP, FLOW_PH, FLOW_PP = 0, 1, 2, 3, 4, 5
 FF_SHELL1, FF_SHELL12 = 5, 9
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_POOL, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+# PAID_MLP_LAYERS of include/paid.h: one forward pass launches a weight cast
+# and one GEMM per layer
+MLP_LAYERS = 5
 CONVERGED, BUDGET, NONFINITE, ROUNDCAP, POOL = 0, 1, 2, 3, 4
 GROUP_NONE, GROUP_PER_PAIR, GROUP_GLOBAL = 0, 1, 2       # options.group_mode
 
@@ -656,6 +659,8 @@ class Proposal:
         self.loss_buf = torch.zeros(1, dtype=torch.float32, device=self.device)
         self.step_count = 0
         self._ws = None
+        # kernels this object has launched for inference (features + forward)
+        self.launches = 0
 
     def _workspace(self, M):
         torch = _torch()
@@ -679,6 +684,7 @@ class Proposal:
                                         ctypes.c_void_p(s.cuda_stream))
         if rc != OK:
             raise PaidError(rc, "paid_mlp_forward")
+        self.launches += 1 + MLP_LAYERS
         return out
 
     def grad(self, x, target, stream=None):
@@ -757,6 +763,7 @@ class Proposal:
         """Level maps for ctx's units of these batches (group mode: one row per
         (kind, q) group; else one per integral), FP32 [units, 256]."""
         torch = _torch()
+        self.launches += sum(1 for b in batches if int(b["q"].shape[0]) > 0)
         if ctx.options.group_mode:
             x = torch.cat([ctx.group_features(b["kind"], b["q"], b["T"], stream) for b in batches])
         else:

@@ -100,3 +100,34 @@ def test_group_global_check(bench):
     st = gs.copy()
     st[P] = 1
     assert bench.group_global_check(w, gv, st, 12, rows_per_batch=4)["parity_failures"] == 1
+
+
+class _DoneProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_keeps_only_the_timed_window(bench, tmp_path):
+    """Only samples stamped inside the marked window count, and a throttle
+    reason seen there is reported; samples before and after are dropped."""
+    import datetime
+    cs = bench.ClockSampler(0)
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+    rows = []
+    for k, (mhz, hw) in enumerate([(1200, "Active"), (2070, "Not Active"), (2070, "Not Active"),
+                                   (1980, "Active"), (900, "Not Active")]):
+        ts = (base + datetime.timedelta(milliseconds=100 * k)).strftime("%Y/%m/%d %H:%M:%S.%f")
+        rows.append(f"{ts[:-3]}, 0, {mhz}, 2070, 500.0, 0x0, Not Active, {hw}, Not Active, "
+                    "Not Active")
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    cs.path, cs.proc = str(path), _DoneProc()
+    cs.window = [(base + datetime.timedelta(milliseconds=100)).timestamp(),
+                 (base + datetime.timedelta(milliseconds=300)).timestamp()]
+    out = cs.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070 and out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["hw_thermal_slowdown"]
