@@ -62,12 +62,12 @@ GROUP_FP64_FLOPS_PER_REGION[12] = 2 * 26843 + 4495 + 8089      # 66,270
 # FP32-pipe thread instructions (FADD + FMUL + FFMA, one issue slot each) and
 # FP32 flops (FFMA counted as 2) per region of the float-float form of the
 # shared-partition kernel (k_eval_group_ff<N, 1>, ph / pp, 81 pairs, moments in
-# the Fourier basis), from the ncu instruction counters of one launch over
-# 6,240 regions of the flow step at T = 0.05 divided by its regions
-# (profiles/k_eval_group_ff_flow_step_q4.md: FADD 150,617, FMUL 23,533, FFMA
-# 49,621 per region).
-GROUP_FP32_INSTR_PER_REGION = {12: 150617 + 23533 + 49621}              # 223,771
-GROUP_FP32_FLOPS_PER_REGION = {12: 150617 + 23533 + 2 * 49621}          # 273,392
+# the Fourier basis, Jacobian in float-float), from the ncu instruction
+# counters of one launch over 6,240 regions of the flow step at T = 0.05
+# divided by its regions (profiles/k_eval_group_ff_flow_step_q4.md: FADD
+# 151,184, FMUL 23,938, FFMA 50,107 per region).
+GROUP_FP32_INSTR_PER_REGION = {12: 151184 + 23938 + 50107}              # 225,229
+GROUP_FP32_FLOPS_PER_REGION = {12: 151184 + 23938 + 2 * 50107}          # 275,336
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
@@ -502,8 +502,7 @@ def run_paid(args):
             flush.fill_(1)
             if not seeded:
                 return c.integrate_multi(dbs, stream=stream)
-            return c.integrate_multi_seeded(dbs, PR.seed_maps(prop, c, dbs, margin), 0.0,
-                                            stream=stream)
+            return PR.integrate(prop, c, dbs, margin, stream=stream)
         return step
 
     step = make_step(ctx, learned)

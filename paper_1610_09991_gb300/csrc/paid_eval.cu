@@ -1421,9 +1421,9 @@ k_eval_group(Work w, Lattice lat, double* rule_q2, double* rule_d)
 // per-row and per-region quantity an unevaluated pair of FP32 numbers on the
 // FP32 pipe (64x the FP64 pipe on this GPU): the node abscissae (rotations of
 // the region centre), the reduced energies, the kernel F, the row sums, the
-// moments and the pair combinations.  FP64 remains for the two sincospi of the
-// exact dyadic centre, the conversions of the per-region inputs, and each
-// pair's Q_2N and Q_N - Q_2N times the Jacobian.
+// moments, the pair combinations and the Jacobian.  FP64 remains for the two
+// sincospi of the exact dyadic centre, the conversions of the per-region
+// inputs, and each pair value's final conversion to FP64.
 //
 // The moments are taken in the Fourier basis phi = (1, cos k, sin k, cos 2k,
 // sin 2k) of each direction instead of the nine products X_ac = g_a(k) g'_c(k')
@@ -1721,8 +1721,10 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
         }
         __syncthreads();
         if (live) {
-            const double scale =
-                ldexp(0.25, -2 * int(L)) * (kind == PH || kind == PP ? B->inv2T : 1.0);
+            // the Jacobian: 1/2T (ph, pp) in float-float times 4^-L / 4, an exact
+            // power of two applied to both words
+            const f2 jac = kind == PH || kind == PP ? ff_ld(S.H[rho][0]) : f2{1.0f, 0.0f};
+            const float p2 = __int_as_float((125 - 2 * int(L)) << 23);
             for (int p = i; p < P; p += NF) {
                 const int l = B->lm[2 * p], m = B->lm[2 * p + 1];
                 f2 q2 = {0.0f, 0.0f}, q1 = {0.0f, 0.0f};
@@ -1738,16 +1740,18 @@ k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
                 }
                 q2 = ff_fast(q2.hi, q2.lo);
                 q1 = ff_fast(q1.hi, q1.lo);
-                // FP64 from here: Q_2N and the embedded-rule difference
-                const double v2 = ff_to(q2) * scale;
-                const double dq = ff_to(ff_sub(q1, q2)) * scale;
+                // Q_2N and the embedded-rule difference Q_N - Q_2N; only the
+                // value's conversion to FP64 leaves the FP32 pipe
+                const f2 v = ff_mul(q2, jac), dq = ff_mul(ff_sub(q1, q2), jac);
+                const double v2 = double(__fmul_rn(v.hi, p2)) + double(__fmul_rn(v.lo, p2));
                 if (rule_q2) {
                     rule_q2[t * P + p] = v2;
-                    rule_d[t * P + p] = dq;
+                    rule_d[t * P + p] =
+                        double(__fmul_rn(dq.hi, p2)) + double(__fmul_rn(dq.lo, p2));
                 } else {
                     const size_t o = size_t(pos) * size_t(w.vstride) + size_t(p);
                     w.vval[cur][o] = v2;
-                    w.verr[cur][o] = float(fabs(dq));
+                    w.verr[cur][o] = fabsf(__fmul_rn(dq.hi, p2));
                 }
             }
         }

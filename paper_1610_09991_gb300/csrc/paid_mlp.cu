@@ -6,9 +6,11 @@
 // convergence.  (Not part of the paper: the proposal of the workload
 // specification.)
 //
-// Kernels: BF16 tensor-core GEMMs (mma.sync m16n8k16, FP32 accumulation)
-// with fused bias / GELU / BF16 cast epilogues, the MSE loss gradient, GELU
-// backward, bias gradients and AdamW on FP32 master weights.
+// Kernels: the forward pass of all five layers in one launch on the tcgen05
+// tensor cores (TMEM accumulators, fused bias / GELU / BF16 epilogues); for
+// training, BF16 GEMMs on mma.sync m16n8k16 for the backward products, the
+// MSE loss gradient, GELU backward, bias gradients and AdamW on FP32 master
+// weights.
 //
 // Parameter buffer (FP32 master weights), layer l = 0..4 with K_0 = 32,
 // K_l = 256 otherwise, N = 256:  W_l [K_l][N] row-major, then b_l [N].
@@ -46,11 +48,10 @@ __host__ __device__ inline int64_t param_count()
 // GEMM  C[M][N] = sum_k A(m, k) B(k, n), A(m, k) = A[m sam + k sak],
 // B(k, n) = B[k sbk + n sbn] (BF16), FP32 accumulation on the tensor cores.
 // Tiles 64 x 64 x 32, 4 warps of 32 x 32 (2 x 4 mma tiles of 16 x 8).
-// Epilogues:
+// Epilogues (the backward products of training):
 //   EPI_STORE : C = acc + bias (FP32)
 //   EPI_ATOMIC: C += acc (FP32 atomics; split reduction over k = blockIdx.z)
-//   EPI_GELU  : pre = acc + bias (FP32), act = gelu(pre) (BF16)
-enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_GELU = 2 };
+enum { EPI_STORE = 0, EPI_ATOMIC = 1 };
 constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
@@ -74,7 +75,7 @@ template <int EPI>
 __global__ void __launch_bounds__(128)
 k_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64_t sam, int64_t sak,
        const __nv_bfloat16* __restrict__ B, int64_t sbk, int64_t sbn, const float* __restrict__ bias,
-       float* __restrict__ C, int64_t ldc, __nv_bfloat16* __restrict__ act, int k_chunk)
+       float* __restrict__ C, int64_t ldc, int k_chunk)
 {
     __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];
@@ -136,9 +137,7 @@ k_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64_t sam, in
                 if (EPI == EPI_ATOMIC) {
                     atomicAdd(&C[int64_t(gm) * ldc + gn], v);
                 } else {
-                    const float y = v + (bias ? bias[gn] : 0.0f);
-                    C[int64_t(gm) * ldc + gn] = y;
-                    if (EPI == EPI_GELU) act[int64_t(gm) * ldc + gn] = __float2bfloat16(gelu(y));
+                    C[int64_t(gm) * ldc + gn] = v + (bias ? bias[gn] : 0.0f);
                 }
             }
 }
@@ -146,14 +145,14 @@ k_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64_t sam, in
 template <int EPI>
 cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64_t sak,
                  const __nv_bfloat16* B, int64_t sbk, int64_t sbn, const float* bias, float* C,
-                 int64_t ldc, __nv_bfloat16* act, int splits, cudaStream_t s)
+                 int64_t ldc, int splits, cudaStream_t s)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     int chunk = (K + splits - 1) / splits;
     chunk = (chunk + BK - 1) / BK * BK;
     const int z = (K + chunk - 1) / chunk;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, z);
-    k_gemm<EPI><<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, C, ldc, act, chunk);
+    k_gemm<EPI><<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, C, ldc, chunk);
     return cudaGetLastError();
 }
 
@@ -300,7 +299,212 @@ int64_t wofs(int l)   // offset of W_l in the BF16 weight arrays
     return o;
 }
 
-// forward of M rows: x [M][32] BF16 -> out [M][256] FP32 (the last layer's pre)
+// ---------------------------------------------------------------------------
+// Forward pass on the 5th-generation tensor cores (tcgen05): one CTA of 128
+// threads per 128 rows runs all five layers.  Per layer the CTA stages the
+// layer's BF16 weights W_l^T [256][K] and its input rows [128][K] in shared
+// memory, one thread issues K/16 tcgen05.mma (M = 128, N = 256, K = 16, BF16
+// in, FP32 out) into 256 TMEM columns, a commit arrives on an mbarrier, and
+// the four warps read their 32 TMEM lanes (= rows) back with tcgen05.ld for
+// the epilogue: + bias, GELU, BF16 into shared memory as the next layer's
+// input (or FP32 rows of the output after the last layer).
+//
+// Shared-memory operands use the canonical K-major layout without swizzling:
+// 8-row x 16-byte core matrices, core matrix (r/8, k/8) at ((r/8) (K/8) + k/8)
+// x 128 bytes, so the descriptor's K step between core matrices (leading byte
+// offset) is 128 B and its row-group step (stride byte offset) K/8 x 128 B.
+namespace tc {
+
+constexpr int kRows = 128;            // rows per CTA = MMA M = TMEM lanes
+constexpr uint32_t kCols = 256;       // TMEM columns: one FP32 accumulator per output
+// instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(kHid) >> 3) << 17) |
+                            ((uint32_t(kRows) >> 4) << 24);
+constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before the CTA gives up
+
+struct Smem {
+    unsigned char a[kRows * kHid * 2];   // input rows, canonical layout
+    unsigned char b[kHid * kHid * 2];    // W_l^T, canonical layout
+    unsigned long long bar;
+    uint32_t tmem;
+};
+constexpr size_t kSmemBytes = sizeof(Smem) + 1024;   // + alignment of the operands
+
+struct Args {
+    const float* params;
+    const __nv_bfloat16* wt;              // BF16 W_l^T [256][K_l], layers back to back
+    const __nv_bfloat16* x;               // [M][32]
+    int M;
+    float* out;                           // last layer's pre-activation [M][256]
+    float* pre[kLayers - 1];              // hidden pre-activations [M][256], or null
+    __nv_bfloat16* h[kLayers - 1];        // hidden activations [M][256], or null
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t canon(int row, int kg, int KG)
+{
+    return uint32_t(((row >> 3) * KG + kg) * 128 + (row & 7) * 16);
+}
+// shared-memory descriptor: start, leading byte offset (K), stride byte offset
+// (rows), bits 46-47 = 1 (tcgen05 descriptor version), no swizzle
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(tc::Args g)
+{
+    extern __shared__ unsigned char smem_raw[];
+    tc::Smem& S = *reinterpret_cast<tc::Smem*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * tc::kRows;
+    const uint32_t bar = tc::smem_u32(&S.bar);
+    const uint32_t sa = tc::smem_u32(S.a), sb = tc::smem_u32(S.b);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(tc::smem_u32(&S.tmem)), "r"(tc::kCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem;
+    const int row = warp * 32 + lane, grow = m0 + row;   // this thread's TMEM lane and row
+    bool ok = true;
+    uint32_t parity = 0;                                  // phase of the current layer's commit
+    int64_t wo = 0;                                       // offset of W_l^T in wt
+    for (int l = 0; l < kLayers && ok; ++l) {
+        const int K = layer_k(l), KG = K / 8;
+        // W_l^T rows n (K contiguous, 16-byte pieces) into the canonical layout
+        for (int c = tid; c < kHid * KG; c += 128) {
+            const int n = c / KG, kg = c - n * KG;
+            *reinterpret_cast<uint4*>(S.b + tc::canon(n, kg, KG)) =
+                __ldg(reinterpret_cast<const uint4*>(g.wt + wo + int64_t(n) * K + kg * 8));
+        }
+        if (l == 0) {
+            // the input rows (zero beyond M), element by element: x needs no alignment
+            for (int c = tid; c < tc::kRows * kIn; c += 128) {
+                const int r = c / kIn, k = c - r * kIn;
+                const __nv_bfloat16 v = m0 + r < g.M ? g.x[int64_t(m0 + r) * kIn + k]
+                                                     : __float2bfloat16(0.0f);
+                *reinterpret_cast<__nv_bfloat16*>(S.a + tc::canon(r, k >> 3, kIn / 8) +
+                                                  (k & 7) * 2) = v;
+            }
+        }
+        // generic-proxy writes of the operands, visible to the tensor core
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int kk = 0; kk < K / 16; ++kk) {
+                const uint64_t ad = tc::desc(sa + kk * 256, 128, KG * 128);
+                const uint64_t bd = tc::desc(sb + kk * 256, 128, KG * 128);
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(tc::kIdesc), "r"(kk) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar) : "memory");
+        }
+        parity = uint32_t(l & 1);
+        ok = tc::wait_bar(bar, parity);
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float* bias = g.params + layer_w_off(l) + int64_t(K) * kHid;
+        const bool last = l == kLayers - 1;
+        for (int c0 = 0; c0 < kHid; c0 += 16) {
+            uint32_t r[16];
+            tc::ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+            float y[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) y[j] = __uint_as_float(r[j]) + __ldg(bias + c0 + j);
+            if (last) {
+                if (grow < g.M) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(g.out + int64_t(grow) * kHid + c0 + j) =
+                            make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+                }
+            } else {
+                __align__(16) __nv_bfloat16 hb[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) hb[j] = __float2bfloat16(gelu(y[j]));
+                *reinterpret_cast<uint4*>(S.a + tc::canon(row, c0 >> 3, kHid / 8)) =
+                    *reinterpret_cast<const uint4*>(hb);
+                *reinterpret_cast<uint4*>(S.a + tc::canon(row, (c0 >> 3) + 1, kHid / 8)) =
+                    *reinterpret_cast<const uint4*>(hb + 8);
+                if (g.pre[l] && grow < g.M) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(g.pre[l] + int64_t(grow) * kHid + c0 + j) =
+                            make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+                    *reinterpret_cast<uint4*>(g.h[l] + int64_t(grow) * kHid + c0) =
+                        *reinterpret_cast<const uint4*>(hb);
+                    *reinterpret_cast<uint4*>(g.h[l] + int64_t(grow) * kHid + c0 + 8) =
+                        *reinterpret_cast<const uint4*>(hb + 8);
+                }
+            }
+        }
+        // every TMEM read done before the next layer's MMAs overwrite the columns
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        wo += int64_t(K) * kHid;
+    }
+    if (!ok) {
+        // an MMA that never signalled: wait once more (bounded) so that nothing
+        // is in flight when the columns are freed, and mark the rows as failed
+        tc::wait_bar(bar, parity);
+        if (grow < g.M)
+            for (int c = 0; c < kHid; ++c) g.out[int64_t(grow) * kHid + c] = __int_as_float(0x7fc00000);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"(tc::kCols) : "memory");
+    }
+}
+
+// forward of M rows: x [M][32] BF16 -> out [M][256] FP32 (the last layer's
+// pre-activation); without out (training) the result goes to w.pre[4] and the
+// hidden layers' pre-activations and activations are kept for the backward
 cudaError_t forward(const float* params, const __nv_bfloat16* x, int64_t M, float* out,
                     MlpWork& w, cudaStream_t s)
 {
@@ -308,21 +512,21 @@ cudaError_t forward(const float* params, const __nv_bfloat16* x, int64_t M, floa
     const int64_t nw = param_count() - int64_t(kLayers) * kHid;
     k_cast_weights<<<int((nw + 255) / 256), 256, 0, s>>>(params, w.w, w.wt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const __nv_bfloat16* in = x;
-    for (int l = 0; l < kLayers; ++l) {
-        const int K = layer_k(l);
-        const float* b = params + layer_w_off(l) + int64_t(K) * kHid;
-        // B(k, n) = W_l[k][n] = wt[n][k]: sbk = 1, sbn = K
-        if (l < kLayers - 1)
-            e = gemm<EPI_GELU>(int(M), kHid, K, in, K, 1, w.wt + wofs(l), 1, K, b, w.pre[l], kHid,
-                               w.h[l], 1, s);
-        else
-            e = gemm<EPI_STORE>(int(M), kHid, K, in, K, 1, w.wt + wofs(l), 1, K, b,
-                                out ? out : w.pre[l], kHid, nullptr, 1, s);
-        if (e != cudaSuccess) return e;
-        in = w.h[l];
+    if ((e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(tc::kSmemBytes))) != cudaSuccess)
+        return e;
+    tc::Args g{};
+    g.params = params;
+    g.wt = w.wt;
+    g.x = x;
+    g.M = int(M);
+    g.out = out ? out : w.pre[kLayers - 1];
+    for (int l = 0; l < kLayers - 1; ++l) {
+        g.pre[l] = out ? nullptr : w.pre[l];
+        g.h[l] = out ? nullptr : w.h[l];
     }
-    return cudaSuccess;
+    k_mlp_forward_tc<<<int((M + tc::kRows - 1) / tc::kRows), 128, tc::kSmemBytes, s>>>(g);
+    return cudaGetLastError();
 }
 
 // MSE gradient of M rows into grad (zeroed first) and loss (zeroed first).
@@ -347,14 +551,14 @@ cudaError_t grad_rows(const float* params, const __nv_bfloat16* xb, const float*
         float* gb = gW + int64_t(K) * kHid;
         // dW[k][n] = sum_m in[m][k] d[m][n]:  A(k, m) = in[m K + k], B(m, n) = d[m 256 + n]
         if ((e = gemm<EPI_ATOMIC>(K, kHid, int(M), in, 1, K, d, kHid, 1, nullptr, gW, kHid,
-                                  nullptr, splits, s)) != cudaSuccess)
+                                  splits, s)) != cudaSuccess)
             return e;
         dim3 gbg((kHid + 127) / 128, int((M + 255) / 256));
         k_bias_grad<<<gbg, 128, 0, s>>>(d, int(M), kHid, gb);
         if (l == 0) break;
         // dh[m][k] = sum_n d[m][n] W_l[k][n]:  B(n, k) = W_l[k][n] = w[k 256 + n]
         if ((e = gemm<EPI_STORE>(int(M), K, kHid, d, kHid, 1, w.w + wofs(l), 1, kHid, nullptr,
-                                 w.dh, K, nullptr, 1, s)) != cudaSuccess)
+                                 w.dh, K, 1, s)) != cudaSuccess)
             return e;
         k_gelu_back<<<int((M * K + tb - 1) / tb), tb, 0, s>>>(w.dh, w.pre[l - 1], M * K, w.da);
         // the next step reads da while this one's d may alias it: swap buffers

@@ -583,9 +583,8 @@ class Context:
         elif callable(margin):
             # a margin per batch temperature (None: the uniform start)
             from . import proposal as PR
-            maps = PR.seed_maps(proposal, self, dbs, margin)
-            outs = self.integrate_multi_seeded(dbs, maps, 0.0, pool_capacity=pool_capacity,
-                                               stream=stream)
+            outs = PR.integrate(proposal, self, dbs, margin, stream=stream,
+                                pool_capacity=pool_capacity)
         else:
             maps = proposal.predict(self, dbs, stream)
             outs = self.integrate_multi_seeded(dbs, maps, margin, pool_capacity=pool_capacity,

@@ -118,6 +118,17 @@ def seed_maps(prop, ctx, batches, policy):
     return maps
 
 
+def integrate(prop, ctx, batches, policy, stream=None, pool_capacity=None):
+    """One call under a margin policy: the seeded start when the policy gives
+    a margin for some batch; the library's uniform start (streaming admission,
+    no inference) when it gives None for every batch, the form the policy was
+    calibrated on."""
+    if all(policy(float(b["T"])) is None for b in batches):
+        return ctx.integrate_multi(batches, pool_capacity=pool_capacity, stream=stream)
+    return ctx.integrate_multi_seeded(batches, seed_maps(prop, ctx, batches, policy), 0.0,
+                                      pool_capacity=pool_capacity, stream=stream)
+
+
 def calibrate_margin(prop, ctx, batches, margins=MARGINS):
     """Region evaluations and rounds of the seeded run at each margin (None:
     the uniform start) on these batches: {margin: (region evaluations, rounds)}."""

@@ -68,6 +68,26 @@ def test_forward_and_gradient_match_fp64_reference(paid, torch):
     assert rel < 0.05 and cos > 0.998, (rel, cos)
 
 
+@pytest.mark.parametrize("M", [1, 128, 1153])
+def test_forward_row_tiles(paid, torch, M):
+    """The forward pass runs 128 rows per CTA on the tcgen05 tensor cores: a
+    single row, one full tile and a ragged last tile against the reference."""
+    prop = paid.Proposal(seed=5)
+    rng = np.random.default_rng(M)
+    x = torch.as_tensor(rng.normal(size=(M, 32)), dtype=torch.bfloat16, device="cuda")
+    y = prop.forward(x)
+    torch.cuda.synchronize()
+    p64 = prop.state().astype(np.float64)
+    o = 0
+    for k, n in omlp.layer_shapes():
+        p64[o:o + k * n] = _bf16_round(p64[o:o + k * n])
+        o += k * n + n
+    yr, _ = omlp.forward(p64, x.float().double().cpu().numpy())
+    yg = y.double().cpu().numpy()
+    assert np.isfinite(yg).all()
+    assert np.abs(yg - yr).max() <= 0.05 * np.abs(yr).mean() + 0.02 * np.abs(yr).max()
+
+
 def test_training_reduces_loss(paid, torch):
     prop = paid.Proposal(seed=1)
     rng = np.random.default_rng(2)
