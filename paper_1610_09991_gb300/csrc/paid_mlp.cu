@@ -157,20 +157,26 @@ cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64
 }
 
 // ---------------------------------------------------------------------------
-// FP32 master weights -> BF16 copies W [K][N] and its transpose [N][K].
+// FP32 master weights -> BF16 copies W [K][N], its transpose [N][K], and the
+// transpose in the byte order of the forward kernel's shared-memory operand
+// (canonical K-major layout of 8-row x 16-byte core matrices: element (n, k)
+// of layer l at byte ((n/8) (K/8) + k/8) 128 + (n%8) 16 + (k%8) 2 of the
+// layer's block), so that one bulk copy stages a layer.
 __global__ void k_cast_weights(const float* __restrict__ p, __nv_bfloat16* __restrict__ w,
-                               __nv_bfloat16* __restrict__ wt)
+                               __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wc)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     int64_t o = 0, ob = 0;
     for (int l = 0; l < kLayers; ++l) {
-        const int64_t kn = int64_t(layer_k(l)) * kHid;
+        const int K = layer_k(l);
+        const int64_t kn = int64_t(K) * kHid;
         if (i >= ob && i < ob + kn) {
             const int64_t e = i - ob;
             const int k = int(e / kHid), n = int(e % kHid);
             const __nv_bfloat16 v = __float2bfloat16(p[o + e]);
             w[ob + e] = v;
-            wt[ob + int64_t(n) * layer_k(l) + k] = v;
+            wt[ob + int64_t(n) * K + k] = v;
+            wc[ob + (((n >> 3) * (K >> 3) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7))] = v;
             return;
         }
         o += kn + kHid;
@@ -261,7 +267,7 @@ __global__ void k_init(float* __restrict__ p, uint64_t seed)
 }
 
 struct MlpWork {
-    __nv_bfloat16 *w, *wt;                 // BF16 weights and transposes
+    __nv_bfloat16 *w, *wt, *wc;            // BF16 weights, transposes, forward-operand order
     float* pre[kLayers];                    // pre-activations (FP32) [M][256]
     __nv_bfloat16* h[kLayers];              // activations (BF16) [M][256]; h[4] unused
     __nv_bfloat16 *dy, *da;                 // BF16 gradients [M][256]
@@ -280,6 +286,7 @@ size_t mlp_work_bytes(int64_t M, MlpWork* w, char* base)
     char* p;
     p = take(sizeof(__nv_bfloat16) * nw); if (w) w->w = (__nv_bfloat16*)p;
     p = take(sizeof(__nv_bfloat16) * nw); if (w) w->wt = (__nv_bfloat16*)p;
+    p = take(sizeof(__nv_bfloat16) * nw); if (w) w->wc = (__nv_bfloat16*)p;
     for (int l = 0; l < kLayers; ++l) {
         p = take(sizeof(float) * M * kHid); if (w) w->pre[l] = (float*)p;
         p = take(sizeof(__nv_bfloat16) * M * kHid); if (w) w->h[l] = (__nv_bfloat16*)p;
@@ -300,14 +307,17 @@ int64_t wofs(int l)   // offset of W_l in the BF16 weight arrays
 }
 
 // ---------------------------------------------------------------------------
-// Forward pass on the 5th-generation tensor cores (tcgen05): one CTA of 128
-// threads per 128 rows runs all five layers.  Per layer the CTA stages the
-// layer's BF16 weights W_l^T [256][K] and its input rows [128][K] in shared
-// memory, one thread issues K/16 tcgen05.mma (M = 128, N = 256, K = 16, BF16
-// in, FP32 out) into 256 TMEM columns, a commit arrives on an mbarrier, and
-// the four warps read their 32 TMEM lanes (= rows) back with tcgen05.ld for
-// the epilogue: + bias, GELU, BF16 into shared memory as the next layer's
-// input (or FP32 rows of the output after the last layer).
+// Forward pass on the 5th-generation tensor cores (tcgen05): one CTA of 256
+// threads per 128 rows runs all five layers.  Per layer one bulk copy
+// (cp.async.bulk, completion on an mbarrier) stages the layer's BF16 weights
+// W_l^T [256][K], already in the operand's byte order, in shared memory; one
+// thread issues K/16 tcgen05.mma (M = 128, N = 256, K = 16, BF16 in, FP32
+// out) into 256 TMEM columns and commits them to a second mbarrier; the next
+// layer's weight copy then starts at once and overlaps the epilogue, in which
+// the eight warps read the accumulators back with tcgen05.ld (warp w: TMEM
+// lanes = rows 32 (w mod 4) ..., columns 128 (w / 4) ...): + bias, GELU, BF16
+// into shared memory as the next layer's input, or FP32 rows of the output
+// after the last layer.
 //
 // Shared-memory operands use the canonical K-major layout without swizzling:
 // 8-row x 16-byte core matrices, core matrix (r/8, k/8) at ((r/8) (K/8) + k/8)
@@ -316,6 +326,7 @@ int64_t wofs(int l)   // offset of W_l in the BF16 weight arrays
 namespace tc {
 
 constexpr int kRows = 128;            // rows per CTA = MMA M = TMEM lanes
+constexpr int kThreads = 256;
 constexpr uint32_t kCols = 256;       // TMEM columns: one FP32 accumulator per output
 // instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
@@ -327,14 +338,14 @@ constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before the CTA gives up
 struct Smem {
     unsigned char a[kRows * kHid * 2];   // input rows, canonical layout
     unsigned char b[kHid * kHid * 2];    // W_l^T, canonical layout
-    unsigned long long bar;
+    unsigned long long bar_mma, bar_w;
     uint32_t tmem;
 };
 constexpr size_t kSmemBytes = sizeof(Smem) + 1024;   // + alignment of the operands
 
 struct Args {
     const float* params;
-    const __nv_bfloat16* wt;              // BF16 W_l^T [256][K_l], layers back to back
+    const __nv_bfloat16* wc;              // BF16 W_l^T in operand order, layers back to back
     const __nv_bfloat16* x;               // [M][32]
     int M;
     float* out;                           // last layer's pre-activation [M][256]
@@ -369,6 +380,15 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity)
     }
     return false;
 }
+// layer l's weights (bytes, 16-byte aligned at both ends) into b, completing on bar
+__device__ __forceinline__ void copy_weights(uint32_t sb, const __nv_bfloat16* src, uint32_t bytes,
+                                             uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(sb), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
 __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -382,17 +402,19 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r)
 
 }  // namespace tc
 
-__global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(tc::Args g)
+__global__ void __launch_bounds__(tc::kThreads, 1) k_mlp_forward_tc(tc::Args g)
 {
     extern __shared__ unsigned char smem_raw[];
     tc::Smem& S = *reinterpret_cast<tc::Smem*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
     const int m0 = blockIdx.x * tc::kRows;
-    const uint32_t bar = tc::smem_u32(&S.bar);
+    const uint32_t bar_mma = tc::smem_u32(&S.bar_mma), bar_w = tc::smem_u32(&S.bar_w);
     const uint32_t sa = tc::smem_u32(S.a), sb = tc::smem_u32(S.b);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_mma) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_w) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -404,53 +426,57 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(tc::Args g)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = S.tmem;
-    const int row = warp * 32 + lane, grow = m0 + row;   // this thread's TMEM lane and row
+    // layer 0's weights in flight while the input rows are staged
+    if (tid == 0) tc::copy_weights(sb, g.wc, uint32_t(kIn * kHid * 2), bar_w);
+    for (int c = tid; c < tc::kRows * kIn; c += tc::kThreads) {
+        const int r = c / kIn, k = c - r * kIn;
+        const __nv_bfloat16 v = m0 + r < g.M ? g.x[int64_t(m0 + r) * kIn + k]
+                                             : __float2bfloat16(0.0f);
+        *reinterpret_cast<__nv_bfloat16*>(S.a + tc::canon(r, k >> 3, kIn / 8) + (k & 7) * 2) = v;
+    }
+    const int row = quarter * 32 + lane, grow = m0 + row;   // this thread's TMEM lane and row
     bool ok = true;
-    uint32_t parity = 0;                                  // phase of the current layer's commit
-    int64_t wo = 0;                                       // offset of W_l^T in wt
+    uint32_t phase = 0;            // completions seen on each barrier (one per layer)
+    bool copy_pending = true;      // a weight copy issued and not yet waited for
+    int64_t wo = 0;                // offset of W_l^T in wc
     for (int l = 0; l < kLayers && ok; ++l) {
         const int K = layer_k(l), KG = K / 8;
-        // W_l^T rows n (K contiguous, 16-byte pieces) into the canonical layout
-        for (int c = tid; c < kHid * KG; c += 128) {
-            const int n = c / KG, kg = c - n * KG;
-            *reinterpret_cast<uint4*>(S.b + tc::canon(n, kg, KG)) =
-                __ldg(reinterpret_cast<const uint4*>(g.wt + wo + int64_t(n) * K + kg * 8));
-        }
-        if (l == 0) {
-            // the input rows (zero beyond M), element by element: x needs no alignment
-            for (int c = tid; c < tc::kRows * kIn; c += 128) {
-                const int r = c / kIn, k = c - r * kIn;
-                const __nv_bfloat16 v = m0 + r < g.M ? g.x[int64_t(m0 + r) * kIn + k]
-                                                     : __float2bfloat16(0.0f);
-                *reinterpret_cast<__nv_bfloat16*>(S.a + tc::canon(r, k >> 3, kIn / 8) +
-                                                  (k & 7) * 2) = v;
-            }
-        }
-        // generic-proxy writes of the operands, visible to the tensor core
+        // generic-proxy writes of the input rows, visible to the tensor core
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int kk = 0; kk < K / 16; ++kk) {
-                const uint64_t ad = tc::desc(sa + kk * 256, 128, KG * 128);
-                const uint64_t bd = tc::desc(sb + kk * 256, 128, KG * 128);
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(tc::kIdesc), "r"(kk) : "memory");
+            ok = tc::wait_bar(bar_w, phase & 1);       // this layer's weights
+            if (ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int kk = 0; kk < K / 16; ++kk) {
+                    const uint64_t ad = tc::desc(sa + kk * 256, 128, KG * 128);
+                    const uint64_t bd = tc::desc(sb + kk * 256, 128, KG * 128);
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(tc::kIdesc), "r"(kk)
+                                 : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(bar_mma) : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(bar) : "memory");
         }
-        parity = uint32_t(l & 1);
-        ok = tc::wait_bar(bar, parity);
         ok = __syncthreads_and(ok);
         if (!ok) break;
+        copy_pending = false;
+        ok = __syncthreads_and(tc::wait_bar(bar_mma, phase & 1));
+        if (!ok) break;
+        ++phase;
+        wo += int64_t(K) * kHid;
+        // the MMAs are done with b: the next layer's weights stream in during the epilogue
+        if (tid == 0 && l + 1 < kLayers)
+            tc::copy_weights(sb, g.wc + wo, uint32_t(kHid * kHid * 2), bar_w);
+        copy_pending = l + 1 < kLayers;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const float* bias = g.params + layer_w_off(l) + int64_t(K) * kHid;
         const bool last = l == kLayers - 1;
-        for (int c0 = 0; c0 < kHid; c0 += 16) {
+        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
             uint32_t r[16];
-            tc::ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+            tc::ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0), r);
             float y[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) y[j] = __uint_as_float(r[j]) + __ldg(bias + c0 + j);
@@ -483,15 +509,15 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(tc::Args g)
         }
         // every TMEM read done before the next layer's MMAs overwrite the columns
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        wo += int64_t(K) * kHid;
     }
     if (!ok) {
-        // an MMA that never signalled: wait once more (bounded) so that nothing
-        // is in flight when the columns are freed, and mark the rows as failed
-        tc::wait_bar(bar, parity);
+        // a copy or an MMA that never signalled: wait once more (bounded) so
+        // that nothing is in flight when the CTA exits, and mark its rows
+        if (copy_pending) tc::wait_bar(bar_w, phase & 1);
+        tc::wait_bar(bar_mma, phase & 1);
         if (grow < g.M)
-            for (int c = 0; c < kHid; ++c) g.out[int64_t(grow) * kHid + c] = __int_as_float(0x7fc00000);
+            for (int c = half * 128; c < half * 128 + 128; ++c)
+                g.out[int64_t(grow) * kHid + c] = __int_as_float(0x7fc00000);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -510,14 +536,14 @@ cudaError_t forward(const float* params, const __nv_bfloat16* x, int64_t M, floa
 {
     cudaError_t e;
     const int64_t nw = param_count() - int64_t(kLayers) * kHid;
-    k_cast_weights<<<int((nw + 255) / 256), 256, 0, s>>>(params, w.w, w.wt);
+    k_cast_weights<<<int((nw + 255) / 256), 256, 0, s>>>(params, w.w, w.wt, w.wc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(tc::kSmemBytes))) != cudaSuccess)
         return e;
     tc::Args g{};
     g.params = params;
-    g.wt = w.wt;
+    g.wc = w.wc;
     g.x = x;
     g.M = int(M);
     g.out = out ? out : w.pre[kLayers - 1];
@@ -525,7 +551,7 @@ cudaError_t forward(const float* params, const __nv_bfloat16* x, int64_t M, floa
         g.pre[l] = out ? nullptr : w.pre[l];
         g.h[l] = out ? nullptr : w.h[l];
     }
-    k_mlp_forward_tc<<<int((M + tc::kRows - 1) / tc::kRows), 128, tc::kSmemBytes, s>>>(g);
+    k_mlp_forward_tc<<<int((M + tc::kRows - 1) / tc::kRows), tc::kThreads, tc::kSmemBytes, s>>>(g);
     return cudaGetLastError();
 }
 
