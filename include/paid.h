@@ -356,8 +356,7 @@ int paid_tu_flow_rhs(paid_ctx* ctx, int nq, int nff, const double* VP, const dou
  *     pool returns PAID_ERR_POOL, with status PAID_POOL on the unfinished
  *     integrals, exactly as paid_integrate_batch does with a small workspace.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) for that device; make that first call before any
- *     stream capture begins.
+ *     (cudaGetSymbolAddress) for that device.
  *   - All calls on a device share the one array and each call leaves its
  *     contents behind.  Nothing in it has to start cleared (every part is
  *     written before it is read within a call), but two calls that overlap on

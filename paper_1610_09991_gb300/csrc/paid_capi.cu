@@ -833,7 +833,7 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
     if (int64_t(t.pool) > cap)
         return fail(ctx, PAID_ERR_OOM, "workspace too small for the seeded partition");
     if ((e = launch_seed(w, proposal, margin, 1, s)) != cudaSuccess) return cuda_fail(ctx, e, "seed");
-    ctx->stats.launches = 5;
+    ctx->stats.launches = 6;   // setup, state, seed (count), scan (blocks, top), seed (write)
     return run_loop(ctx, w, n, int64_t(t.eval), int64_t(t.pool), -1, s);
 }
 

@@ -1140,7 +1140,8 @@ __device__ __forceinline__ f2 bubble_F2T_ff(f2 x1, f2 x2, const float2* tab)
         const float tail = __fmul_rn(__fmul_rn(g, g),
                                      fmaf(g, fmaf(g, 1.0f / 181440.0f, 1.0f / 2520.0f), 1.0f / 60.0f));
         const f2 third = ff_mul(d2, f2{0.3333333432674408f, -9.934107758624577e-09f});
-        const f2 S = ff_add(f2{2.0f, 0.0f}, ff_fast(third.hi, __fadd_rn(third.lo, tail)));
+        const f2 S0 = ff_fast(2.0f, third.hi);    // 2 > d^2/3: exact
+        const f2 S = ff_fast(S0.hi, __fadd_rn(S0.lo, __fadd_rn(third.lo, tail)));
         if (near) {
             num = ff_mul(ff_mul(v1, v2), S);
             den = p;
@@ -1501,7 +1502,7 @@ __device__ __forceinline__ void ff_fourier_to_products(const f2 g[5], f2 cq, f2 
 // only -- so that a launch carries only the kernel F it needs (the row loop's
 // code stays within the instruction cache).
 template <int N, int KF>
-__global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1), 6)
+__global__ void __launch_bounds__(GroupShape<N>::R * (2 * N + 1), 7)
 k_eval_group_ff(Work w, Lattice lat, double* rule_q2, double* rule_d)
 {
     constexpr int NF = 2 * N + 1, R = GroupShape<N>::R;

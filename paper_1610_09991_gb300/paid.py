@@ -22,9 +22,9 @@ LIB_PATH = os.path.join(_HERE, "libpaid.so")
 PH, PP, MONOMIAL, OVERLAP, FLOW_PH, FLOW_PP = 0, 1, 2, 3, 4, 5
 FF_SHELL1, FF_SHELL12 = 5, 9
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_POOL, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
-# PAID_MLP_LAYERS of include/paid.h: one forward pass launches a weight cast
-# and one GEMM per layer
-MLP_LAYERS = 5
+# kernels one paid_mlp_forward call launches: the weight cast and the fused
+# five-layer forward pass
+MLP_FORWARD_LAUNCHES = 2
 CONVERGED, BUDGET, NONFINITE, ROUNDCAP, POOL = 0, 1, 2, 3, 4
 GROUP_NONE, GROUP_PER_PAIR, GROUP_GLOBAL = 0, 1, 2       # options.group_mode
 
@@ -589,13 +589,18 @@ class Context:
             maps = proposal.predict(self, dbs, stream)
             outs = self.integrate_multi_seeded(dbs, maps, margin, pool_capacity=pool_capacity,
                                                stream=stream)
-        res, d2h = [], 0
+        # results into pinned host buffers (torch caches them), one wait
+        hosts, d2h = [], 0
         for r in outs:
-            hv = [t.to("cpu", non_blocking=False).numpy() for t in
-                  (r.values, r.errors, r.regions, r.status)]
-            d2h += sum(x.nbytes for x in hv)
-            res.append(Result(*hv))
-        return res, h2d, d2h
+            hb = []
+            for t in (r.values, r.errors, r.regions, r.status):
+                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                h.copy_(t, non_blocking=True)
+                hb.append(h)
+                d2h += h.numel() * h.element_size()
+            hosts.append(hb)
+        stream.synchronize()
+        return [Result(*(h.numpy() for h in hb)) for hb in hosts], h2d, d2h
 
     def integrate_batch_static(self, kind, q, lm, T, rel_tol=1e-6, abs_tol=1e-10,
                                max_regions=100000, stream=None) -> Result:
@@ -683,7 +688,7 @@ class Proposal:
                                         ctypes.c_void_p(s.cuda_stream))
         if rc != OK:
             raise PaidError(rc, "paid_mlp_forward")
-        self.launches += 1 + MLP_LAYERS
+        self.launches += MLP_FORWARD_LAUNCHES
         return out
 
     def grad(self, x, target, stream=None):
