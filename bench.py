@@ -68,6 +68,13 @@ GROUP_FP64_FLOPS_PER_REGION[12] = 2 * 26843 + 4495 + 8089      # 66,270
 # 151,184, FMUL 23,938, FFMA 50,107 per region).
 GROUP_FP32_INSTR_PER_REGION = {12: 151184 + 23938 + 50107}              # 225,229
 GROUP_FP32_FLOPS_PER_REGION = {12: 151184 + 23938 + 2 * 50107}          # 275,336
+# pipe utilisation of the same launch (ncu, % of peak over active cycles), and
+# the DRAM bytes of the kernel per region evaluated, from the launch list of
+# the default command's timed steps (profiles/launches_flow_step_learned.md:
+# dram__bytes_read.sum + dram__bytes_write.sum over its launches / regions);
+# None while the kernel has changed since the counters were taken
+GROUP_FP32_PIPES_NCU = None
+GROUP_FP32_DRAM_BYTES_PER_REGION = None
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
@@ -398,7 +405,7 @@ def path_options(path, rule_n):
     return o
 
 
-def roofline_fp32_group(n_regions, eval_s, rule_n, peaks):
+def roofline_fp32_group(n_regions, eval_s, rule_n, peaks, launches=0):
     """FP32-pipe roofline of the float-float group kernel: thread instructions
     on the FP32 pipe (FADD, FMUL, FFMA: one issue slot of the pipe each) per
     region from its ncu counters, over the summed event time, against the pipe's
@@ -410,11 +417,16 @@ def roofline_fp32_group(n_regions, eval_s, rule_n, peaks):
     achieved = n_regions * ipr / eval_s / 1e12
     peak = pk / 2.0
     f = GROUP_FP32_FLOPS_PER_REGION[rule_n]
+    bpr = GROUP_FP32_DRAM_BYTES_PER_REGION if rule_n == 12 else None
+    traffic = bpr * n_regions / launches if bpr and launches else None
     return {"bound": "alu", "kernel": "k_eval_group_ff<%d>" % rule_n, "achieved": achieved,
             "peak": peak, "unit": "T FP32-pipe thread instructions/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": traffic,
             "traffic_note": "compute-bound: ~20 B of eval list / key read and 81 x 12 B of pair "
-                            "vectors written per region for %d FP32-pipe instructions" % ipr,
+                            "vectors written per region for %d FP32-pipe instructions; traffic = "
+                            "DRAM bytes per region of the ncu launch list x regions per launch "
+                            "(the pair vectors' write-back partly lands after the kernel)" % ipr,
+            "pipes_ncu": GROUP_FP32_PIPES_NCU if rule_n == 12 else None,
             "peak_source": "measured FFMA micro-benchmark in this run (pipe_peaks.cu), "
                            "2 flops per FFMA instruction",
             "instructions_per_region": ipr,
@@ -584,7 +596,8 @@ def run_paid(args):
     eval_s = agg["eval_ms"] / 1e3
     roof = None
     if group and opts["eval_fp32"]:
-        roof = roofline_fp32_group(agg["region_evals"], eval_s, ctx.options.rule_n, peaks)
+        roof = roofline_fp32_group(agg["region_evals"], eval_s, ctx.options.rule_n, peaks,
+                                   agg["eval_launches"])
     elif group and eval_s > 0:
         flow = all(b.kind in (W.FLOW_PH, W.FLOW_PP) for b in w.batches)
         fpr = (GROUP_FLOW_FP64_FLOPS_PER_REGION if flow
