@@ -62,19 +62,23 @@ GROUP_FP64_FLOPS_PER_REGION[12] = 2 * 26843 + 4495 + 8089      # 66,270
 # FP32-pipe thread instructions (FADD + FMUL + FFMA, one issue slot each) and
 # FP32 flops (FFMA counted as 2) per region of the float-float form of the
 # shared-partition kernel (k_eval_group_ff<N, 1>, ph / pp, 81 pairs, moments in
-# the Fourier basis, Jacobian in float-float), from the ncu instruction
-# counters of one launch over 6,240 regions of the flow step at T = 0.05
-# divided by its regions (profiles/k_eval_group_ff_flow_step_q4.md: FADD
-# 151,184, FMUL 23,938, FFMA 50,107 per region).
-GROUP_FP32_INSTR_PER_REGION = {12: 151184 + 23938 + 50107}              # 225,229
-GROUP_FP32_FLOPS_PER_REGION = {12: 151184 + 23938 + 2 * 50107}          # 275,336
-# pipe utilisation of the same launch (ncu, % of peak over active cycles), and
-# the DRAM bytes of the kernel per region evaluated, from the launch list of
-# the default command's timed steps (profiles/launches_flow_step_learned.md:
-# dram__bytes_read.sum + dram__bytes_write.sum over its launches / regions);
-# None while the kernel has changed since the counters were taken
-GROUP_FP32_PIPES_NCU = None
-GROUP_FP32_DRAM_BYTES_PER_REGION = None
+# the Fourier basis, Jacobian in float-float, seven blocks per SM), from the
+# ncu instruction counters of one launch over 6,240 regions of the flow step
+# at T = 0.05 divided by its regions (profiles/k_eval_group_ff_flow_step_q4.md:
+# FADD 151,014, FMUL 23,938, FFMA 50,107 per region).
+GROUP_FP32_INSTR_PER_REGION = {12: 151014 + 23938 + 50107}              # 225,059
+GROUP_FP32_FLOPS_PER_REGION = {12: 151014 + 23938 + 2 * 50107}          # 275,166
+# pipe utilisation of the same launch (ncu, fraction of peak over active
+# cycles), and the DRAM bytes of the kernel per region evaluated, from the
+# launch list of the default command's timed steps
+# (profiles/launches_flow_step_learned.md: dram__bytes_read.sum +
+# dram__bytes_write.sum of its 6 launches, 29.0 + 783.0 MB, over their
+# 1,116,008 regions)
+GROUP_FP32_PIPES_NCU = {"fma": 0.492, "fp64": 0.280, "alu": 0.173, "lsu": 0.098,
+                        "xu_mufu": 0.005, "issue_slots": 0.657, "warps_active_per_sm": 22.0,
+                        "source": "ncu --set full, one launch of 6,240 regions of the "
+                                  "2,592-integral flow step (k_eval_group_ff_flow_step_q4.md)"}
+GROUP_FP32_DRAM_BYTES_PER_REGION = (29.0e6 + 783.0e6) / 1116008                  # 727.6
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
@@ -574,24 +578,31 @@ def run_paid(args):
     value = conv_all / elapsed
 
     # e2e: host numpy inputs -> pinned H2D -> (proposal) -> integrate -> D2H,
-    # wall clock over several steps
+    # wall clock over several steps, through a context with the library's
+    # default loop (the device loop: what a user's call runs) and the tuned
+    # options
     e2e = None
     if not args.no_e2e:
         hb = [dict(kind=b.kind, T=b.T, q=b.q, lm=b.lm, rel_tol=b.rel_tol, abs_tol=b.abs_tol,
                    max_regions=b.max_regions) for b in w.batches]
-        ctx.integrate_host(hb, proposal=prop, margin=margin)   # warm-up (pinned pools)
+        ce = P.Context(*w.lattice, ffset=ff, device=local, **dict(opts, **tuned))
+        ce.integrate_host(hb, proposal=prop, margin=margin)   # warm-up (graph, pinned pools)
         torch.cuda.synchronize()
         n_e2e = max(5, min(args.steps, 10))
         t0 = time.perf_counter()
         conv_e2e, h2d, d2h = 0, 0, 0
         for _ in range(n_e2e):
             flush.fill_(1)
-            res, h2d, d2h = ctx.integrate_host(hb, proposal=prop, margin=margin)
+            res, h2d, d2h = ce.integrate_host(hb, proposal=prop, margin=margin)
             conv_e2e += sum(int((r.status == 0).sum()) for r in res)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": conv_e2e * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": n_e2e}
+               "d2h_bytes_per_step": d2h, "steps": n_e2e,
+               "loop": "device loop (the library default), tuned options"}
+        ce.close()
+        del ce
+        torch.cuda.empty_cache()
 
     eval_s = agg["eval_ms"] / 1e3
     roof = None
