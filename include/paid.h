@@ -429,9 +429,12 @@ int paid_integrate_multi_seeded(paid_ctx* ctx, const paid_batch* batches, int nb
 #define PAID_MLP_OUT 256
 #define PAID_MLP_LAYERS 5
 
-/* Number of FP32 parameters (270,592). */
+/* Number of FP32 parameters (271,616). */
 int paid_mlp_param_count(int64_t* n);
-/* Workspace bytes for forward / gradient passes over M rows. */
+/* Workspace bytes for forward / gradient passes over M rows.  The workspace
+ * of paid_mlp_forward, paid_mlp_grad and paid_proposal_train must start on a
+ * 256-byte boundary (every torch / cudaMalloc allocation does); otherwise
+ * PAID_ERR_ARG. */
 int paid_mlp_workspace_size(int64_t M, size_t* bytes);
 /* Seeded initialisation on the device (uniform +-1/sqrt(K) weights, zero biases). */
 int paid_mlp_init(float* params, uint64_t seed, void* stream);
@@ -444,7 +447,9 @@ int paid_mlp_features(paid_ctx* ctx, int kind, int nq, const double* q, int npai
  * one-hots zero): the inputs of a group-mode proposal. */
 int paid_mlp_group_features(paid_ctx* ctx, int kind, int nq, const double* q, double T,
                             uint16_t* x, void* stream);
-/* Forward pass: x (BF16 [M][32]) -> out (FP32 [M][256]). */
+/* Forward pass: x (BF16 [M][32], any alignment) -> out (FP32 [M][256],
+ * 16-byte aligned, else PAID_ERR_ARG); one launch on the tensor cores for all
+ * five layers, 128 rows per CTA. */
 int paid_mlp_forward(const float* params, const uint16_t* x, int64_t M, float* out,
                      void* workspace, size_t ws_bytes, void* stream);
 /* Mean-squared-error gradient over M rows against target (FP32 [M][256]):

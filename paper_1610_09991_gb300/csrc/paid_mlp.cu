@@ -662,6 +662,8 @@ uint64_t splitmix64(uint64_t& z)
 
 constexpr char kMagic[8] = {'P', 'A', 'I', 'D', 'M', 'L', 'P', '1'};
 
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
 }  // namespace
 
 extern "C" {
@@ -693,6 +695,9 @@ int paid_mlp_forward(const float* params, const uint16_t* x, int64_t M, float* o
 {
     if (!params || (M > 0 && (!x || !out)) || M < 0) return PAID_ERR_ARG;
     if (M == 0) return PAID_OK;
+    // the forward kernel stores output rows as 16-byte vectors and stages
+    // weights with bulk copies from the workspace (16-byte aligned blocks)
+    if (!aligned(out, 16) || !aligned(workspace, 256)) return PAID_ERR_ARG;
     if (M > int64_t(0x7fffffff)) return PAID_ERR_ARG;
     if (!workspace || ws_bytes < mlp_work_bytes(M, nullptr, nullptr)) return PAID_ERR_OOM;
     MlpWork w;
@@ -706,6 +711,7 @@ int paid_mlp_grad(const float* params, const uint16_t* x, const float* target, i
 {
     if (!params || !x || !target || !grad || !loss || M <= 0) return PAID_ERR_ARG;
     if (M > int64_t(0x7fffffff)) return PAID_ERR_ARG;
+    if (!aligned(workspace, 256)) return PAID_ERR_ARG;
     if (!workspace || ws_bytes < mlp_work_bytes(M, nullptr, nullptr)) return PAID_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MlpWork w;
@@ -738,6 +744,7 @@ int paid_proposal_train(float* params, float* m, float* v, const uint16_t* x, co
         batch <= 0 || M > int64_t(0x7fffffff) || !(lr >= 0.0f) || !(weight_decay >= 0.0f))
         return PAID_ERR_ARG;
     batch = std::min(M, batch);
+    if (!aligned(workspace, 256)) return PAID_ERR_ARG;
     if (!workspace || ws_bytes < train_work_bytes(M, batch, nullptr, nullptr)) return PAID_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TrainWork t;

@@ -743,6 +743,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sums(Work w)
     // what a convergence test or a selection can resolve), then in FP64
     double v[3] = {0.0, 0.0, 0.0};
     float e[3] = {0.0f, 0.0f, 0.0f};
+    // unrolled so that several rows' loads are in flight per warp (the sums
+    // keep their order)
+#pragma unroll 4
     for (uint32_t j = j0 + wid; j < j1; j += kGroupWarps) {
         const size_t r = size_t(base + j) * S;
 #pragma unroll
@@ -932,6 +935,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_scores(Work w)
     uint32_t j0, j1;
     chunk_range(cnt, k, j0, j1);
     double ssum = 0.0, smax = 0.0;
+#pragma unroll 4
     for (uint32_t j = j0 + wid; j < j1; j += kGroupWarps) {
         const size_t r = size_t(base + j) * S;
         float sc = 0.0f;
@@ -1390,25 +1394,43 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_split(Work w)
 
 // Group mode: every kept region's pair vectors to its slot in the next pool
 // (one thread per (slot, pair) element: coalesced on both sides).
+static_assert(kGroupPairs <= 96, "k_copy_vectors: three columns per lane and row");
+
 __global__ void k_copy_vectors(Work w)
 {
+    // one warp per kept region: its source row once per warp, the row's
+    // values and errors in coalesced lane order
     const int cur = w.ls->cur, nxt = cur ^ 1;
-    const size_t S = size_t(w.vstride);
-    const size_t total = size_t(w.totals->pool) * S;
-    const size_t stride = size_t(gridDim.x) * blockDim.x;
-    for (size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-        const size_t p = idx / S, c = idx - p * S;
+    const int S = w.vstride;
+    const int64_t pool = int64_t(w.totals->pool);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < pool; p += nwarps) {
         const uint32_t src = w.vsrc[p];
         if (src == 0xffffffffu) continue;
-        w.vval[nxt][idx] = w.vval[cur][size_t(src) * S + c];
-        w.verr[nxt][idx] = w.verr[cur][size_t(src) * S + c];
+        const double* sv = w.vval[cur] + size_t(src) * S;
+        const float* se = w.verr[cur] + size_t(src) * S;
+        double* dv = w.vval[nxt] + size_t(p) * S;
+        float* de = w.verr[nxt] + size_t(p) * S;
+        double a[3];
+        float b[3];
+#pragma unroll
+        for (int c3 = 0; c3 < 3; ++c3) {
+            const int c = lane + 32 * c3;
+            if (c < S) { a[c3] = sv[c]; b[c3] = se[c]; }
+        }
+#pragma unroll
+        for (int c3 = 0; c3 < 3; ++c3) {
+            const int c = lane + 32 * c3;
+            if (c < S) { dv[c] = a[c3]; de[c] = b[c3]; }
+        }
     }
 }
 
 cudaError_t launch_copy_vectors(const Work& w, int64_t hint_pool, cudaStream_t s)
 {
     if (hint_pool <= 0 || w.vstride <= 0) return cudaSuccess;
-    const int64_t blocks = std::min<int64_t>((hint_pool * w.vstride + 255) / 256, 152 * 16);
+    const int64_t blocks = std::min<int64_t>((hint_pool * 32 + 255) / 256, 152 * 16);
     k_copy_vectors<<<int(blocks), 256, 0, s>>>(w);
     return cudaGetLastError();
 }

@@ -69,6 +69,19 @@ def test_host_side_calls_without_gpu(lib):
     bad.group_mode, bad.eval_fp32 = 3, 0   # modes are 0, 1, 2
     assert lib.paid_create(ctypes.byref(h), 1.0, -0.25, -1.0, 9, ctypes.byref(bad), 0) == paid.ERR_ARG
     assert lib.paid_integrate_multi(None, None, 0, None, 0, None) == paid.ERR_ARG
+    # the proposal's forward pass needs a 16-byte aligned output and a
+    # 256-byte aligned workspace (checked before anything is launched)
+    n = ctypes.c_int64()
+    assert lib.paid_mlp_param_count(ctypes.byref(n)) == paid.OK and n.value == 271616
+    P_, X_, WS = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 1 << 30
+    fwd = lib.paid_mlp_forward
+    fwd.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    assert fwd(P_, X_, 4, ctypes.c_void_p(0x30004), ctypes.c_void_p(0x40000), WS,
+               None) == paid.ERR_ARG
+    assert fwd(P_, X_, 4, ctypes.c_void_p(0x30000), ctypes.c_void_p(0x40010), WS,
+               None) == paid.ERR_ARG
+    assert fwd(P_, X_, 0, None, None, 0, None) == paid.OK
 
 
 def test_no_cpu_fallback_without_device():
