@@ -438,6 +438,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_mlp_forward_tc(tc::Args g)
     bool ok = true;
     uint32_t phase = 0;            // completions seen on each barrier (one per layer)
     bool copy_pending = true;      // a weight copy issued and not yet waited for
+    bool mma_pending = false;      // MMAs committed and not yet waited for
     int64_t wo = 0;                // offset of W_l^T in wc
     for (int l = 0; l < kLayers && ok; ++l) {
         const int K = layer_k(l), KG = K / 8;
@@ -463,8 +464,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_mlp_forward_tc(tc::Args g)
         ok = __syncthreads_and(ok);
         if (!ok) break;
         copy_pending = false;
+        mma_pending = true;
         ok = __syncthreads_and(tc::wait_bar(bar_mma, phase & 1));
         if (!ok) break;
+        mma_pending = false;
         ++phase;
         wo += int64_t(K) * kHid;
         // the MMAs are done with b: the next layer's weights stream in during the epilogue
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_mlp_forward_tc(tc::Args g)
         // a copy or an MMA that never signalled: wait once more (bounded) so
         // that nothing is in flight when the CTA exits, and mark its rows
         if (copy_pending) tc::wait_bar(bar_w, phase & 1);
-        tc::wait_bar(bar_mma, phase & 1);
+        if (mma_pending) tc::wait_bar(bar_mma, phase & 1);
         if (grow < g.M)
             for (int c = half * 128; c < half * 128 + 128; ++c)
                 g.out[int64_t(grow) * kHid + c] = __int_as_float(0x7fc00000);
