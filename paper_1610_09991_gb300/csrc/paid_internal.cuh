@@ -50,7 +50,7 @@ constexpr uint32_t kEscalate = 0xfeu;
 // stride of a region in the pool
 constexpr int kGroupPairs = 81;
 // chunks per group segment in the group reduce (blocks per group)
-constexpr int kGroupSplit = 8;
+constexpr int kGroupSplit = 4;
 
 enum Kind : int { PH = 0, PP = 1, MONOMIAL = 2, OVERLAP = 3, FLOW_PH = 4, FLOW_PP = 5 };
 __host__ __device__ inline bool is_flow(int kind) { return kind == FLOW_PH || kind == FLOW_PP; }
