@@ -72,13 +72,13 @@ GROUP_FP32_FLOPS_PER_REGION = {12: 151014 + 23938 + 2 * 50107}          # 275,16
 # cycles), and the DRAM bytes of the kernel per region evaluated, from the
 # launch list of the default command's timed steps
 # (profiles/launches_flow_step_learned.md: dram__bytes_read.sum +
-# dram__bytes_write.sum of its 6 launches, 29.6 + 781.5 MB, over their
-# 1,116,986 regions)
+# dram__bytes_write.sum of its 6 launches, 28.9 + 784.5 MB, over their
+# 1,115,272 regions)
 GROUP_FP32_PIPES_NCU = {"fma": 0.492, "fp64": 0.280, "alu": 0.173, "lsu": 0.098,
                         "xu_mufu": 0.005, "issue_slots": 0.657, "warps_active_per_sm": 22.0,
                         "source": "ncu --set full, one launch of 6,240 regions of the "
                                   "2,592-integral flow step (k_eval_group_ff_flow_step_q4.md)"}
-GROUP_FP32_DRAM_BYTES_PER_REGION = (29.6e6 + 781.5e6) / 1116986                  # 726.2
+GROUP_FP32_DRAM_BYTES_PER_REGION = (28.9e6 + 784.5e6) / 1115272                  # 729.3
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
