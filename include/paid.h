@@ -123,10 +123,12 @@ typedef struct {
     int eval_fp32;          /* 1: integrand on the FP32 pipe.  One partition per integral: FP32
                                integrand, FP64 sums, integrals whose FP32 rounding noise crowds
                                their tolerance re-evaluated in float-float.  group_mode: the
-                               kernel F, the rule's row sums and the moments in float-float
-                               (unevaluated pairs of FP32 numbers, about 44 significant bits
-                               after rounding), each region's pair values Q_2N, Q_N, their
-                               difference and all totals in FP64.  Default 0 (all FP64) */
+                               kernel F, the rule's row sums and moments (taken in the Fourier
+                               basis 1, cos k, sin k, cos 2k, sin 2k of each direction), each
+                               region's pair values Q_2N, Q_N and their difference in
+                               float-float (unevaluated pairs of FP32 numbers, about 44
+                               significant bits after rounding); Q_2N stored in FP64, the error
+                               estimate in FP32, all totals in FP64.  Default 0 (all FP64) */
     int max_rounds;         /* cap on refinement rounds of an integral, counted from the round
                                it entered the pool. Default 4096 */
     double cover;           /* the regions split in a round cover (E - cover * tol) of the error. Default 0.5 */
