@@ -314,7 +314,7 @@ int paid_get_options(paid_ctx* ctx, paid_options* out);
  * options.init_level (the uniform start) for this GPU by timing paid_integrate_multi on `sample` (a few batches the
  * caller chose as representative; their outputs are overwritten), stagewise:
  * rule_n in {4, 6} (group mode: {4, 6, 8, 10, 12}) at cover 1, then cover in
- * {0.5, 0.75, 0.9, 1.0}, then eval_blocks in {608, 1216, 4864} (group mode),
+ * {0.5, 0.75, 0.9, 1.0}, then eval_blocks in {608, 1216, 4864, 19456} (group mode),
  * then init_level in {2, 3} (every unit's first batch of regions: 16 or 64),
  * each with the choices made so far.  The fastest candidate that completes
  * becomes the context's setting.

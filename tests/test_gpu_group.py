@@ -236,7 +236,7 @@ def test_autotune_picks_a_candidate_and_caches_it(paid, torch, tmp_path):
     path = str(tmp_path / "tune.jsonl")
     ctx = paid.Context(*LAT, ffset=9, group_mode=1)
     o = ctx.autotune(dbs, path)
-    assert o.cover in (0.5, 0.75, 0.9, 1.0) and o.eval_blocks in (608, 1216, 4864)
+    assert o.cover in (0.5, 0.75, 0.9, 1.0) and o.eval_blocks in (608, 1216, 4864, 19456)
     assert o.rule_n in (4, 6, 8, 10, 12) and o.init_level in (2, 3)
     lines = open(path).read().splitlines()
     assert len(lines) == 1 and "group_mode=1" in lines[0] and '"init_level": ' in lines[0]
