@@ -72,13 +72,13 @@ GROUP_FP32_FLOPS_PER_REGION = {12: 151014 + 23938 + 2 * 50107}          # 275,16
 # cycles), and the DRAM bytes of the kernel per region evaluated, from the
 # launch list of the default command's timed steps
 # (profiles/launches_flow_step_learned.md: dram__bytes_read.sum +
-# dram__bytes_write.sum of its 6 launches, 28.9 + 784.5 MB, over their
-# 1,115,272 regions)
+# dram__bytes_write.sum of its 8 launches, 29.1 + 780.8 MB, over their
+# 1,120,076 regions)
 GROUP_FP32_PIPES_NCU = {"fma": 0.492, "fp64": 0.280, "alu": 0.173, "lsu": 0.098,
                         "xu_mufu": 0.005, "issue_slots": 0.657, "warps_active_per_sm": 22.0,
                         "source": "ncu --set full, one launch of 6,240 regions of the "
                                   "2,592-integral flow step (k_eval_group_ff_flow_step_q4.md)"}
-GROUP_FP32_DRAM_BYTES_PER_REGION = (28.9e6 + 784.5e6) / 1115272                  # 729.3
+GROUP_FP32_DRAM_BYTES_PER_REGION = (29.1e6 + 780.8e6) / 1120076                  # 723.1
 # the same for the Omega-regulated flow kinds (no exponential; same counters)
 GROUP_FLOW_FP64_FLOPS_PER_REGION = {4: 2 * 3822 + 527 + 2171, 6: 2 * 6810 + 1006 + 3963,
                                     8: 2 * 10678 + 1659 + 6347, 10: 2 * 15426 + 2486 + 9323,
@@ -483,16 +483,23 @@ def run_paid(args):
     peaks = fp64_peak(local)
     tune = None
     if not args.no_autotune:
-        # autotuner (outside the timed region): rule order, cover and (group
-        # mode) the evaluation grid, timed on every 6th q point of each batch
+        # autotuner (outside the timed region): rule order, cover, start level
+        # and (group mode) the evaluation grid; the shared-partition paths are
+        # tuned on the whole batch up to 10^5 integrals (a trial is one
+        # integration, milliseconds at N = 12, and the grid's best size depends
+        # on the number of regions), everything else on every 6th q point of
+        # each batch
         t0 = time.perf_counter()
-        sample = [dict(d, q=d["q"][::6].contiguous()) for d in dbs]
+        n_all = sum(int(d["q"].shape[0]) * int(d["lm"].shape[0]) for d in dbs)
+        whole = group and n_all <= 100000
+        sample = dbs if whole else [dict(d, q=d["q"][::6].contiguous()) for d in dbs]
         o = ctx.autotune(sample)
+        n_s = sum(int(d["q"].shape[0]) * int(d["lm"].shape[0]) for d in sample)
         tune = {"rule_n": o.rule_n, "cover": o.cover, "eval_blocks": o.eval_blocks,
                 "init_level": o.init_level,
                 "seconds": time.perf_counter() - t0,
-                "sample": "every 6th q point of each batch (%d integrals)"
-                          % sum(int(d["q"].shape[0]) * int(d["lm"].shape[0]) for d in sample)}
+                "sample": ("the whole batch (%d integrals)" % n_s) if whole else
+                          ("every 6th q point of each batch (%d integrals)" % n_s)}
         ctx.release_workspace()
     tuned = dict(rule_n=ctx.options.rule_n, cover=ctx.options.cover,
                  eval_blocks=ctx.options.eval_blocks, init_level=ctx.options.init_level)
