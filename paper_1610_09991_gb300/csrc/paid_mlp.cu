@@ -208,15 +208,16 @@ __global__ void k_gelu_back(const float* __restrict__ dh, const float* __restric
     if (i < n) da[i] = __float2bfloat16(dh[i] * gelu_grad(pre[i]));
 }
 
-// db[n] += sum_m d[m][n]
+// db[n] += sum_m d[m][n], one thread per column summing the rows in order
+// (no atomics: training is bitwise reproducible)
 __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ d, int M, int N, float* __restrict__ db)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int m0 = blockIdx.y * 256, m1 = min(M, m0 + 256);
     float s = 0.0f;
-    for (int m = m0; m < m1; ++m) s += __bfloat162float(d[int64_t(m) * N + n]);
-    atomicAdd(&db[n], s);
+#pragma unroll 8
+    for (int m = 0; m < M; ++m) s += __bfloat162float(d[int64_t(m) * N + n]);
+    db[n] += s;
 }
 
 // AdamW on the FP32 master weights (biases not decayed).
@@ -582,8 +583,7 @@ cudaError_t grad_rows(const float* params, const __nv_bfloat16* xb, const float*
         if ((e = gemm<EPI_ATOMIC>(K, kHid, int(M), in, 1, K, d, kHid, 1, nullptr, gW, kHid,
                                   splits, s)) != cudaSuccess)
             return e;
-        dim3 gbg((kHid + 127) / 128, int((M + 255) / 256));
-        k_bias_grad<<<gbg, 128, 0, s>>>(d, int(M), kHid, gb);
+        k_bias_grad<<<(kHid + 63) / 64, 64, 0, s>>>(d, int(M), kHid, gb);
         if (l == 0) break;
         // dh[m][k] = sum_n d[m][n] W_l[k][n]:  B(n, k) = W_l[k][n] = w[k 256 + n]
         if ((e = gemm<EPI_STORE>(int(M), K, kHid, d, kHid, 1, w.w + wofs(l), 1, kHid, nullptr,

@@ -100,6 +100,23 @@ def test_training_reduces_loss(paid, torch):
     assert hist[-1] < 0.3 * hist[0]
 
 
+def test_training_is_bitwise_reproducible(paid, torch):
+    """Two trainings from the same initialisation, data and order seed give
+    identical weights: no atomics in the gradient of a minibatch of <= 1024
+    rows (one split of the weight product, the bias sums in row order)."""
+    rng = np.random.default_rng(4)
+    M = 3000
+    x = torch.as_tensor(rng.normal(size=(M, 32)), dtype=torch.bfloat16, device="cuda")
+    t = torch.as_tensor(rng.normal(size=(M, 256)), dtype=torch.float32, device="cuda")
+    ps = []
+    for _ in range(2):
+        prop = paid.Proposal(seed=2)
+        prop.train(x, t, epochs=3, batch=1024, lr=2e-3, seed=5)
+        torch.cuda.synchronize()
+        ps.append(prop.state())
+    assert np.array_equal(ps[0], ps[1])
+
+
 def test_cell_error_targets_match_oracle_rule(paid, torch):
     ctx = paid.Context(*LAT, ffset=9)
     q = np.array([(0.4, -1.3)])
