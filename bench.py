@@ -255,7 +255,9 @@ def fp64_peak(device):
 
 
 # --------------------------------------------------------------------------- oracle
-def cpu_baseline(w, sample, seed=1234, rule_n=4):
+def cpu_baseline(w, sample, seed=1234, rule_n=4, one_core=256):
+    """The oracle on a seeded sample of the workload on all host threads, and
+    on the first `one_core` integrals of that sample on one thread."""
     import numpy as np
     import oracle
     from paper_1610_09991_gb300 import workloads as W
@@ -263,16 +265,27 @@ def cpu_baseline(w, sample, seed=1234, rule_n=4):
     idx = W.sample_indices(w.n, sample, seed)
     b0 = w.batches[0]
     cores = oracle.max_threads()
+    args = (w.lattice, b0.rel_tol, b0.abs_tol, b0.max_regions)
     t0 = time.perf_counter()
     v, e, r, s = oracle.integrate_list(flat["kind"][idx], flat["q"][idx], flat["lm"][idx],
-                                       flat["T"][idx], w.lattice, b0.rel_tol, b0.abs_tol,
-                                       b0.max_regions, rule_n=rule_n)
+                                       flat["T"][idx], *args, rule_n=rule_n)
     dt = time.perf_counter() - t0
     conv = int((s == 0).sum())
+    one = None
+    if one_core:
+        i1 = idx[:one_core]
+        t1 = time.perf_counter()
+        _, _, _, s1 = oracle.integrate_list(flat["kind"][i1], flat["q"][i1], flat["lm"][i1],
+                                            flat["T"][i1], *args, rule_n=rule_n, nthreads=1)
+        d1 = time.perf_counter() - t1
+        one = {"value": int((s1 == 0).sum()) / d1, "unit": UNIT, "cores": 1,
+               "sample": "the first %d integrals of the same sample, one thread, %.1f s"
+                         % (len(i1), d1)}
     return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d seeded integrals (seed %d) of the %d-integral batch, all %d host "
                       "threads, rule N = %d, %.1f s" % (len(idx), seed, w.n, cores, rule_n, dt),
-            "seconds": dt, "converged": conv, "regions_mean": float(r.mean())}, (idx, v, s)
+            "seconds": dt, "converged": conv, "regions_mean": float(r.mean()),
+            "one_core": one}, (idx, v, s)
 
 
 def group_global_check(w, gv, gs, rule_n, rows_per_batch=4, seed=2024):

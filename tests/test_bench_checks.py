@@ -131,3 +131,12 @@ def test_clock_sampler_keeps_only_the_timed_window(bench, tmp_path):
     assert out["samples"] == 3
     assert out["sm_mhz"] == 2070 and out["sm_max_mhz"] == 2070
     assert out["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_cpu_baseline_reports_all_threads_and_one_core(bench):
+    """The oracle baseline: a seeded sample on every host thread and its first
+    integrals on one thread, both as converged integrals per second."""
+    cb, (idx, v, s) = bench.cpu_baseline(W.config_first_shell(), 8, one_core=3)
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0
+    assert cb["converged"] == 8 and len(idx) == 8 and np.all(s == 0)
+    assert cb["one_core"]["cores"] == 1 and cb["one_core"]["value"] > 0
